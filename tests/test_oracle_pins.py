@@ -1,0 +1,256 @@
+"""Pins for the CPU oracle: closed forms, invariants and exact identities.
+
+Each test ties the oracle to something other than itself: a value the paper's
+definitions fix in closed form, a textbook identity, or an independent
+construction (dense Kronecker products, the exact density matrix, the
+statevector). A plausible slip anywhere in the oracle (a dropped Kraus term, a
+wrong sign or qubit index, a transposed factor) fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+from oracle import lret as O
+from workloads import random_layered, random_pauli_sum, hea
+
+
+def kron_pauli(n, term):
+    """Dense 2^n x 2^n Pauli string built by Kronecker products (independent of apply_rows)."""
+    mats = [O.I2] * n
+    for q, s in term:
+        mats[q] = O.PAULI[s]
+    out = np.array([[1.0 + 0j]])
+    for q in range(n - 1, -1, -1):  # most significant qubit first
+        out = np.kron(out, mats[q])
+    return out
+
+
+# ---- channels (Sec. III.A) -------------------------------------------------
+
+@pytest.mark.parametrize("p", [0.0, 1e-3, 0.0033, 0.2, 0.75])
+def test_kraus_completeness(p):
+    for ks in (O.depolarizing(p), O.amplitude_damping(p), O.bit_flip(p)):
+        S = sum(K.conj().T @ K for K in ks)
+        assert np.max(np.abs(S - np.eye(2))) < 1e-15
+
+
+def test_depolarizing_on_zero_closed_form():
+    p = 0.03
+    st = O.LRETState(1)
+    st.channel(0, O.depolarizing(p))
+    pr = st.probs()
+    # (1-p)|0><0| + p/3 (|1><1| + |1><1| + |0><0|)
+    assert np.allclose(pr, [1 - 2 * p / 3, 2 * p / 3], atol=1e-15)
+
+
+def test_amplitude_damping_on_one_closed_form():
+    g = 0.07
+    st = O.LRETState(1)
+    st.gate([0], O.PAULI["X"])
+    st.channel(0, O.amplitude_damping(g))
+    assert np.allclose(st.probs(), [g, 1 - g], atol=1e-15)
+
+
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_ry_then_depolarizing_z_closed_form(k):
+    # Ry(t)|0> has <Z> = cos t, <X> = sin t; each depolarizing scales the Bloch vector by 1 - 4p/3
+    t, p = 0.7, 0.02
+    st = O.LRETState(1)
+    st.gate([0], O.rotation("Y", t))
+    for _ in range(k):
+        st.channel(0, O.depolarizing(p))
+    f = (1 - 4 * p / 3) ** k
+    assert abs(st.expect([(1.0, [(0, "Z")])]) - f * np.cos(t)) < 1e-14
+    assert abs(st.expect([(1.0, [(0, "X")])]) - f * np.sin(t)) < 1e-14
+
+
+def test_rotation_sign_conventions():
+    # Ry(pi/2)|0> = |+>; Rz(phi) then gives <X> = cos phi, <Y> = sin phi
+    phi = 0.4
+    st = O.SVState(1)
+    st.gate([0], O.rotation("Y", np.pi / 2))
+    st.gate([0], O.rotation("Z", phi))
+    assert abs(st.expect([(1.0, [(0, "X")])]) - np.cos(phi)) < 1e-14
+    assert abs(st.expect([(1.0, [(0, "Y")])]) - np.sin(phi)) < 1e-14
+    # Rx(t)|0>: <Y> = -sin t
+    st = O.SVState(1)
+    st.gate([0], O.rotation("X", 0.3))
+    assert abs(st.expect([(1.0, [(0, "Y")])]) + np.sin(0.3)) < 1e-14
+
+
+def test_rotation_derivative_matches_fd():
+    for ax in "XYZ":
+        t, h = 0.37, 1e-6
+        fd = (O.rotation(ax, t + h) - O.rotation(ax, t - h)) / (2 * h)
+        assert np.max(np.abs(fd - O.rotation_derivative(ax, t))) < 1e-9
+
+
+def test_cnot_and_qubit_order():
+    # |x> with x = 1 (qubit 0 set). CNOT(0 -> 2) must give x = 1 + 4 = 5.
+    n = 3
+    st = O.SVState(n)
+    st.gate([0], O.PAULI["X"])
+    st.gate([0, 2], O.cnot())
+    assert abs(st.probs()[5] - 1.0) < 1e-15
+    # CNOT(2 -> 0) on the same state does nothing (control qubit 2 is 0)
+    st2 = O.SVState(n)
+    st2.gate([0], O.PAULI["X"])
+    st2.gate([2, 0], O.cnot())
+    assert abs(st2.probs()[1] - 1.0) < 1e-15
+    # CZ phase: |11> on qubits (1,2) picks up -1; check via <X_1> after H-like prep
+    st3 = O.SVState(3)
+    st3.gate([1], O.rotation("Y", np.pi / 2))
+    st3.gate([2], O.PAULI["X"])
+    st3.gate([1, 2], O.cz())
+    assert abs(st3.expect([(1.0, [(1, "X")])]) + 1.0) < 1e-14
+
+
+def test_apply_rows_matches_kron():
+    rng = np.random.default_rng(1)
+    n = 4
+    A = rng.normal(size=(2 ** n, 3)) + 1j * rng.normal(size=(2 ** n, 3))
+    U = np.linalg.qr(rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4)))[0]
+    # dense operator for U on qubits (3, 1): basis index of U = 2*b3 + b1
+    D = np.zeros((2 ** n, 2 ** n), dtype=complex)
+    for x in range(2 ** n):
+        b3, b1 = (x >> 3) & 1, (x >> 1) & 1
+        for o in range(4):
+            y = x & ~(1 << 3) & ~(1 << 1)
+            y |= ((o >> 1) & 1) << 3
+            y |= (o & 1) << 1
+            D[y, x] += U[o, 2 * b3 + b1]
+    assert np.allclose(O.apply_rows(n, A, [3, 1], U), D @ A, atol=1e-13)
+
+
+def test_pauli_expectation_matches_dense_kron():
+    rng = np.random.default_rng(2)
+    n = 5
+    L = rng.normal(size=(2 ** n, 4)) + 1j * rng.normal(size=(2 ** n, 4))
+    terms = random_pauli_sum(n, 12, seed=7)
+    st = O.LRETState(n)
+    st.L = L
+    H = sum(c * kron_pauli(n, t) for c, t in terms)
+    ref = np.real(np.trace(H @ (L @ L.conj().T)))
+    assert abs(st.expect(terms) - ref) < 1e-11
+    # Y on (|0> + i|1>)/sqrt2 is +1
+    s = O.SVState(1)
+    s.psi = np.array([[1.0], [1j]]) / np.sqrt(2)
+    assert abs(s.expect([(1.0, [(0, "Y")])]) - 1.0) < 1e-15
+
+
+# ---- exact evolution (Eq. 1) ----------------------------------------------
+
+def test_fdm_trace_positivity_and_sv():
+    n = 4
+    ops = random_layered(n, 3, seed=11, noise=("mixed", 0.05, 0.08))
+    st = O.run_fdm(n, ops)
+    assert abs(np.trace(st.rho).real - 1) < 1e-13
+    assert np.min(np.linalg.eigvalsh(st.rho)) > -1e-13
+    ops0 = random_layered(n, 3, seed=11, noise=None)
+    fd0 = O.run_fdm(n, ops0)
+    sv = O.run_sv(n, ops0)
+    assert np.max(np.abs(fd0.rho - sv.psi @ sv.psi.conj().T)) < 1e-13
+
+
+# ---- low rank vs exact -----------------------------------------------------
+
+def test_lret_full_rank_equals_fdm():
+    # 6 qubits, r = 64 >= rank: Algorithm 1 reproduces Eq. (1) to 1e-12
+    n = 6
+    ops = random_layered(n, 4, seed=1001, noise=("mixed", 0.01, 0.02))
+    lr = O.run_lret(n, ops, r=2 ** n)
+    fd = O.run_fdm(n, ops)
+    assert np.max(np.abs(lr.rho() - fd.rho)) < 1e-12
+    assert lr.discarded < 1e-12
+    terms = random_pauli_sum(n, 20, seed=5)
+    assert abs(lr.expect(terms) - fd.expect(terms)) < 1e-12
+
+
+def test_lret_zero_noise_equals_statevector():
+    n = 5
+    ops = random_layered(n, 5, seed=3, noise=("dep", 0.0))
+    lr = O.run_lret(n, ops, r=1)
+    sv = O.run_sv(n, ops)
+    assert np.max(np.abs(lr.probs() - sv.probs())) < 1e-13
+    assert abs(lr.trace() - 1.0) < 1e-13
+
+
+def test_theorem1_gram_spectrum():
+    # App. B: B^dag B and B B^dag share the m nonzero eigenvalues; B u are eigenvectors
+    rng = np.random.default_rng(4)
+    B = rng.normal(size=(40, 7)) + 1j * rng.normal(size=(40, 7))
+    lm, U = np.linalg.eigh(B.conj().T @ B)
+    lD = np.linalg.eigvalsh(B @ B.conj().T)
+    assert np.allclose(np.sort(lD)[-7:], lm, rtol=1e-12, atol=1e-10)
+    D = B @ B.conj().T
+    for i in range(7):
+        v = B @ U[:, i]
+        assert np.allclose(D @ v, lm[i] * v, atol=1e-9)
+
+
+def test_truncation_error_equals_discarded_mass():
+    # Eckart-Young (Sec. II.B): || rho' - rho_trunc ||_1 = sum of dropped eigenvalues
+    n = 4
+    ops = random_layered(n, 1, seed=8, noise=("dep", 0.05))
+    chans = [i for i, o in enumerate(ops) if O.is_channel(o)]
+    ops = [o for i, o in enumerate(ops) if not O.is_channel(o) or i in chans[:3]]
+    st = O.run_lret(n, ops, compress=False)  # untruncated L, 4^3 columns
+    rho_full = st.rho()
+    d = st.compress(r=3)
+    diff = np.linalg.eigvalsh(rho_full - st.rho())
+    assert abs(np.sum(np.abs(diff)) - d) < 1e-13
+    assert d > 1e-4
+    # trace bookkeeping: Tr rho = 1 - cumulative discarded mass
+    assert abs(st.trace() - (1 - d)) < 1e-13
+
+
+def test_product_state_spectrum_closed_form():
+    # depolarizing on each of 3 qubits of |000>: eigenvalues are products of (1-2p/3, 2p/3)
+    n, p = 3, 0.1
+    st = O.LRETState(n)
+    for q in range(n):
+        st.channel(q, O.depolarizing(p))
+    a, b = 1 - 2 * p / 3, 2 * p / 3
+    from math import comb
+    expect = sorted([a ** (n - k) * b ** k for k in range(n + 1) for _ in range(comb(n, k))], reverse=True)
+    d = st.compress(r=4)
+    lam = st.log[-1]["lam"]
+    assert np.allclose(lam[:8], expect, atol=1e-14)
+    assert abs(d - sum(expect[4:])) < 1e-14
+
+
+def test_eps_rule_reading():
+    lam = np.array([0.6, 0.3, 0.05, 0.03, 0.02])
+    # cumulative 0.6, 0.9, 0.95, 0.98, 1.0; eps = 0.05 -> reach 0.95 with k = 3 (crossing kept)
+    assert O.choose_rank(lam, eps=0.05) == 3
+    assert O.choose_rank(lam, eps=0.049) == 4
+    assert O.choose_rank(lam, eps=0.5) == 1
+    assert O.choose_rank(lam, r=2) == 2
+    assert O.choose_rank(lam, r=9) == 5
+
+
+def test_lowrank_trace_distance_matches_dense():
+    rng = np.random.default_rng(9)
+    A = rng.normal(size=(32, 3)) + 1j * rng.normal(size=(32, 3))
+    B = rng.normal(size=(32, 5)) + 1j * rng.normal(size=(32, 5))
+    dense = 0.5 * np.sum(np.abs(np.linalg.eigvalsh(A @ A.conj().T - B @ B.conj().T)))
+    assert abs(O.trace_distance_lowrank(A, B) - dense) < 1e-10
+
+
+# ---- gradients -------------------------------------------------------------
+
+def test_gradient_fd_full_rank_matches_parameter_shift():
+    # r = 2^n LRET is exact, so its FD gradient equals the parameter-shift gradient of Eq. (1)
+    n = 3
+    ops, th = hea(n, 2, seed=4000, noise=("dep", 0.02))
+    terms = random_pauli_sum(n, 6, seed=41)
+    g_fd = O.gradient_fd_lret(n, ops, th, terms, r=2 ** n, h=1e-4)
+    g_ps = O.gradient_param_shift_fdm(n, ops, th, terms)
+    assert np.max(np.abs(g_fd - g_ps)) < 1e-8
+    assert np.max(np.abs(g_ps)) > 1e-2
+
+
+def test_distortion_definition():
+    pe = np.array([0.5, 0.3, 0.2])
+    pn = np.array([0.6, 0.3, 0.1])
+    pl = np.array([0.52, 0.29, 0.19])
+    assert abs(O.distortion(pl, pe, pn) - (0.04 / 0.2)) < 1e-15

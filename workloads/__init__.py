@@ -1,0 +1,178 @@
+"""Seeded synthetic workloads shared by the oracle and the CUDA path.
+
+This module holds no arithmetic of the low-rank method. It only draws random
+numbers (NumPy PCG64 via ``default_rng``) and writes them into plain op lists:
+gate names, qubit indices, angles, channel names and strengths, and Pauli
+strings with coefficients. Each consumer turns these descriptions into
+matrices with its own code.
+
+Op list format (a list of dicts, applied in order):
+
+* ``{"op": "ry"|"rz"|"rx", "q": int, "theta": float, "pid": int}`` -- a
+  one-qubit rotation; ``pid`` is the parameter index (``-1`` = fixed).
+* ``{"op": "cnot", "q": [control, target]}`` and ``{"op": "cz", "q": [a, b]}``.
+* ``{"op": "dep", "q": int, "p": float}`` -- one-qubit depolarizing channel.
+* ``{"op": "ad", "q": int, "gamma": float}`` -- one-qubit amplitude damping.
+* ``{"op": "bf", "q": int, "p": float}`` -- one-qubit bit flip.
+
+Qubit ``q`` is bit ``q`` of the computational-basis index (little-endian).
+Channels follow the gate they decorate; the low-rank runners truncate after
+every channel (one-qubit Kraus groups, Sec. II.C with M = 1).
+
+Workload families (Sec. III.A uses random layered circuits; the sizes below
+are those of the five benchmark configurations):
+
+* ``random_layered``: per layer, Ry then Rz on every qubit (angles U[0, 2pi)),
+  then CNOTs on a seeded random perfect matching (first of each pair is the
+  control; with odd n one qubit idles). A channel follows every gate on every
+  qubit that gate touches.
+* ``hea``: hardware-efficient ansatz, per layer Ry and Rz on every qubit
+  (angles N(0, 0.5^2), all differentiable) then a CZ ladder CZ(0,1)...CZ(n-2,n-1).
+* ``random_pauli_sum``: T terms, weight U{1..min(4, n)}, distinct qubits,
+  uniform X/Y/Z, coefficients N(0, 1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "random_layered",
+    "hea",
+    "random_pauli_sum",
+    "count_ops",
+    "CONFIGS",
+]
+
+
+def _channel(rng, q, noise):
+    """Return the channel op for qubit q under a noise spec.
+
+    noise: ("dep", p) | ("ad", gamma) | ("bf", p) | ("mixed", p_dep, gamma_ad)
+    For "mixed", one seeded coin per gate picks the kind (drawn by the caller).
+    """
+    kind = noise[0]
+    if kind == "dep":
+        return {"op": "dep", "q": int(q), "p": float(noise[1])}
+    if kind == "ad":
+        return {"op": "ad", "q": int(q), "gamma": float(noise[1])}
+    if kind == "bf":
+        return {"op": "bf", "q": int(q), "p": float(noise[1])}
+    raise ValueError(f"unknown noise kind {kind!r}")
+
+
+def _noise_for_gate(rng, noise):
+    if noise is None:
+        return None
+    if noise[0] == "mixed":
+        return ("dep", noise[1]) if rng.random() < 0.5 else ("ad", noise[2])
+    return noise
+
+
+def random_layered(n, depth, seed, noise=("dep", 1e-3), two_qubit="cnot",
+                   param_ids=False):
+    """Seeded random layered circuit (Ry, Rz on every qubit, then a matching)."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    rng = np.random.default_rng(seed)
+    ops = []
+    pid = 0
+    for _ in range(depth):
+        for q in range(n):
+            for name in ("ry", "rz"):
+                theta = float(rng.uniform(0.0, 2.0 * np.pi))
+                ops.append({"op": name, "q": q, "theta": theta,
+                            "pid": pid if param_ids else -1})
+                if param_ids:
+                    pid += 1
+                nz = _noise_for_gate(rng, noise)
+                if nz is not None:
+                    ops.append(_channel(rng, q, nz))
+        perm = rng.permutation(n)
+        for i in range(0, n - 1, 2):
+            a, b = int(perm[i]), int(perm[i + 1])
+            ops.append({"op": two_qubit, "q": [a, b]})
+            nz = _noise_for_gate(rng, noise)
+            if nz is not None:
+                ops.append(_channel(rng, a, nz))
+                ops.append(_channel(rng, b, nz))
+    return ops
+
+
+def hea(n, layers, seed, noise=("dep", 1e-3), theta_std=0.5):
+    """Hardware-efficient ansatz: (Ry, Rz on every qubit, CZ ladder) x layers.
+
+    Every rotation is differentiable; parameter ids run 0..2*n*layers-1 in op
+    order. Returns (ops, theta) where theta is the initial parameter vector.
+    """
+    rng = np.random.default_rng(seed)
+    ops = []
+    thetas = []
+    for _ in range(layers):
+        for name in ("ry", "rz"):
+            for q in range(n):
+                th = float(rng.normal(0.0, theta_std))
+                ops.append({"op": name, "q": q, "theta": th, "pid": len(thetas)})
+                thetas.append(th)
+                nz = _noise_for_gate(rng, noise)
+                if nz is not None:
+                    ops.append(_channel(rng, q, nz))
+        for q in range(n - 1):
+            ops.append({"op": "cz", "q": [q, q + 1]})
+            nz = _noise_for_gate(rng, noise)
+            if nz is not None:
+                ops.append(_channel(rng, q, nz))
+                ops.append(_channel(rng, q + 1, nz))
+    return ops, np.asarray(thetas, dtype=np.float64)
+
+
+def random_pauli_sum(n, T, seed, max_weight=4):
+    """T random Pauli strings: list of (coeff, [(qubit, 'X'|'Y'|'Z'), ...])."""
+    rng = np.random.default_rng(seed)
+    terms = []
+    for _ in range(T):
+        w = int(rng.integers(1, min(max_weight, n) + 1))
+        qs = rng.choice(n, size=w, replace=False)
+        letters = rng.integers(0, 3, size=w)
+        c = float(rng.normal())
+        terms.append((c, [(int(q), "XYZ"[int(l)]) for q, l in zip(qs, letters)]))
+    return terms
+
+
+def count_ops(ops):
+    """(gates, channels) in an op list."""
+    g = sum(1 for o in ops if o["op"] in ("rx", "ry", "rz", "cnot", "cz"))
+    c = sum(1 for o in ops if o["op"] in ("dep", "ad", "bf"))
+    return g, c
+
+
+# The five benchmark workloads (sizes and laws of the paper-style random
+# circuits; seeds are 1000 * config_id + instance).
+CONFIGS = {
+    "c1_6q_r13": dict(n=6, r=13, depth=40, noise=("dep", 0.0033), seed=1000),
+    "c2_12q_r32": dict(n=12, r=32, depth=100, noise=("mixed", 1e-3, 2e-3), seed=2000),
+    "c3_20q_r64": dict(n=20, r=64, depth=200, noise=("dep", 5e-4), seed=3000),
+    "c4_14q_hea": dict(n=14, r=32, layers=6, noise=("dep", 1e-3), seed=4000,
+                       terms=50, ckpt_every=8),
+    "c5_batch256": dict(count=256, n_range=(8, 18), ranks=(8, 16, 32, 64),
+                        depth_range=(40, 200), noise=("mixed", 1e-3, 2e-3), seed=5000),
+}
+
+
+def batch_circuits(count=256, n_range=(8, 18), ranks=(8, 16, 32, 64),
+                   depth_range=(40, 200), noise=("mixed", 1e-3, 2e-3), seed=5000,
+                   depth_scale=1.0):
+    """Seeded heterogeneous batch: list of dicts {n, r, depth, ops}.
+
+    depth_scale < 1 shrinks every depth (for quick tests); the draws are the
+    same for every scale so a scaled batch is a prefix-faithful miniature.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        r = int(rng.choice(ranks))
+        depth = int(rng.integers(depth_range[0], depth_range[1] + 1))
+        d = max(1, int(round(depth * depth_scale)))
+        ops = random_layered(n, d, seed + 1 + i, noise=noise)
+        out.append({"n": n, "r": r, "depth": d, "ops": ops})
+    return out
