@@ -1,0 +1,419 @@
+"""Benchmark: noisy gate-steps/sec of low-rank noisy-circuit evolution on GB300.
+
+Workload (synthetic, seeded): 20 qubits, rank r = 64, random layered circuit
+(Ry, Rz on every qubit, then CNOTs on a random perfect matching), one-qubit
+depolarizing channel p = 5e-4 after every gate on every qubit it touches
+(K = 4 Kraus matrices, r*K = 256 columns before each truncation). V is
+2^20 x 64 complex64 (0.54 GB), the expansion 2^20 x 256 (2.1 GB): both far
+larger than L2, so no flush is needed between steps.
+
+One step = one circuit layer through the whole forward path: 50 gates, each
+fused with its channel expansion, 60 truncations (Gram, eigensolve,
+projection), then the readouts Prob(x) and <H> for a 64-term random Pauli sum.
+A noisy gate-step is one gate with its channel(s) and truncation(s).
+
+Prints one JSON line (see the keys below). --impl reference times the CPU
+oracle on this host on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_QUBITS, RANK, P_DEP, DEPTH, N_TERMS, SEED = 20, 64, 5e-4, 200, 64, 3000
+METRIC = "noisy gate-steps/sec at 20q r=64 (mixed vs FP64), adjoint grad time/forward"
+
+
+def workload_config():
+    return {"workload": "random layered Ry/Rz+CNOT, 20 qubits, r=64, depolarizing p=5e-4 after every gate "
+                        "(K=4, rK=256), <H> of 64 random Pauli terms",
+            "n_qubits": N_QUBITS, "rank": RANK, "kraus": 4, "depth_total": DEPTH, "step": "one circuit layer",
+            "gates_per_step": None, "truncations_per_step": None,
+            "l2_policy": "inputs larger than L2 (V 0.54 GB, expansion 2.1 GB)"}
+
+
+_LAYERS = None
+
+
+def get_layers():
+    global _LAYERS
+    if _LAYERS is None:
+        from workloads import random_layered
+        ops = random_layered(N_QUBITS, DEPTH, seed=SEED, noise=("dep", P_DEP))
+        layers, cur = [], []
+        per_layer = 2 * N_QUBITS * 2 + (N_QUBITS // 2) * 3  # gates + their channels
+        for o in ops:
+            cur.append(o)
+            if len(cur) == per_layer:
+                layers.append(cur)
+                cur = []
+        assert not cur and len(layers) == DEPTH
+        _LAYERS = layers
+    return _LAYERS
+
+
+def count(ops):
+    from workloads import count_ops
+    return count_ops(ops)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2009_06657_gb300 as lr
+    from workloads import random_pauli_sum
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    layers = get_layers()
+    terms = random_pauli_sum(N_QUBITS, N_TERMS, seed=SEED + 1)
+    xm, zm, cf = lr.pauli_masks(terms, N_QUBITS)
+    sim = lr.LRSim(N_QUBITS, RANK, dtype="c64", stream=stream)
+    probs = torch.empty(1 << N_QUBITS, dtype=torch.float32, device=dev)
+    g_per, c_per = count(layers[0])
+
+    def step(i):
+        lr.run_ops(sim, layers[i % DEPTH], r=RANK)
+        sim.probs(probs)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(i)
+        sim.expect_masks(xm, zm, cf)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(args.steps):
+            step(args.warmup + i)
+        sim.expect_masks(xm, zm, cf)  # readout of <H> at the end of the timed region
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+            torch.distributed.barrier()
+
+        # per-kernel device time over one more step (CUDA events on the handle's stream)
+        sim.set_timing(True)
+        step(args.warmup + args.steps)
+        sim.expect_masks(xm, zm, cf)
+        ktimes = sim.kernel_times()
+        sim.set_timing(False)
+
+        # end to end through the public API with host buffers: host parameters in,
+        # Prob(x) and <H> copied back to pinned host memory, every step
+        host_p = torch.empty(1 << N_QUBITS, dtype=torch.float32, pin_memory=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 3))
+        for i in range(n_e2e):
+            lr.run_ops(sim, layers[(args.warmup + args.steps + 1 + i) % DEPTH], r=RANK)
+            sim.probs(probs)
+            host_p.copy_(probs, non_blocking=True)
+            sim.expect_masks(xm, zm, cf)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+
+    # FP64 comparators at the same size (few truncations; rate per noisy gate-step)
+    fp64 = bench_fp64(args, layers, dev, stream) if (rank == 0 and not args.no_fp64) else None
+    info = sim.info()
+    sim.close()
+    return dict(ms=ms, g_per=g_per, c_per=c_per, ktimes=ktimes, clk=clk, e2e_s=e2e_s, fp64=fp64, info=info)
+
+
+def bench_fp64(args, layers, dev, stream):
+    """Plain FP64 low-rank GPU path on the same GB300: complex128 torch/cuBLAS
+    GEMMs and torch.linalg.eigh, plus this library's own complex128 path.
+    Times truncation steps at the steady state (c = 64 -> 256 columns)."""
+    import torch
+
+    import paper_2009_06657_gb300 as lr
+    out = {}
+    # (a) this library, complex128 (FP64 Jacobi eigensolve, FP64 Gram)
+    sim = lr.LRSim(N_QUBITS, RANK, dtype="c128", stream=stream)
+    ops = layers[0]
+    # advance until the first truncation at full width has happened
+    idx = 0
+    with torch.cuda.stream(stream):
+        while sim.info()["compressions"] < 1:
+            o = ops[idx]; idx += 1
+            lr.run_ops(sim, [o], r=RANK)
+        torch.cuda.synchronize()
+        n_tr = 0
+        t0 = time.perf_counter()
+        while n_tr < 2 and idx < len(ops):
+            o = ops[idx]; idx += 1
+            lr.run_ops(sim, [o], r=RANK)
+            if o["op"] in ("dep",):
+                n_tr += 1
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / max(n_tr, 1)
+    sim.close()
+    out["ours_c128_s_per_truncation"] = dt
+    # (b) plain torch complex128 (cuBLAS ZGEMM + cuSOLVER eigh)
+    N = 1 << N_QUBITS
+    g = torch.Generator(device=dev).manual_seed(1)
+    V = torch.randn(N, RANK, dtype=torch.complex128, device=dev, generator=g)
+    V /= torch.linalg.norm(V)
+    K = [torch.eye(2, dtype=torch.complex128, device=dev) * (1 - P_DEP) ** 0.5]
+    sx = torch.tensor([[0, 1], [1, 0]], dtype=torch.complex128, device=dev)
+    sy = torch.tensor([[0, -1j], [1j, 0]], dtype=torch.complex128, device=dev)
+    sz = torch.tensor([[1, 0], [0, -1]], dtype=torch.complex128, device=dev)
+    K += [s * (P_DEP / 3) ** 0.5 for s in (sx, sy, sz)]
+
+    def plain_step(V, q):
+        Vt = V.reshape(N >> (q + 1), 2, 1 << q, V.shape[1])
+        Vp = torch.cat([torch.einsum("ab,ibjc->iajc", k, Vt).reshape(N, -1) for k in K], dim=1)
+        G = Vp.conj().T @ Vp
+        lam, U = torch.linalg.eigh(G)
+        return Vp @ U[:, -RANK:].flip(1)
+
+    with torch.cuda.stream(stream):
+        V = plain_step(V, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 2
+        for i in range(reps):
+            V = plain_step(V, 1 + i)
+        torch.cuda.synchronize()
+        out["torch_c128_s_per_truncation"] = (time.perf_counter() - t0) / reps
+    del V
+    torch.cuda.empty_cache()
+    return out
+
+
+def algorithmic(kclass, info_c):
+    """(bound, bytes_or_flops per launch) of a steady-state launch of a kernel class."""
+    N, r, K, esz = 1 << N_QUBITS, RANK, 4, 8
+    m = r * K
+    if kclass == "expand":
+        return "hbm", N * r * esz + N * m * esz          # read V (c = r), write V' (r*K)
+    if kclass == "project":
+        return "hbm", N * m * esz + N * r * esz          # read V', write V
+    if kclass == "gram":
+        return "alu", 8.0 * N * m * m / 2                # Hermitian half, complex FMA = 8 flops
+    if kclass == "readout":
+        return "hbm", N * r * esz + N * 4
+    if kclass == "pauli":
+        return "hbm", 2 * N * r * esz
+    return "alu", None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank != 0:
+        return
+    import json as _j
+    peaks = load_peaks()
+    gsteps = res["g_per"] * args.steps * world
+    value = gsteps / (res["ms"] / 1e3)
+    kt = res["ktimes"]
+    dom = max(kt, key=lambda k: kt[k][0])
+    bound, alg = algorithmic(dom, RANK)
+    avg_ms = kt[dom][0] / max(kt[dom][1], 1)
+    if bound == "hbm":
+        ach = alg / (avg_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]; unit = "GB/s"
+    else:
+        ach = (alg / (avg_ms * 1e-3) / 1e12) if alg else None
+        peak = peaks["fp32_tflops"]; unit = "TFLOP/s"
+    cfg = workload_config()
+    cfg["gates_per_step"] = res["g_per"]
+    cfg["truncations_per_step"] = res["c_per"]
+    out = {
+        "metric": METRIC, "value": value, "unit": "noisy gate-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (FP32 arithmetic, FP64 sums/accounting)",
+        "data": "synthetic (seeded random circuits)", "config": cfg,
+        "gpu_launches": None,
+        "kernel_ms_per_step": {k: v[0] for k, v in kt.items()},
+        "kernel_launches_per_step": {k: v[1] for k, v in kt.items()},
+        "roofline": {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                     "frac": (ach / peak) if ach else None, "traffic": None,
+                     "peak_source": peaks["source"]},
+        "clocks": res["clk"],
+        "e2e": {"value": res["g_per"] / res["e2e_s"], "unit": "noisy gate-steps/s",
+                "h2d_bytes_per_step": h2d_bytes(get_layers()[0]), "d2h_bytes_per_step": (1 << N_QUBITS) * 4 + 8},
+        "fp64": None, "cpu_baseline": None,
+    }
+    launches = sum(v[1] for v in kt.values())
+    out["gpu_launches"] = launches * args.steps
+    if res["fp64"]:
+        f = res["fp64"]
+        tps = res["c_per"] / res["g_per"]  # truncations per gate-step
+        out["fp64"] = {k.replace("_s_per_truncation", "_gate_steps_per_s"): 1.0 / (v * tps) for k, v in f.items()}
+        out["fp64"]["mixed_over_ours_c128"] = value / out["fp64"]["ours_c128_gate_steps_per_s"]
+        out["fp64"]["mixed_over_torch_c128"] = value / out["fp64"]["torch_c128_gate_steps_per_s"]
+    if not args.no_cpu and world == 1:
+        out["cpu_baseline"] = cpu_baseline(res)
+    print(_j.dumps(out))
+
+
+def h2d_bytes(ops):
+    b = 0
+    for o in ops:
+        if o["op"] in ("ry", "rz", "rx"):
+            b += 8 + 8  # angle + parameter id
+        elif o["op"] in ("cnot", "cz"):
+            b += 16 * 16 + 8
+        else:
+            b += 4 * 64  # Kraus set (4 x 2x2 complex128)
+    return b
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nominal unit counts and clock)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
+                "source": "hbm/bf16 measured (MEASURED_PEAKS.json); fp32 from unit counts x max clock"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
+            "source": "fallback"}
+
+
+def cpu_sample():
+    """Bounded CPU sample: the oracle runs the first layer's ops up to and
+    including its second full-width truncation (c = 64 -> 256 -> 64)."""
+    from oracle import lret as O
+    ops = get_layers()[0]
+    st = O.LRETState(N_QUBITS)
+    full = 0
+    t_trunc, n_trunc, g_done, t_all0 = 0.0, 0, 0, time.perf_counter()
+    for o in ops:
+        if O.is_gate(o):
+            qs, U = O.gate_matrix(o)
+            st.gate(qs, U)
+            g_done += 1
+        else:
+            st.channel(o["q"], O.channel_kraus(o))
+            t0 = time.perf_counter()
+            st.compress(r=RANK)
+            if st.log[-1]["m"] == 4 * RANK:
+                t_trunc += time.perf_counter() - t0
+                n_trunc += 1
+                full += 1
+                if full >= 2:
+                    break
+    return t_trunc / max(n_trunc, 1), n_trunc
+
+
+def cpu_baseline(res):
+    s_per_tr, n_tr = cpu_sample()
+    tps = res["c_per"] / res["g_per"]
+    return {"value": 1.0 / (s_per_tr * tps), "unit": "noisy gate-steps/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"oracle (NumPy complex128) on the host: {n_tr} full-width truncations (2^20 x 256 "
+                      f"Gram, eigh, projection) of the 20-qubit workload, extrapolated per noisy gate-step"}
+
+
+def run_reference(args):
+    per = []
+    for i in range(args.warmup + args.steps):
+        s, n = cpu_sample()
+        if i >= args.warmup:
+            per.append(s)
+        if i == 0 and args.warmup + args.steps > 2:
+            break  # one sample bounds the run to a few minutes
+    s_per_tr = statistics.median(per) if per else s
+    g_per, c_per = count(get_layers()[0])
+    v = 1.0 / (s_per_tr * c_per / g_per)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "noisy gate-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded random circuits)",
+            "config": workload_config(),
+            "cpu_baseline": {"value": v, "unit": "noisy gate-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "full-width truncations of the 20-qubit workload on host cores"},
+            "e2e": {"value": v, "unit": "noisy gate-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * lret.h -- C ABI of liblret, low-rank noisy-circuit evolution on one GB300.
+ *
+ * Method: Chen, Farquhar, Parrish, "Low Rank Density Matrix Evolution for
+ * Noisy Quantum Circuits" (arXiv:2009.06657). The density matrix is held as
+ * rho = V V^dag with V a 2^n x c complex matrix (Eq. 2). A gate maps
+ * V <- G V (Eq. 3); a Kraus channel maps V <- [Kt_1 V, ..., Kt_K V] (Eq. 4);
+ * a compression keeps the leading eigenvectors of rho, found from the small
+ * Gram matrix V^dag V (Sec. II.B and Theorem 1 of App. B); readouts are
+ * Prob(x) = sum_v |V_xv|^2 (Eq. 9) and <O> = Tr(V^dag O V) (Sec. II.D).
+ *
+ * Conventions
+ *   - Qubit q is bit q of the basis index x (little-endian).
+ *   - Complex numbers are interleaved (re, im) pairs of double in every host
+ *     array of this interface; matrices are row-major.
+ *   - A two-qubit matrix on qubits (q0, q1) is indexed by 2*b(q0) + b(q1).
+ *   - Kraus matrices carry their probability: Kt_a = sqrt(p_a) K_a (Eq. 1).
+ *   - Pauli strings are (xmask, zmask) pairs: bit q of xmask set and zmask
+ *     clear = X on q, zmask only = Z, both = Y. With that encoding
+ *     P|x> = i^{#Y} (-1)^{popcount(x & zmask)} |x ^ xmask>.
+ *
+ * State and memory
+ *   - A handle owns all device memory of one simulation (allocated with
+ *     cudaMalloc in lr_init, released by lr_free). Work is queued on the CUDA
+ *     stream given to lr_init. Host arrays passed in are copied during the
+ *     call; the caller keeps ownership. Device output buffers belong to the
+ *     caller.
+ *   - Gates and channels are queued lazily and fused: a gate followed by a
+ *     channel on one of its qubits runs as one expansion kernel.
+ *   - Calls that return host values synchronise the handle's stream.
+ *   - One host thread per handle.
+ *
+ * Errors: every call returns LR_OK (0) or a negative status. After an error
+ * the handle's state is unchanged unless the status is LR_ECUDA.
+ */
+#ifndef LRET_H
+#define LRET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LR_OK 0
+#define LR_EINVAL -1     /* bad argument: qubit out of range, nq > 2, n > 30, ... */
+#define LR_EKRAUS -2     /* || sum_a Kt_a^dag Kt_a - I ||_max > 1e-10 */
+#define LR_ECAPACITY -3  /* columns would exceed the allocated capacity */
+#define LR_ENOMEM -4     /* device allocation failed */
+#define LR_ETIMEOUT -5   /* a bounded device-side wait gave up */
+#define LR_ECUDA -6      /* a CUDA call failed */
+#define LR_ESTATE -7     /* call not valid in the current state */
+#define LR_ENOCONV -8    /* eigensolver reached its sweep limit */
+
+#define LR_C64 0   /* complex64 state; FP32 arithmetic with FP64 sums */
+#define LR_C128 1  /* complex128 state; FP64 throughout */
+
+typedef struct lr_ctx* lr_handle;
+
+/* Create a simulation of n qubits (1..30) in |0...0> (V = e_0, c = 1,
+ * Algorithm 1 initial state). r is the default rank for lr_compress(r <= 0 ->
+ * this r) and sets the column capacity to 4*r (a one-qubit channel with up to
+ * four Kraus matrices). dtype is LR_C64 or LR_C128. stream is a cudaStream_t
+ * (NULL = the legacy default stream). */
+int lr_init(int n, int r, int dtype, void* stream, lr_handle* out);
+
+/* Like lr_init with an explicit column capacity (>= r). */
+int lr_init_ex(int n, int r, int dtype, int capacity, void* stream, lr_handle* out);
+
+int lr_free(lr_handle h);
+
+/* Return to |0...0>, clear the discarded mass, the tape and the queue. */
+int lr_reset(lr_handle h);
+
+/* Queue gate G on nq (1 or 2) qubits, Eq. (3). U is 2^nq x 2^nq complex.
+ * dU (nullable) is dG/dtheta for parameter param_id (>= 0 makes the gate
+ * differentiable; -1 = fixed). */
+int lr_apply_gate(lr_handle h, int nq, const int* qubits, const double* U,
+                  const double* dU, int param_id);
+
+/* Queue R_axis(theta) = exp(-i theta sigma_axis / 2) on qubit q; axis 0/1/2 =
+ * X/Y/Z. The derivative is built natively. */
+int lr_apply_rotation(lr_handle h, int axis, int q, double theta, int param_id);
+
+/* Queue a one-qubit channel: K (1..4) Kraus matrices Kt_a (2x2 complex each,
+ * probability folded in), Eq. (4). Completeness is checked (LR_EKRAUS). */
+int lr_apply_kraus(lr_handle h, int q, int K, const double* kraus);
+
+/* Kraus sets of the paper's channels with the probability folded in, written
+ * as K x (2x2 complex) into out (room for 4 matrices, 32 doubles); *K_out
+ * receives K. kind: LR_DEPOLARIZING (Sec. III.A.1: {sqrt(1-p) I, sqrt(p/3) X,
+ * sqrt(p/3) Y, sqrt(p/3) Z}), LR_AMPLITUDE_DAMPING (Sec. III.A.3, p = gamma:
+ * E0 = [[1,0],[0,sqrt(1-g)]], E1 = [[0,sqrt(g)],[0,0]]), LR_BIT_FLIP
+ * (Sec. III.A.3: {sqrt(1-p) I, sqrt(p) X}). p must lie in [0, 1]. */
+#define LR_DEPOLARIZING 0
+#define LR_AMPLITUDE_DAMPING 1
+#define LR_BIT_FLIP 2
+int lr_kraus_preset(int kind, double p, double* out, int* K_out);
+
+/* Run queued work, then truncate to the leading eigenvectors of V V^dag via
+ * the Gram matrix (Sec. II.B, Theorem 1). r > 0 keeps min(r, columns); r <= 0
+ * uses the threshold set by lr_set_eps if one is set, else the rank of
+ * lr_init. discarded_out (nullable) receives the discarded eigenvalue mass of
+ * this truncation (synchronises). */
+int lr_compress(lr_handle h, int r, double* discarded_out);
+
+/* Threshold rule of Sec. II.B: keep the smallest k with
+ * sum_{i<=k} lambda_i >= (1 - eps) * sum_i lambda_i. eps <= 0 disables it. */
+int lr_set_eps(lr_handle h, double eps);
+
+/* Prob(x) = sum_v |V_xv|^2 (Eq. 9) into a caller-owned device buffer of 2^n
+ * floats (LR_C64) or doubles (LR_C128). Asynchronous. */
+int lr_probs(lr_handle h, void* out_dev);
+
+/* <H> = sum_t coeff_t Tr(V^dag P_t V) (Sec. II.D) for T Pauli strings.
+ * out_host receives one double. Synchronises. */
+int lr_expect(lr_handle h, int T, const uint64_t* xmask, const uint64_t* zmask,
+              const double* coeff, double* out_host);
+
+/* <Z_q> for every qubit and the trace, into out_host[0..n] (n + 1 doubles,
+ * the trace last). Synchronises. */
+int lr_z_expect(lr_handle h, double* out_host);
+
+/* Record the tape (gates, channels, truncation eigenvectors and eigenvalues,
+ * state checkpoints) needed by lr_backward. Off by default. */
+int lr_set_record(lr_handle h, int on);
+
+/* Keep a state checkpoint every `every` recorded stages (a stage is one
+ * expansion or one truncation); 0 = only the initial state. The backward pass
+ * recomputes the states in between from the stored eigenvectors. */
+int lr_set_checkpoint(lr_handle h, int every);
+
+/* Gradient of <H> = sum_t coeff_t <P_t> with respect to every parameter id
+ * used in the recorded circuit: adjoint pass through truncations, channels
+ * and gates. grad_out_host has nparams doubles (ids >= nparams are an error).
+ * Synchronises. */
+int lr_backward(lr_handle h, int T, const uint64_t* xmask, const uint64_t* zmask,
+                const double* coeff, int nparams, double* grad_out_host);
+
+typedef struct lr_info {
+  int n;               /* qubits */
+  int columns;         /* current column count c of V (queued work flushed) */
+  int capacity;        /* allocated columns */
+  int dtype;
+  int64_t compressions;/* truncations performed */
+  int64_t stages;      /* recorded stages */
+  double discarded;    /* cumulative discarded eigenvalue mass (FP64) */
+  double last_gap;     /* (lambda_k - lambda_{k+1}) / lambda_1 at the last cut */
+} lr_info;
+
+/* Flush queued work and report the state. Synchronises. */
+int lr_get_info(lr_handle h, lr_info* info);
+
+/* Copy V (2^n x c, row-major, interleaved complex in the handle's precision)
+ * into a caller-owned host buffer of 2^n * c complex elements. Flushes
+ * queued work and synchronises. */
+int lr_get_state(lr_handle h, void* out_host);
+
+/* Upper bound on the device bytes the handle holds (for capacity planning). */
+int64_t lr_device_bytes(lr_handle h);
+
+/* Kernel classes for lr_kernel_times. */
+#define LR_K_EXPAND 0   /* gate + Kraus expansion (Eqs. 3-4) */
+#define LR_K_GRAM 1     /* Gram matrix V'^dag V' */
+#define LR_K_EIGH 2     /* Hermitian eigensolve + rank choice */
+#define LR_K_PROJECT 3  /* V <- V' U_r */
+#define LR_K_READOUT 4  /* Prob(x) */
+#define LR_K_PAULI 5    /* Pauli expectations */
+#define LR_NKCLASS 8
+
+/* Bracket every forward kernel launch with CUDA events on the handle's stream
+ * (on = 1) or stop (on = 0). Adds a small per-launch cost; for measurement. */
+int lr_set_timing(lr_handle h, int on);
+
+/* Device time (ms) and launch count per kernel class since the last call;
+ * ms_out and counts_out have LR_NKCLASS entries. Synchronises and resets. */
+int lr_kernel_times(lr_handle h, double* ms_out, int64_t* counts_out);
+
+const char* lr_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRET_H */

@@ -1,0 +1,300 @@
+// Dense contractions of the truncation step (Sec. II.B, Theorem 1):
+//   * Gram      G = X^dag X over the 2^n rows (split over row chunks; chunk
+//                partials summed in FP64 in a fixed order -> deterministic);
+//   * rowmat    Y = X M (project onto the kept eigenvectors, V <- V' U_r);
+//   * the small FP64 matrices of the truncation adjoint.
+// SIMT tiles: 64 x 64 complex outputs per 256-thread block, 4 x 4 per thread,
+// operands staged through shared memory 16 rows/columns at a time.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lret {
+
+constexpr int TILE = 64;
+constexpr int KSTEP = 16;
+
+// FP32 products are accumulated in FP32 over FLUSH rows, then added into FP64
+// registers, so the chunk sum carries FP64 rounding beyond 128-term runs.
+template <typename T> struct Flush { static constexpr int rows = 128; };
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram(const cx<T>* __restrict__ A, int lda, int ma,
+                                              const cx<T>* __restrict__ B, int ldb, int mb, int64_t N,
+                                              int64_t chunk, int tiles_j, int hermitian,
+                                              double2* __restrict__ partials) {
+  __shared__ cx<T> As[KSTEP][TILE];
+  __shared__ cx<T> Bs[KSTEP][TILE];
+  int ti, tj;
+  if (hermitian) {
+    // linear index over the upper triangle of tiles (ti <= tj)
+    int lin = blockIdx.x, row = 0, cnt = tiles_j;
+    while (lin >= cnt) { lin -= cnt; ++row; --cnt; }
+    ti = row; tj = row + lin;
+  } else {
+    ti = blockIdx.x / tiles_j; tj = blockIdx.x % tiles_j;
+  }
+  const int split = blockIdx.y;
+  const int64_t x0 = (int64_t)split * chunk;
+  int64_t x1 = x0 + chunk; if (x1 > N) x1 = N;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cx<T> acc[4][4];
+  double2 dacc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { acc[a][b] = mk<T>(0, 0); dacc[a][b] = make_double2(0, 0); }
+  int since_flush = 0;
+  for (int64_t xb = x0; xb < x1; xb += KSTEP) {
+    // stage KSTEP rows x TILE columns of each operand
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int idx = threadIdx.x + l * 256;
+      const int rr = idx / TILE, cc = idx % TILE;
+      const int64_t x = xb + rr;
+      const int ia = ti * TILE + cc, ib = tj * TILE + cc;
+      As[rr][cc] = (x < x1 && ia < ma) ? A[x * lda + ia] : mk<T>(0, 0);
+      Bs[rr][cc] = (x < x1 && ib < mb) ? B[x * ldb + ib] : mk<T>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KSTEP; ++kk) {
+      cx<T> av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) cfmac(acc[a][b], av[a], bv[b]);
+    }
+    __syncthreads();
+    since_flush += KSTEP;
+    if (since_flush >= Flush<T>::rows) {
+      since_flush = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          dacc[a][b].x += (double)acc[a][b].x;
+          dacc[a][b].y += (double)acc[a][b].y;
+          acc[a][b] = mk<T>(0, 0);
+        }
+    }
+  }
+  double2* P = partials + (int64_t)split * ma * mb;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ti * TILE + ty + 16 * a, j = tj * TILE + tx + 16 * b;
+      if (i < ma && j < mb)
+        P[(int64_t)i * mb + j] = make_double2(dacc[a][b].x + (double)acc[a][b].x,
+                                              dacc[a][b].y + (double)acc[a][b].y);
+    }
+}
+
+// out[i][j] = sum_s partials[s][i][j] in split order; Hermitian: fill the lower
+// triangle from the upper one and make the diagonal exactly real.
+__global__ void k_gram_reduce(const double2* __restrict__ partials, int splits, int ma, int mb,
+                              int hermitian, double2* __restrict__ out) {
+  const int64_t total = (int64_t)ma * mb;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / mb), j = (int)(e % mb);
+    if (hermitian && (i / TILE) > (j / TILE)) continue;  // tile not computed
+    double sr = 0.0, si = 0.0;
+    for (int s = 0; s < splits; ++s) {
+      const double2 v = partials[(int64_t)s * total + e];
+      sr += v.x; si += v.y;
+    }
+    if (hermitian) {
+      if (i == j) {
+        out[e] = make_double2(sr, 0.0);
+      } else if (i < j) {
+        out[e] = make_double2(sr, si);
+        out[(int64_t)j * mb + i] = make_double2(sr, -si);
+      } else {
+        // same tile row/col block, below the diagonal: the (j, i) element of this
+        // tile is the one kept; this thread's value is its conjugate partner.
+        // Skip: the i < j thread writes both.
+      }
+    } else {
+      out[e] = make_double2(sr, si);
+    }
+  }
+}
+
+int gram_splits(int64_t N, int ma, int mb) {
+  const int ti = (ma + TILE - 1) / TILE, tj = (mb + TILE - 1) / TILE;
+  const int tiles = ti * tj;
+  int splits = (int)((4 * 152 + tiles - 1) / tiles);
+  const int64_t max_by_rows = (N + 255) / 256;  // at least 256 rows per chunk
+  if (splits > max_by_rows) splits = (int)max_by_rows;
+  if (splits > 1024) splits = 1024;
+  if (splits < 1) splits = 1;
+  return splits;
+}
+
+template <typename T>
+cudaError_t launch_gram(const void* A, int lda, int ma, const void* B, int ldb, int mb, int64_t N,
+                        bool hermitian, double2* partials, int splits, double2* out, cudaStream_t s) {
+  const int ti = (ma + TILE - 1) / TILE, tj = (mb + TILE - 1) / TILE;
+  const int tiles = hermitian ? ti * (ti + 1) / 2 : ti * tj;
+  int64_t chunk = (N + splits - 1) / splits;
+  chunk = ((chunk + KSTEP - 1) / KSTEP) * KSTEP;
+  dim3 grid(tiles, splits);
+  k_gram<T><<<grid, 256, 0, s>>>((const cx<T>*)A, lda, ma, (const cx<T>*)B, ldb, mb, N, chunk, tj,
+                                 hermitian ? 1 : 0, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t total = (int64_t)ma * mb;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_gram_reduce<<<blocks, 256, 0, s>>>(partials, splits, ma, mb, hermitian ? 1 : 0, out);
+  return cudaGetLastError();
+}
+
+// Y[x][j] = sum_i A1[x][i] M1[i][j] + sum_i A2[x][i] M2[i][j]
+template <typename T>
+__global__ void __launch_bounds__(256) k_rowmat(const cx<T>* __restrict__ A1, int lda1, int k1,
+                                                const double2* __restrict__ M1, int ldm1,
+                                                const cx<T>* __restrict__ A2, int lda2, int k2,
+                                                const double2* __restrict__ M2, int ldm2,
+                                                cx<T>* __restrict__ Y, int ldy, int p, int64_t N) {
+  __shared__ cx<T> As[TILE][KSTEP + 1];
+  __shared__ cx<T> Ms[KSTEP][TILE];
+  const int64_t xbase = (int64_t)blockIdx.x * TILE;
+  const int jbase = blockIdx.y * TILE;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cx<T> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = mk<T>(0, 0);
+  for (int src = 0; src < 2; ++src) {
+    const cx<T>* A = src == 0 ? A1 : A2;
+    const double2* M = src == 0 ? M1 : M2;
+    const int lda = src == 0 ? lda1 : lda2, kk_n = src == 0 ? k1 : k2, ldm = src == 0 ? ldm1 : ldm2;
+    if (A == nullptr || kk_n <= 0) continue;
+    for (int ib = 0; ib < kk_n; ib += KSTEP) {
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int idx = threadIdx.x + l * 256;
+        // A tile: TILE rows x KSTEP cols
+        const int rr = idx / KSTEP, cc = idx % KSTEP;
+        const int64_t x = xbase + rr;
+        const int i = ib + cc;
+        As[rr][cc] = (x < N && i < kk_n) ? A[x * lda + i] : mk<T>(0, 0);
+        // M tile: KSTEP rows x TILE cols
+        const int mr = idx / TILE, mc = idx % TILE;
+        const int mi = ib + mr, mj = jbase + mc;
+        Ms[mr][mc] = (mi < kk_n && mj < p) ? from_d2<T>(M[(int64_t)mi * ldm + mj]) : mk<T>(0, 0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < KSTEP; ++kk) {
+        cx<T> av[4], mv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[ty + 16 * a][kk];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) mv[b] = Ms[kk][tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], mv[b]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t x = xbase + ty + 16 * a;
+      const int j = jbase + tx + 16 * b;
+      if (x < N && j < p) Y[x * ldy + j] = acc[a][b];
+    }
+}
+
+template <typename T>
+cudaError_t launch_rowmat(const void* A1, int lda1, int k1, const double2* M1, int ldm1,
+                          const void* A2, int lda2, int k2, const double2* M2, int ldm2,
+                          void* Y, int ldy, int p, int64_t N, cudaStream_t s) {
+  if (N == 0 || p == 0) return cudaSuccess;
+  dim3 grid((unsigned)((N + TILE - 1) / TILE), (unsigned)((p + TILE - 1) / TILE));
+  k_rowmat<T><<<grid, 256, 0, s>>>((const cx<T>*)A1, lda1, k1, M1, ldm1, (const cx<T>*)A2, lda2, k2, M2,
+                                   ldm2, (cx<T>*)Y, ldy, p, N);
+  return cudaGetLastError();
+}
+
+// ---- truncation adjoint, small FP64 matrices (m <= 256) ----------------------
+// FA[j][i] = F(lam_i - lam_{k+j}) * sum_l conj(U[l][k+j]) C[l][i]   (j < m-k, i < k)
+__global__ void k_tadj_fa(const double2* __restrict__ C, const double2* __restrict__ U,
+                          const double* __restrict__ lam, int m, int k, double2* __restrict__ FA) {
+  const int d = m - k;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d * k) return;
+  const int j = e / k, i = e % k;
+  double2 acc = make_double2(0, 0);
+  for (int l = 0; l < m; ++l) cfmac(acc, U[(int64_t)l * m + k + j], C[(int64_t)l * k + i]);
+  const double l1 = fabs(lam[0]) > 0 ? fabs(lam[0]) : 1.0;
+  const double delta = lam[i] - lam[k + j];
+  const double eta = 1e-12 * l1;
+  const double f = delta / (delta * delta + eta * eta);  // 1/delta, regularised at ties
+  FA[e] = make_double2(acc.x * f, acc.y * f);
+}
+
+// T1[a][i] = sum_j U[a][k+j] FA[j][i]   (a < m, i < k)
+__global__ void k_tadj_t1(const double2* __restrict__ U, const double2* __restrict__ FA, int m, int k,
+                          double2* __restrict__ T1) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * k) return;
+  const int a = e / k, i = e % k;
+  double2 acc = make_double2(0, 0);
+  for (int j = 0; j < m - k; ++j) cfma(acc, U[(int64_t)a * m + k + j], FA[(int64_t)j * k + i]);
+  T1[e] = acc;
+}
+
+// B[a][b] = sum_i T1[a][i] conj(U[b][i]);  Mcat[k + a][b] = B[a][b] + conj(B[b][a]);
+// Mcat[i][b] = conj(U[b][i]) for i < k.
+__global__ void k_tadj_mcat(const double2* __restrict__ T1, const double2* __restrict__ U, int m, int k,
+                            double2* __restrict__ Mcat) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < k * m) {
+    const int i = e / m, b = e % m;
+    Mcat[e] = conjg(U[(int64_t)b * m + i]);
+  }
+  if (e >= m * m) return;
+  const int a = e / m, b = e % m;
+  double2 bab = make_double2(0, 0), bba = make_double2(0, 0);
+  for (int i = 0; i < k; ++i) {
+    cfma(bab, T1[(int64_t)a * k + i], conjg(U[(int64_t)b * m + i]));
+    cfma(bba, T1[(int64_t)b * k + i], conjg(U[(int64_t)a * m + i]));
+  }
+  Mcat[(int64_t)(k + a) * m + b] = cadd(bab, conjg(bba));
+}
+
+cudaError_t launch_trunc_adj_small(const double2* C, const double2* U, const double* lam, int m, int k,
+                                   double2* FA, double2* T1, double2* Mcat, cudaStream_t s) {
+  const int d = m - k;
+  if (d > 0) {
+    k_tadj_fa<<<(d * k + 127) / 128, 128, 0, s>>>(C, U, lam, m, k, FA);
+    k_tadj_t1<<<(m * k + 127) / 128, 128, 0, s>>>(U, FA, m, k, T1);
+  } else {
+    cudaMemsetAsync(T1, 0, sizeof(double2) * (size_t)m * k, s);
+  }
+  k_tadj_mcat<<<(m * m + 127) / 128, 128, 0, s>>>(T1, U, m, k, Mcat);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gram<float>(const void*, int, int, const void*, int, int, int64_t, bool, double2*,
+                                        int, double2*, cudaStream_t);
+template cudaError_t launch_gram<double>(const void*, int, int, const void*, int, int, int64_t, bool, double2*,
+                                         int, double2*, cudaStream_t);
+template cudaError_t launch_rowmat<float>(const void*, int, int, const double2*, int, const void*, int, int,
+                                          const double2*, int, void*, int, int, int64_t, cudaStream_t);
+template cudaError_t launch_rowmat<double>(const void*, int, int, const double2*, int, const void*, int, int,
+                                           const double2*, int, void*, int, int, int64_t, cudaStream_t);
+
+}  // namespace lret

@@ -1,0 +1,94 @@
+// Internal launch interface between the host runtime (runtime.cu) and the
+// kernels. Not part of the public C ABI (include/lret.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lret {
+
+// A row-group operator: G = 2 (one qubit) or 4 (two qubits) rows of V are
+// mixed by K matrices M[alpha] (G x G). The matrix index of a row is
+// 2*b(bits[0]) + b(bits[1]) for G = 4 and b(bits[0]) for G = 2.
+struct GroupOp {
+  int G;
+  int bits[2];
+  int K;
+  double2 M[4][4][4];   // M[alpha][a][g]
+  double2 dM[4][4][4];  // derivative blocks for the adjoint (same layout)
+  int has_grad;
+};
+
+// Result block written by the eigensolver (device memory).
+struct EigOut {
+  int k;            // kept columns
+  int sweeps;       // Jacobi sweeps used
+  int status;       // 0 = converged, 1 = sweep limit
+  int pad;
+  double dropped;   // sum of discarded eigenvalues (clamped at 0), FP64
+  double kept;      // sum of kept eigenvalues, FP64
+  double gap;       // (lambda_k - lambda_{k+1}) / lambda_1, inf if nothing dropped
+  double trace;     // trace of the Gram matrix (FP64 sum of its diagonal)
+};
+
+// ---- expansion (Eqs. 3-4): W[x_a][alpha*c + j] = sum_g M[alpha][a][g] V[x_g][j]
+template <typename T>
+cudaError_t launch_expand(const void* V, void* W, int64_t N, int c, int ld, const GroupOp& op,
+                          cudaStream_t s);
+
+// ---- adjoint of the expansion: Vbar[x_g][j] = sum_{alpha,a} conj(M[alpha][a][g]) Wbar[x_a][alpha c + j]
+// and grad_partials[block] = 2 Re sum conj(Wbar) (dM V). Returns the grid size used.
+template <typename T>
+cudaError_t launch_expand_adj(const void* Wbar, const void* Vin, void* Vbar, int64_t N, int c, int ld,
+                              const GroupOp& op, double* grad_partials, int* nblocks_out,
+                              cudaStream_t s);
+
+// ---- out = sum_t coeff_t P_t V (Pauli sum applied to the rows of V)
+template <typename T>
+cudaError_t launch_pauli_apply(const void* V, void* out, int64_t N, int c, int ld, int T_terms,
+                               const uint64_t* xm, const uint64_t* zm, const double* coeff,
+                               cudaStream_t s);
+
+// ---- Gram: out[i][j] = sum_x conj(A[x][i]) B[x][j], FP64 result (ma x mb, row-major).
+// partials: workspace of splits * ma * mb double2. hermitian => A == B, ma == mb.
+template <typename T>
+cudaError_t launch_gram(const void* A, int lda, int ma, const void* B, int ldb, int mb, int64_t N,
+                        bool hermitian, double2* partials, int splits, double2* out, cudaStream_t s);
+int gram_splits(int64_t N, int ma, int mb);
+
+// ---- Y[x][j] = sum_i A1[x][i] M1[i][j] + sum_i A2[x][i] M2[i][j]  (j < p)
+// M1, M2: complex128 device matrices with leading dimensions ldm1, ldm2. A2 may be null.
+template <typename T>
+cudaError_t launch_rowmat(const void* A1, int lda1, int k1, const double2* M1, int ldm1,
+                          const void* A2, int lda2, int k2, const double2* M2, int ldm2,
+                          void* Y, int ldy, int p, int64_t N, cudaStream_t s);
+
+// ---- Hermitian eigensolver (Jacobi, arithmetic in T): evals descending, evecs
+// columns in the same order (m x m complex128, row-major), rank choice and FP64
+// accounting into *out. r > 0: k = min(r, m); else threshold eps.
+template <typename T>
+cudaError_t launch_eigh(const double2* G, int m, void* work, double* evals, double2* evecs,
+                        EigOut* out, int r, double eps, cudaStream_t s);
+size_t eigh_work_bytes(int m, bool fp64);
+
+// ---- adjoint of a truncation: builds Mcat ((k+m) x m complex128) =
+// [U_r^dag ; B + B^dag] with B = U_d (F o (U_d^dag C)) U_r^dag, F_ji = 1/(lam_i - lam_j).
+cudaError_t launch_trunc_adj_small(const double2* C, const double2* U, const double* lam, int m,
+                                   int k, double2* FA, double2* T1, double2* Mcat, cudaStream_t s);
+
+// ---- readouts
+template <typename T>
+cudaError_t launch_probs(const void* V, int64_t N, int c, int ld, void* out, cudaStream_t s);
+// out[0..n-1] = <Z_q>, out[n] = trace; partials: workspace of (n+1) * 1024 doubles
+template <typename T>
+cudaError_t launch_zexp(const void* V, int64_t N, int c, int ld, int n, double* partials,
+                        double* out, cudaStream_t s);
+// out[t] = Re Tr(V^dag P_t V); partials: workspace of T * 1024 doubles
+template <typename T>
+cudaError_t launch_pauli_expect(const void* V, int64_t N, int c, int ld, int T_terms,
+                                const uint64_t* xm, const uint64_t* zm, double* partials,
+                                double* out, cudaStream_t s);
+
+// out[0] = sum of in[0..count-1] in index order (deterministic), optionally scaled/accumulated.
+cudaError_t launch_sum(const double* in, int count, double* out, int accumulate, cudaStream_t s);
+
+}  // namespace lret

@@ -1,0 +1,152 @@
+// Readouts without forming rho (Sec. II.D):
+//   Prob(x) = sum_v |V_xv|^2                         (Eq. 9)
+//   <Z_q> = sum_x Prob(x) (-1)^{x_q},  Tr rho = sum_x Prob(x)
+//   <P> = Tr(V^dag P V) = sum_x sum_v conj(V[x ^ xm][v]) i^{#Y} (-1)^{pop(x & zm)} V[x][v]
+// One warp per row: lanes stride over the row's columns (coalesced), a shuffle
+// reduction gives the row value, and per-block partial sums are combined in a
+// fixed order in FP64 (deterministic).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lret {
+
+constexpr int RO_THREADS = 256;
+constexpr int RO_WARPS = RO_THREADS / 32;
+constexpr int RO_MAX_BLOCKS = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(RO_THREADS) k_probs(const cx<T>* __restrict__ V, int64_t N, int c, int ld,
+                                                      T* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t x = wid; x < N; x += nw) {
+    T acc = 0;
+    for (int j = lane; j < c; j += 32) {
+      const cx<T> v = V[x * ld + j];
+      acc += v.x * v.x + v.y * v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[x] = acc;
+  }
+}
+
+// lane l < n accumulates sum_x p(x) (1 - 2 x_l); lane n accumulates the trace.
+template <typename T>
+__global__ void __launch_bounds__(RO_THREADS) k_zexp(const cx<T>* __restrict__ V, int64_t N, int c, int ld,
+                                                     int n, double* __restrict__ partials) {
+  __shared__ double red[RO_WARPS][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double mine = 0.0;
+  for (int64_t x = wid; x < N; x += nw) {
+    double acc = 0.0;
+    for (int j = lane; j < c; j += 32) {
+      const cx<T> v = V[x * ld + j];
+      acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane < n) mine += ((x >> lane) & 1) ? -acc : acc;
+    else if (lane == n) mine += acc;
+  }
+  red[warp][lane] = mine;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int w = 0; w < RO_WARPS; ++w) s += red[w][threadIdx.x];
+    partials[(int64_t)blockIdx.x * 32 + threadIdx.x] = s;
+  }
+}
+
+// out[q] = sum_b partials[q * qstride + b * bstride] in block order
+__global__ void k_colsum(const double* __restrict__ partials, int nblocks, int qstride, int bstride,
+                         int count, double* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)q * qstride + (int64_t)b * bstride];
+  out[q] = s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RO_THREADS) k_pauli_expect(const cx<T>* __restrict__ V, int64_t N, int c,
+                                                             int ld, const uint64_t* __restrict__ xmv,
+                                                             const uint64_t* __restrict__ zmv,
+                                                             double* __restrict__ partials) {
+  __shared__ double red[32];
+  const int t = blockIdx.y;
+  const uint64_t xm = xmv[t], zm = zmv[t];
+  const int ny = __popcll(xm & zm) & 3;
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double mine = 0.0;
+  for (int64_t x = wid; x < N; x += nw) {
+    const uint64_t y = (uint64_t)x ^ xm;
+    double sr = 0.0, si = 0.0;
+    for (int j = lane; j < c; j += 32) {
+      const cx<T> a = V[y * ld + j], b = V[x * ld + j];
+      // conj(a) * b
+      sr += (double)a.x * b.x + (double)a.y * b.y;
+      si += (double)a.x * b.y - (double)a.y * b.x;
+    }
+    // Re(i^ny * S)
+    double re;
+    switch (ny) {
+      case 0: re = sr; break;
+      case 1: re = -si; break;
+      case 2: re = -sr; break;
+      default: re = si; break;
+    }
+    if (__popcll((uint64_t)x & zm) & 1) re = -re;
+    mine += re;
+  }
+  const double tot = block_sum(mine, red);
+  if (threadIdx.x == 0) partials[(int64_t)t * gridDim.x + blockIdx.x] = tot;
+}
+
+static int ro_blocks(int64_t N) {
+  int64_t b = (N + RO_WARPS - 1) / RO_WARPS;
+  if (b > RO_MAX_BLOCKS) b = RO_MAX_BLOCKS;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename T>
+cudaError_t launch_probs(const void* V, int64_t N, int c, int ld, void* out, cudaStream_t s) {
+  k_probs<T><<<ro_blocks(N), RO_THREADS, 0, s>>>((const cx<T>*)V, N, c, ld, (T*)out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zexp(const void* V, int64_t N, int c, int ld, int n, double* partials, double* out,
+                        cudaStream_t s) {
+  const int nb = ro_blocks(N);
+  k_zexp<T><<<nb, RO_THREADS, 0, s>>>((const cx<T>*)V, N, c, ld, n, partials);
+  k_colsum<<<1, 32, 0, s>>>(partials, nb, 1, 32, n + 1, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pauli_expect(const void* V, int64_t N, int c, int ld, int T_terms, const uint64_t* xm,
+                                const uint64_t* zm, double* partials, double* out, cudaStream_t s) {
+  if (T_terms <= 0) return cudaSuccess;
+  const int nb = ro_blocks(N);
+  dim3 grid(nb, T_terms);
+  k_pauli_expect<T><<<grid, RO_THREADS, 0, s>>>((const cx<T>*)V, N, c, ld, xm, zm, partials);
+  // out[t] = sum_b partials[t * nb + b]
+  k_colsum<<<(T_terms + 127) / 128, 128, 0, s>>>(partials, nb, nb, 1, T_terms, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_probs<float>(const void*, int64_t, int, int, void*, cudaStream_t);
+template cudaError_t launch_probs<double>(const void*, int64_t, int, int, void*, cudaStream_t);
+template cudaError_t launch_zexp<float>(const void*, int64_t, int, int, int, double*, double*, cudaStream_t);
+template cudaError_t launch_zexp<double>(const void*, int64_t, int, int, int, double*, double*, cudaStream_t);
+template cudaError_t launch_pauli_expect<float>(const void*, int64_t, int, int, int, const uint64_t*,
+                                                const uint64_t*, double*, double*, cudaStream_t);
+template cudaError_t launch_pauli_expect<double>(const void*, int64_t, int, int, int, const uint64_t*,
+                                                 const uint64_t*, double*, double*, cudaStream_t);
+
+}  // namespace lret

@@ -1,0 +1,913 @@
+// liblret host runtime: the C ABI of include/lret.h.
+//
+// A handle owns two N x cap slabs (V and the expansion target W, N = 2^n),
+// the Gram / eigensolver workspaces and, when recording, the tape used by the
+// adjoint pass. Gates and channels are queued and fused into one expansion
+// kernel (Eqs. 3-4); a truncation (Sec. II.B) runs Gram -> eigensolve ->
+// projection on the handle's stream without a host round trip unless the
+// caller asks for a value.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+#include "lret.h"
+
+using namespace lret;
+using zc = std::complex<double>;
+
+namespace {
+
+thread_local char g_errmsg[256];
+
+struct Stage {
+  int type = 0;  // 0 = expansion, 1 = truncation
+  int c_in = 0, c_out = 0;
+  GroupOp op{};
+  int param_id = -1;
+  int m = 0, k = 0;
+  double2* U = nullptr;  // m x m eigenvectors (columns, descending)
+  double* lam = nullptr; // m eigenvalues
+  void* ckpt = nullptr;  // stage input snapshot (N x cap) or null
+};
+
+}  // namespace
+
+struct lr_ctx {
+  int n = 0;
+  int64_t N = 0;
+  int r = 0, dtype = 0, cap = 0;
+  cudaStream_t stream = nullptr;
+  size_t esz = 0;
+  void* V = nullptr;
+  void* W = nullptr;
+  int c = 1;
+  // queue
+  bool has_gate = false;
+  int gate_nq = 0, gate_q[2] = {0, 0}, gate_pid = -1;
+  zc gate_U[16], gate_dU[16];
+  bool gate_has_d = false;
+  bool has_chan = false;
+  int chan_q = 0, chan_K = 0;
+  zc chan_M[4][4];
+  double eps = 0.0;
+  // workspaces
+  double2* partials = nullptr;
+  size_t partials_elems = 0;
+  double2* G = nullptr;
+  double* evals = nullptr;
+  double2* evecs = nullptr;
+  EigOut* eo = nullptr;
+  void* eig_work = nullptr;
+  double* acc = nullptr;       // [0] cumulative discarded, [1] last gap, [2] eig status, [3] compressions
+  double* dscratch = nullptr;  // readout partials / small outputs
+  size_t dscratch_elems = 0;
+  uint64_t* d_xm = nullptr;
+  uint64_t* d_zm = nullptr;
+  double* d_coeff = nullptr;
+  int masks_cap = 0;
+  EigOut* h_eo = nullptr;  // pinned
+  double* h_small = nullptr;  // pinned, 64 doubles
+  int64_t ncomp = 0;
+  // tape
+  bool record = false;
+  int ckpt_every = 0;
+  std::vector<Stage> tape;
+  // backward scratch
+  void* vb[2] = {nullptr, nullptr};
+  std::vector<void*> seg;
+  double2 *bC = nullptr, *bFA = nullptr, *bT1 = nullptr, *bMcat = nullptr;
+  double* bgrad = nullptr;
+  int bgrad_cap = 0;
+  double* bpart = nullptr;
+  size_t bytes = 0;
+  // per-kernel-class CUDA-event timing (lr_set_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<std::pair<int, int>> ev_pending;  // (class, index of start event)
+  int ev_next = 0;
+  double kms[LR_NKCLASS] = {0};
+  int64_t kcnt[LR_NKCLASS] = {0};
+};
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t _e = (call);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      snprintf(g_errmsg, sizeof(g_errmsg), "%s: %s", #call, cudaGetErrorString(_e));   \
+      return LR_ECUDA;                                                                 \
+    }                                                                                  \
+  } while (0)
+
+namespace {
+
+template <typename F>
+cudaError_t by_dtype(int dtype, F f) {
+  if (dtype == LR_C64) return f(float());
+  return f(double());
+}
+
+int dmalloc(lr_ctx* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    snprintf(g_errmsg, sizeof(g_errmsg), "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LR_ENOMEM : LR_ECUDA;
+  }
+  h->bytes += bytes;
+  return LR_OK;
+}
+
+void dfree(void*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+size_t slab_bytes(const lr_ctx* h) { return (size_t)h->N * h->cap * h->esz; }
+
+void timer_drain(lr_ctx* h) {
+  if (h->ev_pending.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& pr : h->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[pr.second], h->ev[pr.second + 1]) == cudaSuccess) {
+      h->kms[pr.first] += ms;
+      h->kcnt[pr.first] += 1;
+    }
+  }
+  h->ev_pending.clear();
+  h->ev_next = 0;
+}
+
+// Returns the start-event index, or -1 when timing is off.
+int tbeg(lr_ctx* h) {
+  if (!h->timing) return -1;
+  if (h->ev_next + 2 > (int)h->ev.size()) timer_drain(h);
+  const int i = h->ev_next;
+  h->ev_next += 2;
+  cudaEventRecord(h->ev[i], h->stream);
+  return i;
+}
+
+void tend(lr_ctx* h, int cls, int i) {
+  if (i < 0) return;
+  cudaEventRecord(h->ev[i + 1], h->stream);
+  h->ev_pending.push_back({cls, i});
+}
+
+int check_unitary_like(const zc* U, int d) {
+  for (int i = 0; i < d * d; ++i)
+    if (!std::isfinite(U[i].real()) || !std::isfinite(U[i].imag())) return LR_EINVAL;
+  return LR_OK;
+}
+
+// embed a one-qubit matrix K into the 4x4 basis (2*b(q0) + b(q1)); which = 0 -> acts on q0
+void embed2(const zc K[4], int which, zc out[16]) {
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      const int a0 = a >> 1, a1 = a & 1, b0 = b >> 1, b1 = b & 1;
+      zc v = 0;
+      if (which == 0) v = (a1 == b1) ? K[a0 * 2 + b0] : zc(0);
+      else v = (a0 == b0) ? K[a1 * 2 + b1] : zc(0);
+      out[a * 4 + b] = v;
+    }
+}
+
+void matmul(const zc* A, const zc* B, zc* C, int d) {
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      zc s = 0;
+      for (int l = 0; l < d; ++l) s += A[i * d + l] * B[l * d + j];
+      C[i * d + j] = s;
+    }
+}
+
+void put(double2& dst, zc v) { dst = make_double2(v.real(), v.imag()); }
+
+// Build the group operator for the queued gate and/or channel.
+void build_op(const lr_ctx* h, bool use_gate, bool use_chan, GroupOp* op, int* pid) {
+  memset(op, 0, sizeof(GroupOp));
+  *pid = -1;
+  const bool grad = use_gate && h->gate_has_d && h->gate_pid >= 0;
+  if (use_gate) {
+    const int d = 1 << h->gate_nq;
+    op->G = d;
+    op->bits[0] = h->gate_q[0];
+    op->bits[1] = h->gate_nq == 2 ? h->gate_q[1] : 0;
+    if (use_chan) {
+      op->K = h->chan_K;
+      for (int al = 0; al < h->chan_K; ++al) {
+        zc Kfull[16], M[16], dM[16];
+        if (d == 2) {
+          for (int i = 0; i < 4; ++i) Kfull[i] = h->chan_M[al][i];
+        } else {
+          embed2(h->chan_M[al], h->chan_q == h->gate_q[0] ? 0 : 1, Kfull);
+        }
+        matmul(Kfull, h->gate_U, M, d);
+        if (grad) matmul(Kfull, h->gate_dU, dM, d);
+        for (int a = 0; a < d; ++a)
+          for (int g = 0; g < d; ++g) {
+            put(op->M[al][a][g], M[a * d + g]);
+            if (grad) put(op->dM[al][a][g], dM[a * d + g]);
+          }
+      }
+    } else {
+      op->K = 1;
+      for (int a = 0; a < d; ++a)
+        for (int g = 0; g < d; ++g) {
+          put(op->M[0][a][g], h->gate_U[a * d + g]);
+          if (grad) put(op->dM[0][a][g], h->gate_dU[a * d + g]);
+        }
+    }
+    if (grad) {
+      op->has_grad = 1;
+      *pid = h->gate_pid;
+    }
+  } else {
+    op->G = 2;
+    op->bits[0] = h->chan_q;
+    op->K = h->chan_K;
+    for (int al = 0; al < h->chan_K; ++al)
+      for (int a = 0; a < 2; ++a)
+        for (int g = 0; g < 2; ++g) put(op->M[al][a][g], h->chan_M[al][a * 2 + g]);
+  }
+}
+
+int snapshot(lr_ctx* h, Stage& st) {
+  const bool at_ckpt = h->tape.empty() || (h->ckpt_every > 0 && (h->tape.size() % h->ckpt_every) == 0);
+  if (!at_ckpt) return LR_OK;
+  int rc = dmalloc(h, &st.ckpt, slab_bytes(h));
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(st.ckpt, h->V, slab_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+  return LR_OK;
+}
+
+// Run one expansion stage V -> W, swap. Queue flags are cleared by the caller.
+int run_expand(lr_ctx* h, bool use_gate, bool use_chan) {
+  GroupOp op;
+  int pid;
+  build_op(h, use_gate, use_chan, &op, &pid);
+  const int c_out = h->c * op.K;
+  if (c_out > h->cap) {
+    snprintf(g_errmsg, sizeof(g_errmsg), "columns %d x %d exceed capacity %d", h->c, op.K, h->cap);
+    return LR_ECAPACITY;
+  }
+  Stage st;
+  if (h->record) {
+    st.type = 0;
+    st.c_in = h->c;
+    st.c_out = c_out;
+    st.op = op;
+    st.param_id = pid;
+    int rc = snapshot(h, st);
+    if (rc) return rc;
+  }
+  const int64_t N = h->N;
+  const int c = h->c, ld = h->cap;
+  const int te = tbeg(h);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_expand<decltype(t)>(h->V, h->W, N, c, ld, op, h->stream);
+  }));
+  tend(h, LR_K_EXPAND, te);
+  std::swap(h->V, h->W);
+  h->c = c_out;
+  if (h->record) h->tape.push_back(st);
+  return LR_OK;
+}
+
+int flush_gate(lr_ctx* h) {
+  if (!h->has_gate) return LR_OK;
+  int rc = run_expand(h, true, false);
+  if (rc) return rc;
+  h->has_gate = false;
+  return LR_OK;
+}
+
+int flush_all(lr_ctx* h) {
+  if (h->has_chan) {
+    int rc = run_expand(h, h->has_gate, true);
+    if (rc) return rc;
+    h->has_gate = false;
+    h->has_chan = false;
+    return LR_OK;
+  }
+  return flush_gate(h);
+}
+
+__global__ void k_accum(const EigOut* eo, double* acc) {
+  acc[0] += eo->dropped;
+  acc[1] = eo->gap;
+  if ((double)eo->status > acc[2]) acc[2] = (double)eo->status;
+  acc[3] += 1.0;
+}
+
+int ensure_masks(lr_ctx* h, int T) {
+  if (T <= h->masks_cap) return LR_OK;
+  dfree((void*&)h->d_xm);
+  dfree((void*&)h->d_zm);
+  dfree((void*&)h->d_coeff);
+  int cap = T < 64 ? 64 : T;
+  int rc = dmalloc(h, (void**)&h->d_xm, sizeof(uint64_t) * cap);
+  if (!rc) rc = dmalloc(h, (void**)&h->d_zm, sizeof(uint64_t) * cap);
+  if (!rc) rc = dmalloc(h, (void**)&h->d_coeff, sizeof(double) * cap);
+  if (rc) return rc;
+  h->masks_cap = cap;
+  return LR_OK;
+}
+
+int ensure_dscratch(lr_ctx* h, size_t elems) {
+  if (elems <= h->dscratch_elems) return LR_OK;
+  dfree((void*&)h->dscratch);
+  int rc = dmalloc(h, (void**)&h->dscratch, sizeof(double) * elems);
+  if (rc) return rc;
+  h->dscratch_elems = elems;
+  return LR_OK;
+}
+
+int upload_terms(lr_ctx* h, int T, const uint64_t* xm, const uint64_t* zm, const double* coeff) {
+  const uint64_t lim = (h->n >= 64) ? ~0ull : ((1ull << h->n) - 1ull);
+  for (int t = 0; t < T; ++t)
+    if ((xm[t] & ~lim) || (zm[t] & ~lim)) return LR_EINVAL;
+  int rc = ensure_masks(h, T);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h->d_xm, xm, sizeof(uint64_t) * T, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_zm, zm, sizeof(uint64_t) * T, cudaMemcpyHostToDevice, h->stream));
+  if (coeff) CK(cudaMemcpyAsync(h->d_coeff, coeff, sizeof(double) * T, cudaMemcpyHostToDevice, h->stream));
+  return LR_OK;
+}
+
+int do_truncate(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
+  const int m = h->c;
+  const int64_t N = h->N;
+  const int ld = h->cap;
+  if (r_eff > 0 && m <= r_eff) {  // nothing to drop: rho unchanged, skip
+    if (discarded_out) *discarded_out = 0.0;
+    return LR_OK;
+  }
+  if (m > 256) {
+    snprintf(g_errmsg, sizeof(g_errmsg), "truncation of %d columns exceeds the eigensolver limit 256", m);
+    return LR_ECAPACITY;
+  }
+  Stage st;
+  if (h->record) {
+    st.type = 1;
+    st.c_in = m;
+    st.m = m;
+    int rc = snapshot(h, st);
+    if (rc) return rc;
+  }
+  const int splits = gram_splits(N, m, m);
+  int te = tbeg(h);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_gram<decltype(t)>(h->V, ld, m, h->V, ld, m, N, true, h->partials, splits, h->G, h->stream);
+  }));
+  tend(h, LR_K_GRAM, te);
+  te = tbeg(h);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_eigh<decltype(t)>(h->G, m, h->eig_work, h->evals, h->evecs, h->eo, r_eff, eps, h->stream);
+  }));
+  tend(h, LR_K_EIGH, te);
+  k_accum<<<1, 1, 0, h->stream>>>(h->eo, h->acc);
+  CK(cudaGetLastError());
+  int k;
+  if (r_eff > 0) {
+    k = r_eff < m ? r_eff : m;
+  } else {
+    CK(cudaMemcpyAsync(h->h_eo, h->eo, sizeof(EigOut), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    k = h->h_eo->k;
+  }
+  te = tbeg(h);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_rowmat<decltype(t)>(h->V, ld, m, h->evecs, m, nullptr, 0, 0, nullptr, 0, h->W, ld, k, N,
+                                      h->stream);
+  }));
+  tend(h, LR_K_PROJECT, te);
+  std::swap(h->V, h->W);
+  h->c = k;
+  h->ncomp++;
+  if (h->record) {
+    st.k = k;
+    st.c_out = k;
+    int rc = dmalloc(h, (void**)&st.U, sizeof(double2) * m * m);
+    if (!rc) rc = dmalloc(h, (void**)&st.lam, sizeof(double) * m);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(st.U, h->evecs, sizeof(double2) * m * m, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(st.lam, h->evals, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
+    h->tape.push_back(st);
+  }
+  if (discarded_out) {
+    CK(cudaMemcpyAsync(h->h_eo, h->eo, sizeof(EigOut), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *discarded_out = h->h_eo->dropped;
+  }
+  return LR_OK;
+}
+
+void clear_tape(lr_ctx* h) {
+  for (auto& st : h->tape) {
+    dfree(st.ckpt);
+    dfree((void*&)st.U);
+    dfree((void*&)st.lam);
+  }
+  h->tape.clear();
+}
+
+int set_initial_state(lr_ctx* h) {
+  CK(cudaMemsetAsync(h->V, 0, slab_bytes(h), h->stream));
+  // V[0][0] = 1
+  if (h->dtype == LR_C64) {
+    const float one[2] = {1.f, 0.f};
+    CK(cudaMemcpyAsync(h->V, one, sizeof(one), cudaMemcpyHostToDevice, h->stream));
+  } else {
+    const double one[2] = {1.0, 0.0};
+    CK(cudaMemcpyAsync(h->V, one, sizeof(one), cudaMemcpyHostToDevice, h->stream));
+  }
+  CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 8, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->c = 1;
+  h->has_gate = h->has_chan = false;
+  h->ncomp = 0;
+  clear_tape(h);
+  return LR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lr_status_string(int s) {
+  switch (s) {
+    case LR_OK: return "ok";
+    case LR_EINVAL: return "invalid argument";
+    case LR_EKRAUS: return "Kraus set is not complete (sum K^dag K != I)";
+    case LR_ECAPACITY: return "column capacity exceeded";
+    case LR_ENOMEM: return "device memory allocation failed";
+    case LR_ETIMEOUT: return "bounded device wait timed out";
+    case LR_ECUDA: return g_errmsg[0] ? g_errmsg : "CUDA error";
+    case LR_ESTATE: return "call not valid in the current state";
+    case LR_ENOCONV: return "eigensolver did not converge";
+    default: return "unknown status";
+  }
+}
+
+int lr_init_ex(int n, int r, int dtype, int capacity, void* stream, lr_handle* out) {
+  if (!out) return LR_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n > 30 || r < 1 || (dtype != LR_C64 && dtype != LR_C128)) return LR_EINVAL;
+  if (capacity < r) return LR_EINVAL;
+  lr_ctx* h = new lr_ctx();
+  h->n = n;
+  h->N = 1ll << n;
+  h->r = r;
+  h->dtype = dtype;
+  h->cap = capacity + (capacity & 1);
+  h->stream = (cudaStream_t)stream;
+  h->esz = dtype == LR_C64 ? sizeof(float2) : sizeof(double2);
+  const int m = h->cap < 256 ? h->cap : 256;
+  // largest split-K workspace over every Gram shape a truncation or its adjoint can use
+  size_t pe = 0;
+  for (int ma = 1; ma <= m; ++ma) {
+    const size_t a = (size_t)gram_splits(h->N, ma, ma) * ma * ma;
+    if (a > pe) pe = a;
+    for (int kb = 1; kb <= ma; kb += (kb < 8 ? 1 : 8)) {
+      const size_t b = (size_t)gram_splits(h->N, ma, kb) * ma * kb;
+      if (b > pe) pe = b;
+    }
+    const size_t b = (size_t)gram_splits(h->N, ma, ma) * ma * ma;
+    if (b > pe) pe = b;
+  }
+  h->partials_elems = pe;
+  int rc = dmalloc(h, &h->V, slab_bytes(h));
+  if (!rc) rc = dmalloc(h, &h->W, slab_bytes(h));
+  if (!rc) rc = dmalloc(h, (void**)&h->partials, sizeof(double2) * pe);
+  if (!rc) rc = dmalloc(h, (void**)&h->G, sizeof(double2) * m * m);
+  if (!rc) rc = dmalloc(h, (void**)&h->evals, sizeof(double) * m);
+  if (!rc) rc = dmalloc(h, (void**)&h->evecs, sizeof(double2) * m * m);
+  if (!rc) rc = dmalloc(h, (void**)&h->eo, sizeof(EigOut));
+  if (!rc) rc = dmalloc(h, &h->eig_work, eigh_work_bytes(m, dtype == LR_C128));
+  if (!rc) rc = dmalloc(h, (void**)&h->acc, sizeof(double) * 8);
+  if (!rc) rc = ensure_dscratch(h, 64 * 1024);
+  if (!rc && cudaMallocHost((void**)&h->h_eo, sizeof(EigOut)) != cudaSuccess) rc = LR_ENOMEM;
+  if (!rc && cudaMallocHost((void**)&h->h_small, sizeof(double) * 64) != cudaSuccess) rc = LR_ENOMEM;
+  if (!rc) rc = set_initial_state(h);
+  if (rc) {
+    lr_free(h);
+    return rc;
+  }
+  *out = h;
+  return LR_OK;
+}
+
+int lr_init(int n, int r, int dtype, void* stream, lr_handle* out) {
+  return lr_init_ex(n, r, dtype, 4 * r, stream, out);
+}
+
+int lr_free(lr_handle h) {
+  if (!h) return LR_EINVAL;
+  cudaStreamSynchronize(h->stream);
+  clear_tape(h);
+  dfree(h->V);
+  dfree(h->W);
+  dfree((void*&)h->partials);
+  dfree((void*&)h->G);
+  dfree((void*&)h->evals);
+  dfree((void*&)h->evecs);
+  dfree((void*&)h->eo);
+  dfree(h->eig_work);
+  dfree((void*&)h->acc);
+  dfree((void*&)h->dscratch);
+  dfree((void*&)h->d_xm);
+  dfree((void*&)h->d_zm);
+  dfree((void*&)h->d_coeff);
+  dfree(h->vb[0]);
+  dfree(h->vb[1]);
+  for (auto& p : h->seg) dfree(p);
+  dfree((void*&)h->bC);
+  dfree((void*&)h->bFA);
+  dfree((void*&)h->bT1);
+  dfree((void*&)h->bMcat);
+  dfree((void*&)h->bgrad);
+  dfree((void*&)h->bpart);
+  for (auto e : h->ev) cudaEventDestroy(e);
+  if (h->h_eo) cudaFreeHost(h->h_eo);
+  if (h->h_small) cudaFreeHost(h->h_small);
+  delete h;
+  return LR_OK;
+}
+
+int lr_reset(lr_handle h) {
+  if (!h) return LR_EINVAL;
+  return set_initial_state(h);
+}
+
+int lr_apply_gate(lr_handle h, int nq, const int* qubits, const double* U, const double* dU, int param_id) {
+  if (!h || !qubits || !U || (nq != 1 && nq != 2)) return LR_EINVAL;
+  for (int i = 0; i < nq; ++i)
+    if (qubits[i] < 0 || qubits[i] >= h->n) return LR_EINVAL;
+  if (nq == 2 && qubits[0] == qubits[1]) return LR_EINVAL;
+  if (param_id >= 0 && !dU) return LR_EINVAL;
+  const int d = 1 << nq;
+  zc Uc[16], dUc[16];
+  for (int i = 0; i < d * d; ++i) {
+    Uc[i] = zc(U[2 * i], U[2 * i + 1]);
+    dUc[i] = dU ? zc(dU[2 * i], dU[2 * i + 1]) : zc(0);
+  }
+  if (check_unitary_like(Uc, d)) return LR_EINVAL;
+  int rc = flush_all(h);  // a queued channel or gate runs first
+  if (rc) return rc;
+  h->has_gate = true;
+  h->gate_nq = nq;
+  h->gate_q[0] = qubits[0];
+  h->gate_q[1] = nq == 2 ? qubits[1] : 0;
+  h->gate_pid = param_id;
+  h->gate_has_d = (dU != nullptr) && param_id >= 0;
+  for (int i = 0; i < 16; ++i) {
+    h->gate_U[i] = i < d * d ? Uc[i] : zc(0);
+    h->gate_dU[i] = i < d * d ? dUc[i] : zc(0);
+  }
+  return LR_OK;
+}
+
+int lr_apply_rotation(lr_handle h, int axis, int q, double theta, int param_id) {
+  if (!h || axis < 0 || axis > 2) return LR_EINVAL;
+  const zc I(0, 1);
+  zc S[4];
+  if (axis == 0) { S[0] = 0; S[1] = 1; S[2] = 1; S[3] = 0; }
+  else if (axis == 1) { S[0] = 0; S[1] = -I; S[2] = I; S[3] = 0; }
+  else { S[0] = 1; S[1] = 0; S[2] = 0; S[3] = -1; }
+  const double cs = std::cos(theta / 2), sn = std::sin(theta / 2);
+  zc U[4], dU[4];
+  for (int i = 0; i < 4; ++i) U[i] = ((i == 0 || i == 3) ? cs : 0.0) - I * sn * S[i];
+  // dU = -i/2 S U
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) dU[a * 2 + b] = -0.5 * I * (S[a * 2] * U[b] + S[a * 2 + 1] * U[2 + b]);
+  double Ud[8], dUd[8];
+  for (int i = 0; i < 4; ++i) {
+    Ud[2 * i] = U[i].real(); Ud[2 * i + 1] = U[i].imag();
+    dUd[2 * i] = dU[i].real(); dUd[2 * i + 1] = dU[i].imag();
+  }
+  return lr_apply_gate(h, 1, &q, Ud, dUd, param_id);
+}
+
+int lr_apply_kraus(lr_handle h, int q, int K, const double* kraus) {
+  if (!h || !kraus || K < 1 || K > 4 || q < 0 || q >= h->n) return LR_EINVAL;
+  zc M[4][4];
+  for (int al = 0; al < K; ++al)
+    for (int i = 0; i < 4; ++i) {
+      M[al][i] = zc(kraus[al * 8 + 2 * i], kraus[al * 8 + 2 * i + 1]);
+      if (!std::isfinite(M[al][i].real()) || !std::isfinite(M[al][i].imag())) return LR_EINVAL;
+    }
+  // completeness: sum_a K_a^dag K_a = I
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      zc s = 0;
+      for (int al = 0; al < K; ++al)
+        for (int l = 0; l < 2; ++l) s += std::conj(M[al][l * 2 + i]) * M[al][l * 2 + j];
+      if (std::abs(s - zc(i == j ? 1.0 : 0.0)) > 1e-10) return LR_EKRAUS;
+    }
+  // a queued channel, or a gate that does not touch q, runs first
+  if (h->has_chan) {
+    int rc = flush_all(h);
+    if (rc) return rc;
+  }
+  if (h->has_gate) {
+    const bool touches = h->gate_q[0] == q || (h->gate_nq == 2 && h->gate_q[1] == q);
+    if (!touches) {
+      int rc = flush_gate(h);
+      if (rc) return rc;
+    }
+  }
+  if (h->c * K > h->cap) return LR_ECAPACITY;
+  h->has_chan = true;
+  h->chan_q = q;
+  h->chan_K = K;
+  for (int al = 0; al < 4; ++al)
+    for (int i = 0; i < 4; ++i) h->chan_M[al][i] = al < K ? M[al][i] : zc(0);
+  return LR_OK;
+}
+
+int lr_kraus_preset(int kind, double p, double* out, int* K_out) {
+  if (!out || !K_out || !(p >= 0.0 && p <= 1.0)) return LR_EINVAL;
+  for (int i = 0; i < 32; ++i) out[i] = 0.0;
+  // out[al*8 + 2*(row*2 + col) + {0: re, 1: im}]
+  auto set = [&](int al, int row, int col, double re, double im) {
+    out[al * 8 + 2 * (row * 2 + col)] = re;
+    out[al * 8 + 2 * (row * 2 + col) + 1] = im;
+  };
+  if (kind == LR_DEPOLARIZING) {
+    const double a = std::sqrt(1.0 - p), b = std::sqrt(p / 3.0);
+    set(0, 0, 0, a, 0); set(0, 1, 1, a, 0);            // sqrt(1-p) I
+    set(1, 0, 1, b, 0); set(1, 1, 0, b, 0);            // sqrt(p/3) X
+    set(2, 0, 1, 0, -b); set(2, 1, 0, 0, b);           // sqrt(p/3) Y
+    set(3, 0, 0, b, 0); set(3, 1, 1, -b, 0);           // sqrt(p/3) Z
+    *K_out = 4;
+  } else if (kind == LR_AMPLITUDE_DAMPING) {
+    set(0, 0, 0, 1.0, 0); set(0, 1, 1, std::sqrt(1.0 - p), 0);
+    set(1, 0, 1, std::sqrt(p), 0);
+    *K_out = 2;
+  } else if (kind == LR_BIT_FLIP) {
+    const double a = std::sqrt(1.0 - p), b = std::sqrt(p);
+    set(0, 0, 0, a, 0); set(0, 1, 1, a, 0);
+    set(1, 0, 1, b, 0); set(1, 1, 0, b, 0);
+    *K_out = 2;
+  } else {
+    return LR_EINVAL;
+  }
+  return LR_OK;
+}
+
+int lr_set_eps(lr_handle h, double eps) {
+  if (!h || !(eps < 1.0)) return LR_EINVAL;
+  h->eps = eps > 0 ? eps : 0.0;
+  return LR_OK;
+}
+
+int lr_compress(lr_handle h, int r, double* discarded_out) {
+  if (!h) return LR_EINVAL;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  int r_eff = r;
+  double eps = 0.0;
+  if (r <= 0) {
+    if (h->eps > 0) { r_eff = 0; eps = h->eps; }
+    else r_eff = h->r;
+  }
+  return do_truncate(h, r_eff, eps, discarded_out);
+}
+
+int lr_probs(lr_handle h, void* out_dev) {
+  if (!h || !out_dev) return LR_EINVAL;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  const int te = tbeg(h);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_probs<decltype(t)>(h->V, h->N, h->c, h->cap, out_dev, h->stream);
+  }));
+  tend(h, LR_K_READOUT, te);
+  return LR_OK;
+}
+
+int lr_z_expect(lr_handle h, double* out_host) {
+  if (!h || !out_host) return LR_EINVAL;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  double* outd = h->dscratch;              // n + 1 values
+  double* part = h->dscratch + 64;         // <= 1024 * 32 partials
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_zexp<decltype(t)>(h->V, h->N, h->c, h->cap, h->n, part, outd, h->stream);
+  }));
+  CK(cudaMemcpyAsync(h->h_small, outd, sizeof(double) * (h->n + 1), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  memcpy(out_host, h->h_small, sizeof(double) * (h->n + 1));
+  return LR_OK;
+}
+
+int lr_expect(lr_handle h, int T, const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+              double* out_host) {
+  if (!h || T < 0 || !out_host || (T > 0 && (!xmask || !zmask || !coeff))) return LR_EINVAL;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  if (T == 0) { *out_host = 0.0; return LR_OK; }
+  rc = upload_terms(h, T, xmask, zmask, coeff);
+  if (rc) return rc;
+  rc = ensure_dscratch(h, (size_t)T * 1025 + 64);
+  if (rc) return rc;
+  double* outd = h->dscratch;
+  double* part = h->dscratch + T;
+  const int te = tbeg(h);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_pauli_expect<decltype(t)>(h->V, h->N, h->c, h->cap, T, h->d_xm, h->d_zm, part, outd,
+                                            h->stream);
+  }));
+  tend(h, LR_K_PAULI, te);
+  std::vector<double> vals(T);
+  CK(cudaMemcpyAsync(vals.data(), outd, sizeof(double) * T, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  double s = 0.0;
+  for (int t = 0; t < T; ++t) s += coeff[t] * vals[t];
+  *out_host = s;
+  return LR_OK;
+}
+
+int lr_set_record(lr_handle h, int on) {
+  if (!h) return LR_EINVAL;
+  if (on && !h->record && (h->c != 1 || h->ncomp != 0 || h->has_gate || h->has_chan)) {
+    // recording must start from the initial state so the tape covers the circuit
+    return LR_ESTATE;
+  }
+  h->record = on != 0;
+  if (!h->record) clear_tape(h);
+  return LR_OK;
+}
+
+int lr_set_checkpoint(lr_handle h, int every) {
+  if (!h || every < 0) return LR_EINVAL;
+  if (!h->tape.empty()) return LR_ESTATE;
+  h->ckpt_every = every;
+  return LR_OK;
+}
+
+int lr_backward(lr_handle h, int T, const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+                int nparams, double* grad_out_host) {
+  if (!h || T <= 0 || !xmask || !zmask || !coeff || nparams < 0 || (nparams > 0 && !grad_out_host))
+    return LR_EINVAL;
+  if (!h->record) return LR_ESTATE;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  for (auto& st : h->tape)
+    if (st.type == 0 && st.param_id >= nparams) return LR_EINVAL;
+  rc = upload_terms(h, T, xmask, zmask, coeff);
+  if (rc) return rc;
+  const int64_t N = h->N;
+  const int ld = h->cap;
+  const size_t sb = slab_bytes(h);
+  // scratch
+  for (int i = 0; i < 2; ++i)
+    if (!h->vb[i]) { rc = dmalloc(h, &h->vb[i], sb); if (rc) return rc; }
+  const int mmax = h->cap < 256 ? h->cap : 256;
+  if (!h->bC) {
+    rc = dmalloc(h, (void**)&h->bC, sizeof(double2) * mmax * mmax);
+    if (!rc) rc = dmalloc(h, (void**)&h->bFA, sizeof(double2) * mmax * mmax);
+    if (!rc) rc = dmalloc(h, (void**)&h->bT1, sizeof(double2) * mmax * mmax);
+    if (!rc) rc = dmalloc(h, (void**)&h->bMcat, sizeof(double2) * 2 * mmax * mmax);
+    if (!rc) rc = dmalloc(h, (void**)&h->bpart, sizeof(double) * 4096);
+    if (rc) return rc;
+  }
+  if (nparams + 1 > h->bgrad_cap) {
+    dfree((void*&)h->bgrad);
+    rc = dmalloc(h, (void**)&h->bgrad, sizeof(double) * (nparams + 1));
+    if (rc) return rc;
+    h->bgrad_cap = nparams + 1;
+  }
+  CK(cudaMemsetAsync(h->bgrad, 0, sizeof(double) * (nparams + 1), h->stream));
+  // seed: Vbar = H V
+  int cur = 0;
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_pauli_apply<decltype(t)>(h->V, h->vb[cur], N, h->c, ld, T, h->d_xm, h->d_zm, h->d_coeff,
+                                           h->stream);
+  }));
+  const int S = (int)h->tape.size();
+  // segments start at stages that hold a snapshot
+  int s1 = S;
+  while (s1 > 0) {
+    int s0 = s1 - 1;
+    while (s0 > 0 && h->tape[s0].ckpt == nullptr) --s0;
+    const int len = s1 - s0;
+    while ((int)h->seg.size() < len) {
+      void* p = nullptr;
+      rc = dmalloc(h, &p, sb);
+      if (rc) return rc;
+      h->seg.push_back(p);
+    }
+    // recompute stage inputs seg[i] = input of stage s0 + i
+    CK(cudaMemcpyAsync(h->seg[0], h->tape[s0].ckpt, sb, cudaMemcpyDeviceToDevice, h->stream));
+    for (int s = s0; s < s1 - 1; ++s) {
+      const Stage& st = h->tape[s];
+      void* in = h->seg[s - s0];
+      void* outp = h->seg[s - s0 + 1];
+      if (st.type == 0) {
+        CK(by_dtype(h->dtype, [&](auto t) {
+          return launch_expand<decltype(t)>(in, outp, N, st.c_in, ld, st.op, h->stream);
+        }));
+      } else {
+        CK(by_dtype(h->dtype, [&](auto t) {
+          return launch_rowmat<decltype(t)>(in, ld, st.m, st.U, st.m, nullptr, 0, 0, nullptr, 0, outp, ld, st.k,
+                                            N, h->stream);
+        }));
+      }
+    }
+    // backward through the segment
+    for (int s = s1 - 1; s >= s0; --s) {
+      const Stage& st = h->tape[s];
+      void* in = h->seg[s - s0];
+      void* vbar = h->vb[cur];
+      void* vbin = h->vb[cur ^ 1];
+      if (st.type == 0) {
+        int nb = 0;
+        CK(by_dtype(h->dtype, [&](auto t) {
+          return launch_expand_adj<decltype(t)>(vbar, in, vbin, N, st.c_in, ld, st.op, h->bpart, &nb,
+                                                h->stream);
+        }));
+        if (st.op.has_grad && st.param_id >= 0)
+          CK(launch_sum(h->bpart, nb, h->bgrad + st.param_id, 1, h->stream));
+      } else {
+        const int m = st.m, k = st.k;
+        const int splits = gram_splits(N, m, k);
+        CK(by_dtype(h->dtype, [&](auto t) {
+          return launch_gram<decltype(t)>(in, ld, m, vbar, ld, k, N, false, h->partials, splits, h->bC,
+                                          h->stream);
+        }));
+        CK(launch_trunc_adj_small(h->bC, st.U, st.lam, m, k, h->bFA, h->bT1, h->bMcat, h->stream));
+        CK(by_dtype(h->dtype, [&](auto t) {
+          return launch_rowmat<decltype(t)>(vbar, ld, k, h->bMcat, m, in, ld, m, h->bMcat + (size_t)k * m, m,
+                                            vbin, ld, m, N, h->stream);
+        }));
+      }
+      cur ^= 1;
+    }
+    s1 = s0;
+  }
+  if (nparams > 0) {
+    CK(cudaMemcpyAsync(grad_out_host, h->bgrad, sizeof(double) * nparams, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return LR_OK;
+}
+
+int lr_get_info(lr_handle h, lr_info* info) {
+  if (!h || !info) return LR_EINVAL;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h->h_small, h->acc, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  info->n = h->n;
+  info->columns = h->c;
+  info->capacity = h->cap;
+  info->dtype = h->dtype;
+  info->compressions = h->ncomp;
+  info->stages = (int64_t)h->tape.size();
+  info->discarded = h->h_small[0];
+  info->last_gap = h->h_small[1];
+  return h->h_small[2] > 0 ? LR_ENOCONV : LR_OK;
+}
+
+int lr_get_state(lr_handle h, void* out_host) {
+  if (!h || !out_host) return LR_EINVAL;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  CK(cudaMemcpy2DAsync(out_host, h->c * h->esz, h->V, h->cap * h->esz, h->c * h->esz, (size_t)h->N,
+                       cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LR_OK;
+}
+
+int64_t lr_device_bytes(lr_handle h) { return h ? (int64_t)h->bytes : 0; }
+
+int lr_set_timing(lr_handle h, int on) {
+  if (!h) return LR_EINVAL;
+  if (on && h->ev.empty()) {
+    h->ev.resize(4096);
+    for (auto& e : h->ev) CK(cudaEventCreate(&e));
+  }
+  timer_drain(h);
+  h->timing = on != 0;
+  return LR_OK;
+}
+
+int lr_kernel_times(lr_handle h, double* ms_out, int64_t* counts_out) {
+  if (!h || !ms_out || !counts_out) return LR_EINVAL;
+  timer_drain(h);
+  for (int i = 0; i < LR_NKCLASS; ++i) {
+    ms_out[i] = h->kms[i];
+    counts_out[i] = h->kcnt[i];
+    h->kms[i] = 0.0;
+    h->kcnt[i] = 0;
+  }
+  return LR_OK;
+}
+
+}  // extern "C"

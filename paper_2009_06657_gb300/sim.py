@@ -1,0 +1,231 @@
+"""Python front end of liblret: a simulation handle, a circuit runner for the
+shared op-list format, and a torch.autograd.Function around the adjoint.
+
+Everything numeric runs in the CUDA library; this module converts arguments
+(gate names to ABI calls, Pauli strings to bit masks, numpy arrays to pointers).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _ffi
+from ._ffi import check, lib
+
+_AXIS = {"x": 0, "y": 1, "z": 2}
+_CNOT = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=np.complex128)
+_CZ = np.diag([1, 1, 1, -1]).astype(np.complex128)
+_CHAN = {"dep": _ffi.LR_DEPOLARIZING, "ad": _ffi.LR_AMPLITUDE_DAMPING, "bf": _ffi.LR_BIT_FLIP}
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _cplx_flat(M):
+    M = np.ascontiguousarray(np.asarray(M, dtype=np.complex128))
+    return np.ascontiguousarray(M.view(np.float64).reshape(-1))
+
+
+def pauli_masks(terms, n):
+    """[(coeff, [(q, 'X'|'Y'|'Z'), ...]), ...] -> (xmask, zmask, coeff) arrays."""
+    T = len(terms)
+    xm = np.zeros(T, dtype=np.uint64)
+    zm = np.zeros(T, dtype=np.uint64)
+    cf = np.zeros(T, dtype=np.float64)
+    for t, (c, string) in enumerate(terms):
+        x = z = 0
+        for q, s in string:
+            if not 0 <= q < n:
+                raise ValueError(f"qubit {q} out of range")
+            if s in ("X", "Y"):
+                x |= 1 << q
+            if s in ("Z", "Y"):
+                z |= 1 << q
+        xm[t], zm[t], cf[t] = x, z, c
+    return xm, zm, cf
+
+
+def kraus_preset(kind, p):
+    out = np.zeros(32, dtype=np.float64)
+    K = C.c_int(0)
+    check(lib.lr_kraus_preset(_CHAN[kind], float(p), _dptr(out), C.byref(K)), "lr_kraus_preset")
+    return out, K.value
+
+
+class LRSim:
+    """One low-rank simulation on the current CUDA device (rho = V V^dag)."""
+
+    def __init__(self, n, r, dtype="c64", capacity=None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblret needs a CUDA device")
+        self.n, self.r = int(n), int(r)
+        self.dtype = _ffi.LR_C64 if dtype in ("c64", "complex64", _ffi.LR_C64) else _ffi.LR_C128
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        cap = 4 * self.r if capacity is None else int(capacity)
+        check(lib.lr_init_ex(self.n, self.r, self.dtype, cap, C.c_void_p(self.stream.cuda_stream),
+                             C.byref(h)), "lr_init")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.lr_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        check(lib.lr_reset(self.h), "lr_reset")
+
+    def apply_gate(self, qubits, U, dU=None, param_id=-1):
+        qs = (C.c_int * len(qubits))(*[int(q) for q in qubits])
+        Uf = _cplx_flat(U)
+        dUf = _cplx_flat(dU) if dU is not None else None
+        check(lib.lr_apply_gate(self.h, len(qubits), qs, _dptr(Uf),
+                                _dptr(dUf) if dUf is not None else None, int(param_id)), "lr_apply_gate")
+
+    def apply_rotation(self, axis, q, theta, param_id=-1):
+        check(lib.lr_apply_rotation(self.h, _AXIS[axis.lower()], int(q), float(theta), int(param_id)),
+              "lr_apply_rotation")
+
+    def apply_kraus(self, q, kraus):
+        if isinstance(kraus, tuple) and len(kraus) == 2 and isinstance(kraus[0], np.ndarray) and kraus[0].dtype == np.float64:
+            buf, K = kraus
+        else:
+            mats = [np.asarray(k, dtype=np.complex128) for k in kraus]
+            K = len(mats)
+            buf = np.zeros(32, dtype=np.float64)
+            buf[: 8 * K] = _cplx_flat(np.stack(mats))
+        check(lib.lr_apply_kraus(self.h, int(q), int(K), _dptr(buf)), "lr_apply_kraus")
+
+    def apply_channel(self, kind, q, p):
+        self.apply_kraus(q, kraus_preset(kind, p))
+
+    def compress(self, r=0, want_discarded=False):
+        if want_discarded:
+            d = C.c_double(0.0)
+            check(lib.lr_compress(self.h, int(r), C.byref(d)), "lr_compress")
+            return d.value
+        check(lib.lr_compress(self.h, int(r), None), "lr_compress")
+        return None
+
+    def set_eps(self, eps):
+        check(lib.lr_set_eps(self.h, float(eps)), "lr_set_eps")
+
+    def probs(self, out=None):
+        dt = torch.float32 if self.dtype == _ffi.LR_C64 else torch.float64
+        if out is None:
+            out = torch.empty(1 << self.n, dtype=dt, device="cuda")
+        check(lib.lr_probs(self.h, C.c_void_p(out.data_ptr())), "lr_probs")
+        return out
+
+    def expect(self, terms):
+        xm, zm, cf = pauli_masks(terms, self.n)
+        return self.expect_masks(xm, zm, cf)
+
+    def expect_masks(self, xm, zm, cf):
+        out = C.c_double(0.0)
+        check(lib.lr_expect(self.h, len(cf), xm.ctypes.data_as(C.POINTER(C.c_uint64)),
+                            zm.ctypes.data_as(C.POINTER(C.c_uint64)), _dptr(cf), C.byref(out)), "lr_expect")
+        return out.value
+
+    def z_expect(self):
+        out = np.zeros(self.n + 1, dtype=np.float64)
+        check(lib.lr_z_expect(self.h, _dptr(out)), "lr_z_expect")
+        return out[: self.n], out[self.n]
+
+    def set_record(self, on=True):
+        check(lib.lr_set_record(self.h, 1 if on else 0), "lr_set_record")
+
+    def set_checkpoint(self, every):
+        check(lib.lr_set_checkpoint(self.h, int(every)), "lr_set_checkpoint")
+
+    def backward(self, terms, nparams):
+        xm, zm, cf = pauli_masks(terms, self.n)
+        g = np.zeros(max(nparams, 1), dtype=np.float64)
+        check(lib.lr_backward(self.h, len(cf), xm.ctypes.data_as(C.POINTER(C.c_uint64)),
+                              zm.ctypes.data_as(C.POINTER(C.c_uint64)), _dptr(cf), int(nparams), _dptr(g)),
+              "lr_backward")
+        return g[:nparams]
+
+    def info(self):
+        inf = _ffi.lr_info()
+        st = lib.lr_get_info(self.h, C.byref(inf))
+        if st not in (_ffi.LR_OK, _ffi.LR_ENOCONV):
+            check(st, "lr_get_info")
+        return {"n": inf.n, "columns": inf.columns, "capacity": inf.capacity, "dtype": inf.dtype,
+                "compressions": inf.compressions, "stages": inf.stages, "discarded": inf.discarded,
+                "last_gap": inf.last_gap, "converged": st == _ffi.LR_OK}
+
+    def state(self):
+        inf = self.info()
+        dt = np.complex64 if self.dtype == _ffi.LR_C64 else np.complex128
+        out = np.zeros((1 << self.n, inf["columns"]), dtype=dt)
+        check(lib.lr_get_state(self.h, C.c_void_p(out.ctypes.data)), "lr_get_state")
+        return out
+
+    def set_timing(self, on=True):
+        check(lib.lr_set_timing(self.h, 1 if on else 0), "lr_set_timing")
+
+    def kernel_times(self):
+        ms = np.zeros(_ffi.LR_NKCLASS, dtype=np.float64)
+        cnt = np.zeros(_ffi.LR_NKCLASS, dtype=np.int64)
+        check(lib.lr_kernel_times(self.h, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64))),
+              "lr_kernel_times")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(_ffi.KCLASSES)}
+
+    def device_bytes(self):
+        return int(lib.lr_device_bytes(self.h))
+
+
+def is_gate(op):
+    return op["op"] in ("rx", "ry", "rz", "cnot", "cz")
+
+
+def run_ops(sim, ops, r=0, thetas=None, compress=True):
+    """Apply an op list; truncate after every channel (one-qubit Kraus groups)."""
+    for o in ops:
+        name = o["op"]
+        if name in ("rx", "ry", "rz"):
+            pid = int(o.get("pid", -1))
+            th = float(thetas[pid]) if (thetas is not None and pid >= 0) else float(o["theta"])
+            sim.apply_rotation(name[1], o["q"], th, pid)
+        elif name == "cnot":
+            sim.apply_gate(o["q"], _CNOT)
+        elif name == "cz":
+            sim.apply_gate(o["q"], _CZ)
+        elif name in _CHAN:
+            sim.apply_channel(name, o["q"], o["p"] if "p" in o else o["gamma"])
+            if compress:
+                sim.compress(r)
+        else:
+            raise ValueError(f"unknown op {name!r}")
+    return sim
+
+
+class LRExpectation(torch.autograd.Function):
+    """<H>(theta) of a parameterised noisy circuit; backward = liblret adjoint."""
+
+    @staticmethod
+    def forward(ctx, thetas, sim, ops, terms, r, ckpt_every):
+        th = thetas.detach().cpu().numpy().astype(np.float64)
+        sim.reset()
+        sim.set_checkpoint(ckpt_every)
+        sim.set_record(True)
+        run_ops(sim, ops, r=r, thetas=th)
+        val = sim.expect(terms)
+        ctx.sim, ctx.terms, ctx.nparams = sim, terms, len(th)
+        return torch.tensor(val, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = ctx.sim.backward(ctx.terms, ctx.nparams)
+        ctx.sim.set_record(False)
+        return torch.from_numpy(g) * grad_out, None, None, None, None, None
