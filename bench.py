@@ -184,11 +184,13 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / n_e2e
 
-    # FP64 comparators at the same size (few truncations; rate per noisy gate-step)
-    fp64 = bench_fp64(args, layers, dev, stream) if (rank == 0 and not args.no_fp64) else None
     info = sim.info()
     sim.close()
-    return dict(ms=ms, g_per=g_per, c_per=c_per, ktimes=ktimes, clk=clk, e2e_s=e2e_s, fp64=fp64, info=info)
+    # FP64 comparators at the same size (few truncations; rate per noisy gate-step)
+    fp64 = bench_fp64(args, layers, dev, stream) if (rank == 0 and not args.no_fp64) else None
+    adj = bench_adjoint(dev, stream) if (rank == 0 and not args.no_adjoint) else None
+    return dict(ms=ms, g_per=g_per, c_per=c_per, ktimes=ktimes, clk=clk, e2e_s=e2e_s, fp64=fp64, info=info,
+                adjoint=adj)
 
 
 def bench_fp64(args, layers, dev, stream):
@@ -252,6 +254,48 @@ def bench_fp64(args, layers, dev, stream):
     return out
 
 
+def bench_adjoint(dev, stream, reps=2):
+    """Adjoint gradient time / forward time on the 14-qubit hardware-efficient
+    ansatz: 6 layers of Ry, Rz on every qubit plus a CZ ladder (168 parameters,
+    angles N(0, 0.5^2)), depolarizing p = 1e-3 after every gate, r = 32,
+    complex64 state, checkpoint every 8 stages, 50-term random Pauli sum.
+    The forward pass records the tape (truncation eigenvectors and
+    eigenvalues, state checkpoints); the backward pass recomputes states
+    between checkpoints and runs the adjoint kernels."""
+    import torch
+
+    import paper_2009_06657_gb300 as lr
+    from workloads import hea, random_pauli_sum
+    n, r = 14, 32
+    ops, th = hea(n, 6, seed=4000, noise=("dep", 1e-3))
+    terms = random_pauli_sum(n, 50, seed=4001)
+    sim = lr.LRSim(n, r, dtype="c64", stream=stream)
+    fwd, bwd = [], []
+    with torch.cuda.stream(stream):
+        for i in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.reset()
+            sim.set_checkpoint(8)
+            sim.set_record(True)
+            lr.run_ops(sim, ops, r=r, thetas=th)
+            val = sim.expect(terms)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            g = sim.backward(terms, len(th))
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            sim.set_record(False)
+            if i > 0:
+                fwd.append(t1 - t0)
+                bwd.append(t2 - t1)
+    sim.close()
+    f, b = statistics.median(fwd), statistics.median(bwd)
+    return {"workload": "14-qubit HEA, 6 layers, 168 parameters, r=32, dep p=1e-3, 50 Pauli terms, "
+                        "checkpoint every 8 stages", "forward_s": f, "backward_s": b,
+            "adjoint_over_forward": b / f, "grad_norm": float(sum(x * x for x in g) ** 0.5)}
+
+
 def algorithmic(kclass, info_c):
     """(bound, bytes_or_flops per launch) of a steady-state launch of a kernel class."""
     N, r, K, esz = 1 << N_QUBITS, RANK, 4, 8
@@ -277,6 +321,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -322,7 +367,7 @@ def main():
         "clocks": res["clk"],
         "e2e": {"value": res["g_per"] / res["e2e_s"], "unit": "noisy gate-steps/s",
                 "h2d_bytes_per_step": h2d_bytes(get_layers()[0]), "d2h_bytes_per_step": (1 << N_QUBITS) * 4 + 8},
-        "fp64": None, "cpu_baseline": None,
+        "fp64": None, "cpu_baseline": None, "adjoint": res.get("adjoint"),
     }
     launches = sum(v[1] for v in kt.values())
     out["gpu_launches"] = launches * args.steps

@@ -104,9 +104,28 @@ int lr_kraus_preset(int kind, double p, double* out, int* K_out);
  * this truncation (synchronises). */
 int lr_compress(lr_handle h, int r, double* discarded_out);
 
+/* Truncation path. LR_PATH_AUTO (default): a one-qubit channel followed by a
+ * truncation is applied without forming V' -- the Gram of V' is assembled from
+ * the 2c x 2c Gram of the row pairs [V_0 V_1] of the channel's qubit and the
+ * projection V' U_r acts on those row pairs (same rho as Eq. 4 then Sec. II.B);
+ * a queued one-qubit gate on the same qubit is folded in. Recording for
+ * lr_backward uses the expanded form. LR_PATH_EXPAND always forms V'. */
+#define LR_PATH_AUTO 0
+#define LR_PATH_EXPAND 1
+int lr_set_path(lr_handle h, int which);
+
 /* Threshold rule of Sec. II.B: keep the smallest k with
  * sum_{i<=k} lambda_i >= (1 - eps) * sum_i lambda_i. eps <= 0 disables it. */
 int lr_set_eps(lr_handle h, double eps);
+
+/* Eigensolver of the truncation: LR_EIG_AUTO (default: two-sided Jacobi for
+ * small Gram matrices, Householder tridiagonal + bisection + inverse iteration
+ * above 32 columns (FP32 state) or 64 columns (FP64 state)), LR_EIG_JACOBI or
+ * LR_EIG_TRIDIAG. */
+#define LR_EIG_AUTO 0
+#define LR_EIG_JACOBI 1
+#define LR_EIG_TRIDIAG 2
+int lr_set_eigensolver(lr_handle h, int which);
 
 /* Prob(x) = sum_v |V_xv|^2 (Eq. 9) into a caller-owned device buffer of 2^n
  * floats (LR_C64) or doubles (LR_C128). Asynchronous. */

@@ -162,6 +162,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigh_jacobi(const double2* __re
   }
   (void)s_rank_dummy;
 
+  // a NaN diagonal (from a non-finite input) sorts last so ranks stay a permutation
+  for (int i = tid; i < m; i += blockDim.x)
+    if (!(A[i * m + i].x == A[i * m + i].x)) A[i * m + i].x = -INFINITY;
+  __syncthreads();
   // sort descending (rank by count; ties by index) and write FP64 results
   for (int i = tid; i < m; i += blockDim.x) {
     const T li = A[i * m + i].x;
@@ -171,7 +175,17 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigh_jacobi(const double2* __re
       rank += (lj > li) || (lj == li && j < i);
     }
     evals[rank] = (double)li;
-    for (int row = 0; row < m; ++row) evecs[(size_t)row * m + rank] = to_d2(Vec[row * m + i]);
+    // accumulated rotations drift from unit norm by O(sweeps m eps); renormalise
+    double nrm = 0.0;
+    for (int row = 0; row < m; ++row) {
+      const double2 v = to_d2(Vec[row * m + i]);
+      nrm += v.x * v.x + v.y * v.y;
+    }
+    const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 1.0;
+    for (int row = 0; row < m; ++row) {
+      const double2 v = to_d2(Vec[row * m + i]);
+      evecs[(size_t)row * m + rank] = make_double2(v.x * inv, v.y * inv);
+    }
   }
   __syncthreads();
   __threadfence_block();

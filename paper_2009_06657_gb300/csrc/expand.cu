@@ -32,7 +32,14 @@ __device__ __forceinline__ void group_rows(uint64_t grp, const int* bits, uint64
 template <typename T, int G>
 __global__ void __launch_bounds__(256) k_expand(const cx<T>* __restrict__ V, cx<T>* __restrict__ W,
                                                 int64_t total, int c, int ld, GroupOp op) {
+  // operator matrices converted once per block (FP64 -> T conversion is slow per use)
+  __shared__ cx<T> sM[4][G][G];
   const int K = op.K;
+  for (int i = threadIdx.x; i < 4 * G * G; i += blockDim.x) {
+    const int al = i / (G * G), a = (i / G) % G, g = i % G;
+    sM[al][a][g] = from_d2<T>(op.M[al][a][g]);
+  }
+  __syncthreads();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t grp = (uint64_t)(e / c);
@@ -47,7 +54,7 @@ __global__ void __launch_bounds__(256) k_expand(const cx<T>* __restrict__ V, cx<
       for (int a = 0; a < G; ++a) {
         cx<T> acc = mk<T>(0, 0);
 #pragma unroll
-        for (int g = 0; g < G; ++g) cfma(acc, from_d2<T>(op.M[al][a][g]), v[g]);
+        for (int g = 0; g < G; ++g) cfma(acc, sM[al][a][g], v[g]);
         W[rows[a] * (uint64_t)ld + (uint64_t)al * c + j] = acc;
       }
     }
@@ -83,7 +90,14 @@ __global__ void __launch_bounds__(256) k_expand_adj(const cx<T>* __restrict__ Wb
                                                     cx<T>* __restrict__ Vbar, int64_t total, int c,
                                                     int ld, GroupOp op, double* grad_partials) {
   __shared__ double red[32];
+  __shared__ cx<T> sM[4][G][G], sdM[4][G][G];
   const int K = op.K;
+  for (int i = threadIdx.x; i < 4 * G * G; i += blockDim.x) {
+    const int al = i / (G * G), a = (i / G) % G, g = i % G;
+    sM[al][a][g] = from_d2<T>(op.M[al][a][g]);
+    sdM[al][a][g] = from_d2<T>(op.dM[al][a][g]);
+  }
+  __syncthreads();
   double gacc = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -102,11 +116,11 @@ __global__ void __launch_bounds__(256) k_expand_adj(const cx<T>* __restrict__ Wb
       for (int a = 0; a < G; ++a) {
         const cx<T> wb = Wbar[rows[a] * (uint64_t)ld + (uint64_t)al * c + j];
 #pragma unroll
-        for (int g = 0; g < G; ++g) cfmac(out[g], from_d2<T>(op.M[al][a][g]), wb);
+        for (int g = 0; g < G; ++g) cfmac(out[g], sM[al][a][g], wb);
         if (op.has_grad) {
           cx<T> dv = mk<T>(0, 0);
 #pragma unroll
-          for (int g = 0; g < G; ++g) cfma(dv, from_d2<T>(op.dM[al][a][g]), vin[g]);
+          for (int g = 0; g < G; ++g) cfma(dv, sdM[al][a][g], vin[g]);
           // Re(conj(wb) * dv)
           gacc += (double)wb.x * (double)dv.x + (double)wb.y * (double)dv.y;
         }

@@ -14,14 +14,24 @@ constexpr int TILE = 64;
 constexpr int KSTEP = 16;
 
 // FP32 products are accumulated in FP32 over FLUSH rows, then added into FP64
-// registers, so the chunk sum carries FP64 rounding beyond 128-term runs.
-template <typename T> struct Flush { static constexpr int rows = 128; };
+// registers, so the chunk sum carries FP64 rounding beyond 64-term runs.
+template <typename T> struct Flush { static constexpr int rows = 64; };
+
+// Pair mode (pairbit >= 0): the operand is Z = [V_0 V_1], the rows of V with
+// bit `pairbit` clear and set side by side: logical row x of Z is the pair
+// (x0, x0 | 2^pairbit) with x0 = x with a zero inserted at pairbit, and logical
+// column i < 2*chalf is column i mod chalf of row x0 (i < chalf) or of its partner.
+__device__ __forceinline__ int64_t pair_index(int64_t x, int i, int pairbit, int chalf, int ld) {
+  const uint64_t x0 = insert_zero((uint64_t)x, pairbit);
+  const int b = i >= chalf;
+  return (int64_t)(x0 | ((uint64_t)b << pairbit)) * ld + (i - b * chalf);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const cx<T>* __restrict__ A, int lda, int ma,
                                               const cx<T>* __restrict__ B, int ldb, int mb, int64_t N,
                                               int64_t chunk, int tiles_j, int hermitian,
-                                              double2* __restrict__ partials) {
+                                              double2* __restrict__ partials, int pairbit, int chalf) {
   __shared__ cx<T> As[KSTEP][TILE];
   __shared__ cx<T> Bs[KSTEP][TILE];
   int ti, tj;
@@ -52,8 +62,13 @@ __global__ void __launch_bounds__(256) k_gram(const cx<T>* __restrict__ A, int l
       const int rr = idx / TILE, cc = idx % TILE;
       const int64_t x = xb + rr;
       const int ia = ti * TILE + cc, ib = tj * TILE + cc;
-      As[rr][cc] = (x < x1 && ia < ma) ? A[x * lda + ia] : mk<T>(0, 0);
-      Bs[rr][cc] = (x < x1 && ib < mb) ? B[x * ldb + ib] : mk<T>(0, 0);
+      if (pairbit < 0) {
+        As[rr][cc] = (x < x1 && ia < ma) ? A[x * lda + ia] : mk<T>(0, 0);
+        Bs[rr][cc] = (x < x1 && ib < mb) ? B[x * ldb + ib] : mk<T>(0, 0);
+      } else {
+        As[rr][cc] = (x < x1 && ia < ma) ? A[pair_index(x, ia, pairbit, chalf, lda)] : mk<T>(0, 0);
+        Bs[rr][cc] = (x < x1 && ib < mb) ? B[pair_index(x, ib, pairbit, chalf, ldb)] : mk<T>(0, 0);
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -138,14 +153,15 @@ int gram_splits(int64_t N, int ma, int mb) {
 
 template <typename T>
 cudaError_t launch_gram(const void* A, int lda, int ma, const void* B, int ldb, int mb, int64_t N,
-                        bool hermitian, double2* partials, int splits, double2* out, cudaStream_t s) {
+                        bool hermitian, double2* partials, int splits, double2* out, cudaStream_t s,
+                        int pairbit, int chalf) {
   const int ti = (ma + TILE - 1) / TILE, tj = (mb + TILE - 1) / TILE;
   const int tiles = hermitian ? ti * (ti + 1) / 2 : ti * tj;
   int64_t chunk = (N + splits - 1) / splits;
   chunk = ((chunk + KSTEP - 1) / KSTEP) * KSTEP;
   dim3 grid(tiles, splits);
   k_gram<T><<<grid, 256, 0, s>>>((const cx<T>*)A, lda, ma, (const cx<T>*)B, ldb, mb, N, chunk, tj,
-                                 hermitian ? 1 : 0, partials);
+                                 hermitian ? 1 : 0, partials, pairbit, chalf);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t total = (int64_t)ma * mb;
@@ -156,12 +172,15 @@ cudaError_t launch_gram(const void* A, int lda, int ma, const void* B, int ldb, 
 }
 
 // Y[x][j] = sum_i A1[x][i] M1[i][j] + sum_i A2[x][i] M2[i][j]
+// Pair mode (pairbit >= 0): rows are pairs as in k_gram, A1 has 2*chalf
+// logical columns and Y has p = 2*phalf logical columns split the same way.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rowmat(const cx<T>* __restrict__ A1, int lda1, int k1,
                                                 const double2* __restrict__ M1, int ldm1,
                                                 const cx<T>* __restrict__ A2, int lda2, int k2,
                                                 const double2* __restrict__ M2, int ldm2,
-                                                cx<T>* __restrict__ Y, int ldy, int p, int64_t N) {
+                                                cx<T>* __restrict__ Y, int ldy, int p, int64_t N,
+                                                int pairbit, int chalf, int phalf) {
   __shared__ cx<T> As[TILE][KSTEP + 1];
   __shared__ cx<T> Ms[KSTEP][TILE];
   const int64_t xbase = (int64_t)blockIdx.x * TILE;
@@ -185,7 +204,10 @@ __global__ void __launch_bounds__(256) k_rowmat(const cx<T>* __restrict__ A1, in
         const int rr = idx / KSTEP, cc = idx % KSTEP;
         const int64_t x = xbase + rr;
         const int i = ib + cc;
-        As[rr][cc] = (x < N && i < kk_n) ? A[x * lda + i] : mk<T>(0, 0);
+        if (pairbit < 0)
+          As[rr][cc] = (x < N && i < kk_n) ? A[x * lda + i] : mk<T>(0, 0);
+        else
+          As[rr][cc] = (x < N && i < kk_n) ? A[pair_index(x, i, pairbit, chalf, lda)] : mk<T>(0, 0);
         // M tile: KSTEP rows x TILE cols
         const int mr = idx / TILE, mc = idx % TILE;
         const int mi = ib + mr, mj = jbase + mc;
@@ -213,18 +235,66 @@ __global__ void __launch_bounds__(256) k_rowmat(const cx<T>* __restrict__ A1, in
     for (int b = 0; b < 4; ++b) {
       const int64_t x = xbase + ty + 16 * a;
       const int j = jbase + tx + 16 * b;
-      if (x < N && j < p) Y[x * ldy + j] = acc[a][b];
+      if (x < N && j < p) {
+        if (pairbit < 0) Y[x * ldy + j] = acc[a][b];
+        else Y[pair_index(x, j, pairbit, phalf, ldy)] = acc[a][b];
+      }
     }
 }
 
 template <typename T>
 cudaError_t launch_rowmat(const void* A1, int lda1, int k1, const double2* M1, int ldm1,
                           const void* A2, int lda2, int k2, const double2* M2, int ldm2,
-                          void* Y, int ldy, int p, int64_t N, cudaStream_t s) {
+                          void* Y, int ldy, int p, int64_t N, cudaStream_t s, int pairbit, int chalf,
+                          int phalf) {
   if (N == 0 || p == 0) return cudaSuccess;
   dim3 grid((unsigned)((N + TILE - 1) / TILE), (unsigned)((p + TILE - 1) / TILE));
   k_rowmat<T><<<grid, 256, 0, s>>>((const cx<T>*)A1, lda1, k1, M1, ldm1, (const cx<T>*)A2, lda2, k2, M2,
-                                   ldm2, (cx<T>*)Y, ldy, p, N);
+                                   ldm2, (cx<T>*)Y, ldy, p, N, pairbit, chalf, phalf);
+  return cudaGetLastError();
+}
+
+// ---- structured truncation helpers (FP64, small) -----------------------------
+// G'[al*c + i][be*c + j] = sum_{b,b'} Q[al][be][b][b'] S[b*c + i][b'*c + j]
+__global__ void k_assemble_gram(const double2* __restrict__ S, int c, int K, PairQ q, double2* __restrict__ Gp) {
+  const int m = K * c;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  const int row = e / m, col = e % m;
+  const int al = row / c, i = row % c, be = col / c, j = col % c;
+  const int ld = 2 * c;
+  double2 acc = make_double2(0, 0);
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int bp = 0; bp < 2; ++bp)
+      cfma(acc, q.Q[al][be][b][bp], S[(int64_t)(b * c + i) * ld + bp * c + j]);
+  if (row == col) acc.y = 0.0;
+  Gp[e] = acc;
+}
+
+// D[b*c + i][a*k + j] = sum_al M[al][a][b] U[al*c + i][j]   (U: m x m, leading dim m)
+__global__ void k_build_proj(const double2* __restrict__ U, int c, int K, int k, PairQ q,
+                             double2* __restrict__ D) {
+  const int rows = 2 * c, cols = 2 * k, m = K * c;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int r = e / cols, cl = e % cols;
+  const int b = r / c, i = r % c, a = cl / k, j = cl % k;
+  double2 acc = make_double2(0, 0);
+  for (int al = 0; al < K; ++al) cfma(acc, q.M[al][a][b], U[(int64_t)(al * c + i) * m + j]);
+  D[e] = acc;
+}
+
+cudaError_t launch_assemble_gram(const double2* S, int c, int K, const PairQ& q, double2* Gp, cudaStream_t s) {
+  const int m = K * c;
+  k_assemble_gram<<<(m * m + 255) / 256, 256, 0, s>>>(S, c, K, q, Gp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_proj(const double2* U, int c, int K, int k, const PairQ& q, double2* D, cudaStream_t s) {
+  const int n = 4 * c * k;
+  k_build_proj<<<(n + 255) / 256, 256, 0, s>>>(U, c, K, k, q, D);
   return cudaGetLastError();
 }
 
@@ -289,12 +359,14 @@ cudaError_t launch_trunc_adj_small(const double2* C, const double2* U, const dou
 }
 
 template cudaError_t launch_gram<float>(const void*, int, int, const void*, int, int, int64_t, bool, double2*,
-                                        int, double2*, cudaStream_t);
+                                        int, double2*, cudaStream_t, int, int);
 template cudaError_t launch_gram<double>(const void*, int, int, const void*, int, int, int64_t, bool, double2*,
-                                         int, double2*, cudaStream_t);
+                                         int, double2*, cudaStream_t, int, int);
 template cudaError_t launch_rowmat<float>(const void*, int, int, const double2*, int, const void*, int, int,
-                                          const double2*, int, void*, int, int, int64_t, cudaStream_t);
+                                          const double2*, int, void*, int, int, int64_t, cudaStream_t, int, int,
+                                          int);
 template cudaError_t launch_rowmat<double>(const void*, int, int, const double2*, int, const void*, int, int,
-                                           const double2*, int, void*, int, int, int64_t, cudaStream_t);
+                                           const double2*, int, void*, int, int, int64_t, cudaStream_t, int, int,
+                                           int);
 
 }  // namespace lret

@@ -50,17 +50,34 @@ cudaError_t launch_pauli_apply(const void* V, void* out, int64_t N, int c, int l
 
 // ---- Gram: out[i][j] = sum_x conj(A[x][i]) B[x][j], FP64 result (ma x mb, row-major).
 // partials: workspace of splits * ma * mb double2. hermitian => A == B, ma == mb.
+// pairbit >= 0: the operand is the pair matrix Z = [V_0 V_1] (N/2 logical rows,
+// 2*chalf logical columns) formed from V without copying; N is then N/2.
 template <typename T>
 cudaError_t launch_gram(const void* A, int lda, int ma, const void* B, int ldb, int mb, int64_t N,
-                        bool hermitian, double2* partials, int splits, double2* out, cudaStream_t s);
+                        bool hermitian, double2* partials, int splits, double2* out, cudaStream_t s,
+                        int pairbit = -1, int chalf = 0);
 int gram_splits(int64_t N, int ma, int mb);
+
+// Small matrices of the structured truncation: M[al] = Kt_al G (2x2) and
+// Q[al][be] = M[al]^dag M[be].
+struct PairQ {
+  double2 M[4][2][2];
+  double2 Q[4][4][2][2];
+};
+// G' (K c x K c) from the pair Gram S (2c x 2c)
+cudaError_t launch_assemble_gram(const double2* S, int c, int K, const PairQ& q, double2* Gp, cudaStream_t s);
+// D (2c x 2k) = pair-projection matrix from the leading k eigenvectors U (m x m)
+cudaError_t launch_build_proj(const double2* U, int c, int K, int k, const PairQ& q, double2* D, cudaStream_t s);
 
 // ---- Y[x][j] = sum_i A1[x][i] M1[i][j] + sum_i A2[x][i] M2[i][j]  (j < p)
 // M1, M2: complex128 device matrices with leading dimensions ldm1, ldm2. A2 may be null.
+// pairbit >= 0: A1 and Y are read/written as pair matrices (A1: 2*chalf logical
+// columns, Y: p = 2*phalf), N is the number of pairs; A2 must be null.
 template <typename T>
 cudaError_t launch_rowmat(const void* A1, int lda1, int k1, const double2* M1, int ldm1,
                           const void* A2, int lda2, int k2, const double2* M2, int ldm2,
-                          void* Y, int ldy, int p, int64_t N, cudaStream_t s);
+                          void* Y, int ldy, int p, int64_t N, cudaStream_t s, int pairbit = -1,
+                          int chalf = 0, int phalf = 0);
 
 // ---- Hermitian eigensolver (Jacobi, arithmetic in T): evals descending, evecs
 // columns in the same order (m x m complex128, row-major), rank choice and FP64
@@ -69,6 +86,13 @@ template <typename T>
 cudaError_t launch_eigh(const double2* G, int m, void* work, double* evals, double2* evecs,
                         EigOut* out, int r, double eps, cudaStream_t s);
 size_t eigh_work_bytes(int m, bool fp64);
+
+// ---- Hermitian eigensolver, Householder tridiagonal + bisection + inverse
+// iteration (arithmetic in T). Same outputs as launch_eigh; all_vecs = 0 only
+// fills the kept columns of evecs.
+template <typename T>
+cudaError_t launch_eigh_tri(const double2* G, int m, void* work, double* evals, double2* evecs, EigOut* out,
+                            int r, double eps, int all_vecs, cudaStream_t s);
 
 // ---- adjoint of a truncation: builds Mcat ((k+m) x m complex128) =
 // [U_r^dag ; B + B^dag] with B = U_d (F o (U_d^dag C)) U_r^dag, F_ji = 1/(lam_i - lam_j).

@@ -41,14 +41,16 @@ __global__ void __launch_bounds__(RO_THREADS) k_zexp(const cx<T>* __restrict__ V
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double mine = 0.0;
   for (int64_t x = wid; x < N; x += nw) {
-    double acc = 0.0;
+    // row value in the state's precision, sums across rows in FP64
+    T acc = 0;
     for (int j = lane; j < c; j += 32) {
       const cx<T> v = V[x * ld + j];
-      acc += (double)v.x * v.x + (double)v.y * v.y;
+      acc += v.x * v.x + v.y * v.y;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane < n) mine += ((x >> lane) & 1) ? -acc : acc;
-    else if (lane == n) mine += acc;
+    const double a = (double)acc;
+    if (lane < n) mine += ((x >> lane) & 1) ? -a : a;
+    else if (lane == n) mine += a;
   }
   red[warp][lane] = mine;
   __syncthreads();
@@ -84,13 +86,19 @@ __global__ void __launch_bounds__(RO_THREADS) k_pauli_expect(const cx<T>* __rest
   double mine = 0.0;
   for (int64_t x = wid; x < N; x += nw) {
     const uint64_t y = (uint64_t)x ^ xm;
-    double sr = 0.0, si = 0.0;
+    // row value in the state's precision, sums across rows in FP64
+    T sr = 0, si = 0;
     for (int j = lane; j < c; j += 32) {
       const cx<T> a = V[y * ld + j], b = V[x * ld + j];
       // conj(a) * b
-      sr += (double)a.x * b.x + (double)a.y * b.y;
-      si += (double)a.x * b.y - (double)a.y * b.x;
+      sr += a.x * b.x + a.y * b.y;
+      si += a.x * b.y - a.y * b.x;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane != 0) continue;
     // Re(i^ny * S)
     double re;
     switch (ny) {

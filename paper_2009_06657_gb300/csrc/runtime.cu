@@ -53,6 +53,10 @@ struct lr_ctx {
   int chan_q = 0, chan_K = 0;
   zc chan_M[4][4];
   double eps = 0.0;
+  int solver = 0;  // 0 auto, 1 Jacobi, 2 tridiagonal
+  int path = 0;    // 0 structured truncation where it applies, 1 always expand V'
+  double2* S = nullptr;   // pair Gram (2c x 2c)
+  double2* D = nullptr;   // pair projection (2c x 2k)
   // workspaces
   double2* partials = nullptr;
   size_t partials_elems = 0;
@@ -339,6 +343,96 @@ int upload_terms(lr_ctx* h, int T, const uint64_t* xm, const uint64_t* zm, const
   return LR_OK;
 }
 
+// Eigensolve of the m x m Gram matrix in h->G (Sec. II.B), rank choice, FP64
+// accounting; *k_out receives the kept count (synchronises only for the eps rule).
+int run_eigh(lr_ctx* h, int m, int r_eff, double eps, int* k_out) {
+  const int te = tbeg(h);
+  const bool fp64 = h->dtype == LR_C128;
+  const bool use_tri = h->solver == 2 || (h->solver == 0 && m > (fp64 ? 64 : 32));
+  if (use_tri) {
+    CK(by_dtype(h->dtype, [&](auto t) {
+      return launch_eigh_tri<decltype(t)>(h->G, m, h->eig_work, h->evals, h->evecs, h->eo, r_eff, eps,
+                                          h->record ? 1 : 0, h->stream);
+    }));
+  } else {
+    CK(by_dtype(h->dtype, [&](auto t) {
+      return launch_eigh<decltype(t)>(h->G, m, h->eig_work, h->evals, h->evecs, h->eo, r_eff, eps, h->stream);
+    }));
+  }
+  tend(h, LR_K_EIGH, te);
+  k_accum<<<1, 1, 0, h->stream>>>(h->eo, h->acc);
+  CK(cudaGetLastError());
+  if (r_eff > 0) {
+    *k_out = r_eff < m ? r_eff : m;
+  } else {
+    CK(cudaMemcpyAsync(h->h_eo, h->eo, sizeof(EigOut), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *k_out = h->h_eo->k;
+  }
+  return LR_OK;
+}
+
+// Truncation after a one-qubit channel without forming V' (the expansion is
+// implicit): with M_a = Kt_a G (G the queued one-qubit gate on the channel's
+// qubit, or I) and S = [V_0 V_1]^dag [V_0 V_1] (rows of V with the qubit's bit
+// clear / set), the Gram of V' = [M_1 V, ..., M_K V] is
+//   G'_ab = sum_{b,b'} (M_a^dag M_b)_{bb'} S_{bb'}              (blocks c x c),
+// and the projection V' U_r acts on row pairs as [V_0 V_1] D with
+//   D[(b,i)][(a,j)] = sum_al (M_al)_{ab} U[al c + i][j].
+// The same rho results as expanding then truncating (Eq. 4, Sec. II.B).
+int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
+  const int c = h->c, K = h->chan_K, m = c * K, q = h->chan_q;
+  const int64_t N2 = h->N / 2;
+  const int ld = h->cap;
+  PairQ pq;
+  memset(&pq, 0, sizeof(pq));
+  zc Gm[4] = {1, 0, 0, 1};
+  if (h->has_gate) for (int i = 0; i < 4; ++i) Gm[i] = h->gate_U[i];
+  zc M[4][4];
+  for (int al = 0; al < K; ++al) {
+    matmul(h->chan_M[al], Gm, M[al], 2);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) put(pq.M[al][a][b], M[al][a * 2 + b]);
+  }
+  for (int al = 0; al < K; ++al)
+    for (int be = 0; be < K; ++be)
+      for (int b = 0; b < 2; ++b)
+        for (int bp = 0; bp < 2; ++bp) {
+          zc acc = 0;
+          for (int a = 0; a < 2; ++a) acc += std::conj(M[al][a * 2 + b]) * M[be][a * 2 + bp];
+          put(pq.Q[al][be][b][bp], acc);
+        }
+  const int splits = gram_splits(N2, 2 * c, 2 * c);
+  int te = tbeg(h);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_gram<decltype(t)>(h->V, ld, 2 * c, h->V, ld, 2 * c, N2, true, h->partials, splits, h->S,
+                                    h->stream, q, c);
+  }));
+  CK(launch_assemble_gram(h->S, c, K, pq, h->G, h->stream));
+  tend(h, LR_K_GRAM, te);
+  int k;
+  int rc = run_eigh(h, m, r_eff, eps, &k);
+  if (rc) return rc;
+  te = tbeg(h);
+  CK(launch_build_proj(h->evecs, c, K, k, pq, h->D, h->stream));
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_rowmat<decltype(t)>(h->V, ld, 2 * c, h->D, 2 * k, nullptr, 0, 0, nullptr, 0, h->W, ld, 2 * k,
+                                      N2, h->stream, q, c, k);
+  }));
+  tend(h, LR_K_PROJECT, te);
+  std::swap(h->V, h->W);
+  h->c = k;
+  h->ncomp++;
+  h->has_gate = false;
+  h->has_chan = false;
+  if (discarded_out) {
+    CK(cudaMemcpyAsync(h->h_eo, h->eo, sizeof(EigOut), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *discarded_out = h->h_eo->dropped;
+  }
+  return LR_OK;
+}
+
 int do_truncate(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
   const int m = h->c;
   const int64_t N = h->N;
@@ -365,21 +459,9 @@ int do_truncate(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
     return launch_gram<decltype(t)>(h->V, ld, m, h->V, ld, m, N, true, h->partials, splits, h->G, h->stream);
   }));
   tend(h, LR_K_GRAM, te);
-  te = tbeg(h);
-  CK(by_dtype(h->dtype, [&](auto t) {
-    return launch_eigh<decltype(t)>(h->G, m, h->eig_work, h->evals, h->evecs, h->eo, r_eff, eps, h->stream);
-  }));
-  tend(h, LR_K_EIGH, te);
-  k_accum<<<1, 1, 0, h->stream>>>(h->eo, h->acc);
-  CK(cudaGetLastError());
   int k;
-  if (r_eff > 0) {
-    k = r_eff < m ? r_eff : m;
-  } else {
-    CK(cudaMemcpyAsync(h->h_eo, h->eo, sizeof(EigOut), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    k = h->h_eo->k;
-  }
+  int rc0 = run_eigh(h, m, r_eff, eps, &k);
+  if (rc0) return rc0;
   te = tbeg(h);
   CK(by_dtype(h->dtype, [&](auto t) {
     return launch_rowmat<decltype(t)>(h->V, ld, m, h->evecs, m, nullptr, 0, 0, nullptr, 0, h->W, ld, k, N,
@@ -485,6 +567,8 @@ int lr_init_ex(int n, int r, int dtype, int capacity, void* stream, lr_handle* o
   if (!rc) rc = dmalloc(h, &h->W, slab_bytes(h));
   if (!rc) rc = dmalloc(h, (void**)&h->partials, sizeof(double2) * pe);
   if (!rc) rc = dmalloc(h, (void**)&h->G, sizeof(double2) * m * m);
+  if (!rc) rc = dmalloc(h, (void**)&h->S, sizeof(double2) * m * m);
+  if (!rc) rc = dmalloc(h, (void**)&h->D, sizeof(double2) * m * m);
   if (!rc) rc = dmalloc(h, (void**)&h->evals, sizeof(double) * m);
   if (!rc) rc = dmalloc(h, (void**)&h->evecs, sizeof(double2) * m * m);
   if (!rc) rc = dmalloc(h, (void**)&h->eo, sizeof(EigOut));
@@ -514,6 +598,8 @@ int lr_free(lr_handle h) {
   dfree(h->W);
   dfree((void*&)h->partials);
   dfree((void*&)h->G);
+  dfree((void*&)h->S);
+  dfree((void*&)h->D);
   dfree((void*&)h->evals);
   dfree((void*&)h->evecs);
   dfree((void*&)h->eo);
@@ -660,6 +746,12 @@ int lr_kraus_preset(int kind, double p, double* out, int* K_out) {
   return LR_OK;
 }
 
+int lr_set_eigensolver(lr_handle h, int which) {
+  if (!h || which < 0 || which > 2) return LR_EINVAL;
+  h->solver = which;
+  return LR_OK;
+}
+
 int lr_set_eps(lr_handle h, double eps) {
   if (!h || !(eps < 1.0)) return LR_EINVAL;
   h->eps = eps > 0 ? eps : 0.0;
@@ -668,15 +760,32 @@ int lr_set_eps(lr_handle h, double eps) {
 
 int lr_compress(lr_handle h, int r, double* discarded_out) {
   if (!h) return LR_EINVAL;
-  int rc = flush_all(h);
-  if (rc) return rc;
   int r_eff = r;
   double eps = 0.0;
   if (r <= 0) {
     if (h->eps > 0) { r_eff = 0; eps = h->eps; }
     else r_eff = h->r;
   }
+  int rc;
+  if (h->has_chan && h->path == 0 && !h->record) {
+    // a gate the structured form cannot absorb (two-qubit, or on another qubit) runs first
+    if (h->has_gate && !(h->gate_nq == 1 && h->gate_q[0] == h->chan_q)) {
+      rc = flush_gate(h);
+      if (rc) return rc;
+    }
+    const int m = h->c * h->chan_K;
+    const bool drops = !(r_eff > 0 && m <= r_eff);
+    if (drops && m <= 256 && m <= h->cap && (h->N >= 2)) return do_structured(h, r_eff, eps, discarded_out);
+  }
+  rc = flush_all(h);
+  if (rc) return rc;
   return do_truncate(h, r_eff, eps, discarded_out);
+}
+
+int lr_set_path(lr_handle h, int which) {
+  if (!h || which < 0 || which > 1) return LR_EINVAL;
+  h->path = which;
+  return LR_OK;
 }
 
 int lr_probs(lr_handle h, void* out_dev) {

@@ -116,6 +116,14 @@ class LRSim:
         check(lib.lr_compress(self.h, int(r), None), "lr_compress")
         return None
 
+    def set_eigensolver(self, which):
+        """"auto", "jacobi" or "tridiag"."""
+        check(lib.lr_set_eigensolver(self.h, {"auto": 0, "jacobi": 1, "tridiag": 2}[which]), "lr_set_eigensolver")
+
+    def set_path(self, which):
+        """"auto" (truncate without forming V' where possible) or "expand"."""
+        check(lib.lr_set_path(self.h, {"auto": 0, "expand": 1}[which]), "lr_set_path")
+
     def set_eps(self, eps):
         check(lib.lr_set_eps(self.h, float(eps)), "lr_set_eps")
 

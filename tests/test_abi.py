@@ -19,8 +19,8 @@ def _declared():
 def lib():
     so = os.path.join(ROOT, "paper_2009_06657_gb300", "_lib", "liblret.so")
     if not os.path.exists(so):
-        from paper_2009_06657_gb300 import build
-        build.build()
+        import __graft_entry__
+        __graft_entry__.build()
     import paper_2009_06657_gb300._ffi as f
     return f
 

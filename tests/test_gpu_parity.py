@@ -15,7 +15,10 @@ from oracle import lret as O  # noqa: E402
 from workloads import hea, random_layered, random_pauli_sum  # noqa: E402
 
 TOL = {"c128": 1e-11, "c64": 1e-5}
-GAP_MIN = {"c128": 1e-8, "c64": 1e-4}
+# Relative gap (lambda_k - lambda_{k+1}) / lambda_1 required at every cut whose
+# kept eigenvalue is not negligible. Below it the truncation is not unique.
+GAP_MIN = {"c128": 1e-7, "c64": 1e-5}
+ZERO_REL = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -36,8 +39,49 @@ def _first_channels(ops, k):
 
 
 def _min_gap(st):
-    g = [e["gap"] for e in st.log if e["k"] < e["m"]]
+    """Smallest relative gap over cuts that split non-negligible eigenvalues
+    (a cut among zero eigenvalues drops no mass and leaves rho unique)."""
+    g = [e["gap"] for e in st.log
+         if e["k"] < e["m"] and e["lam"][e["k"] - 1] > ZERO_REL * e["lam"][0]]
     return min(g) if g else np.inf
+
+
+# Unit roundoff of each path's arithmetic, for the cut-sensitivity estimate.
+UNIT = {"c128": 1.1e-16, "c64": 6e-8}
+
+
+def _cut_sensitivity(st):
+    """sum over cuts of lambda_1 * lambda_k / (lambda_k - lambda_{k+1}).
+
+    A backward error e * lambda_1 in the Gram matrix rotates the kept subspace
+    by about e * lambda_1 / gap at a cut, which moves rho by about that angle
+    times lambda_k; unit roundoff times this sum predicts the truncation part
+    of the error of a correct implementation. An exact tie gives infinity
+    (several correct truncations)."""
+    tot = 0.0
+    for e in st.log:
+        k, lam = e["k"], e["lam"]
+        if k >= e["m"] or lam[k - 1] <= ZERO_REL * lam[0]:
+            continue
+        gap = lam[k - 1] - lam[k]
+        if gap <= 0:
+            return np.inf
+        tot += lam[0] * lam[k - 1] / gap
+    return tot
+
+
+# Fraction of the tolerance the predicted truncation error may take.
+SENS_BUDGET = {"c128": 0.1, "c64": 1.0}
+
+
+def _pick(n, r, depth, noise, seed, dtype, tries=24):
+    """First seed >= `seed` whose predicted truncation error fits the tolerance budget."""
+    for s in range(seed, seed + tries):
+        ops = random_layered(n, depth, seed=s, noise=noise, qubit_jitter=(0.5, 1.5))
+        ref = O.run_lret(n, ops, r=r)
+        if UNIT[dtype] * _cut_sensitivity(ref) < SENS_BUDGET[dtype] * TOL[dtype]:
+            return ops, ref, s
+    pytest.skip("no seed with well-separated cuts")
 
 
 def _compare(lr, sim, ref, n, terms, tol):
@@ -78,39 +122,87 @@ def test_two_qubit_orientation_and_edge_qubits(lr, dtype):
 
 
 CIRCUITS = [
-    # (n, r, depth, noise, seed): config-1 family at full size, and larger tiles with ragged tails
+    # (n, r, depth, noise, seed): the 6-qubit family at full depth, and larger
+    # shapes whose column counts span several 64-wide tiles with ragged tails
     (6, 13, 40, ("dep", 0.0033), 1000),
     (8, 20, 3, ("mixed", 1e-2, 2e-2), 1001),
     (10, 24, 2, ("mixed", 1e-3, 2e-3), 1002),
     (7, 60, 2, ("dep", 5e-3), 1003),
+    (12, 32, 2, ("mixed", 1e-3, 2e-3), 2000),
 ]
 
 
+@pytest.mark.parametrize("solver", ["auto", "jacobi", "tridiag"])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("case", CIRCUITS, ids=[f"n{c[0]}r{c[1]}d{c[2]}" for c in CIRCUITS])
-def test_truncated_circuit_parity(lr, dtype, case):
+def test_truncated_circuit_parity(lr, dtype, case, solver):
     n, r, depth, noise, seed = case
-    if dtype == "c128" and r > 32 and n > 6:
-        pytest.skip("FP64 Jacobi at m > 128 is slow on this part; covered by c64")
-    ops = random_layered(n, depth, seed=seed, noise=noise)
-    ref = O.run_lret(n, ops, r=r)
-    if _min_gap(ref) < GAP_MIN[dtype]:
-        pytest.skip(f"tie at a cut (gap {_min_gap(ref):.2e}): several correct results")
+    if dtype == "c128" and solver != "tridiag" and 4 * r > 128:
+        pytest.skip("FP64 Jacobi above 128 columns runs at the FP64 rate of this part; tridiagonal path covers it")
+    if solver == "jacobi" and dtype == "c64" and 4 * r > 128:
+        pytest.skip("FP32 Jacobi above 128 columns is the slow reference solver")
+    if dtype == "c64":
+        depth = 1  # FP32 rounding at deep near-tied cuts alone would approach the tolerance
+    ops, ref, _ = _pick(n, r, depth, noise, seed, dtype)
     sim = lr.LRSim(n, r, dtype=dtype)
+    sim.set_eigensolver(solver)
     lr.run_ops(sim, ops, r=r)
     terms = random_pauli_sum(n, 16, seed=seed + 7)
-    _compare(lr, sim, ref, n, terms, TOL[dtype] * (10 if dtype == "c64" and depth > 10 else 1))
+    _compare(lr, sim, ref, n, terms, TOL[dtype])
     info = sim.info()
     assert abs(info["discarded"] - ref.discarded) < TOL[dtype]
     assert info["converged"]
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("case", CIRCUITS, ids=[f"n{c[0]}r{c[1]}d{c[2]}" for c in CIRCUITS])
+def test_structured_truncation_matches_oracle_and_expanded(lr, dtype, case):
+    """The truncation without forming V' (Gram from row pairs, projection on
+    row pairs) gives the oracle's rho, like the path that expands V' first."""
+    n, r, depth, noise, seed = case
+    if dtype == "c64":
+        depth = 1
+    ops, ref, _ = _pick(n, r, depth, noise, seed, dtype)
+    terms = random_pauli_sum(n, 16, seed=seed + 7)
+    probs = {}
+    for path in ("auto", "expand"):
+        sim = lr.LRSim(n, r, dtype=dtype)
+        sim.set_path(path)
+        lr.run_ops(sim, ops, r=r)
+        _compare(lr, sim, ref, n, terms, TOL[dtype])
+        assert abs(sim.info()["discarded"] - ref.discarded) < TOL[dtype]
+        probs[path] = sim.probs().double().cpu().numpy()
+    assert np.sum(np.abs(probs["auto"] - probs["expand"])) < TOL[dtype]
+
+
+def test_six_qubit_workload_within_discarded_mass_of_exact(lr):
+    """The 6-qubit, r = 13, depth-40 workload as specified (identical channels on
+    every qubit). Its early cuts fall inside exact eigenvalue ties, so the
+    truncated rho is not unique. What every correct run satisfies: a truncation
+    moves rho by exactly its discarded mass in trace norm (Eckart-Young, Sec.
+    II.B) and the channels and gates after it do not increase trace distance, so
+    the L1 distance of Prob(x) to the exact evolution (Eq. 1) is at most the
+    cumulative discarded mass, and Tr rho = 1 - that mass."""
+    n, r = 6, 13
+    ops = random_layered(n, 40, seed=1000, noise=("dep", 0.0033))
+    fdm = O.run_fdm(n, ops)
+    ref = O.run_lret(n, ops, r=r)
+    assert np.sum(np.abs(ref.probs() - fdm.probs())) <= ref.discarded + 1e-12
+    for dtype, tol in (("c128", 1e-11), ("c64", 1e-5)):
+        sim = lr.LRSim(n, r, dtype=dtype)
+        lr.run_ops(sim, ops, r=r)
+        p = sim.probs().double().cpu().numpy()
+        d = sim.info()["discarded"]
+        assert np.sum(np.abs(p - fdm.probs())) <= d + tol
+        assert abs(p.sum() - (1.0 - d)) < tol
+        assert 0.5 * ref.discarded < d < 2.0 * ref.discarded
+
+
 def test_eps_threshold_policy(lr):
     n, eps = 6, 1e-3
-    ops = random_layered(n, 3, seed=1200, noise=("dep", 0.01))
+    ops = random_layered(n, 3, seed=1200, noise=("dep", 0.01), qubit_jitter=(0.5, 1.5))
     ref = O.run_lret(n, ops, eps=eps)
-    if _min_gap(ref) < 1e-8:
-        pytest.skip("tie at a cut")
+    assert _min_gap(ref) > 1e-8
     sim = lr.LRSim(n, 64, dtype="c128")
     sim.set_eps(eps)
     lr.run_ops(sim, ops, r=0)
@@ -167,22 +259,41 @@ def _grad_gpu(lr, n, ops, th, terms, r, dtype, ckpt):
     t = torch.tensor(th, requires_grad=True)
     v = lr.LRExpectation.apply(t, sim, ops, terms, r, ckpt)
     v.backward()
-    return float(v), t.grad.numpy().copy()
+    return float(v.detach()), t.grad.numpy().copy()
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_gradient_matches_finite_differences(lr, dtype):
     n, r = 4, 6
-    ops, th = hea(n, 2, seed=4000, noise=("dep", 1e-2))
+    ops, th = hea(n, 2, seed=4000, noise=("dep", 1e-2), qubit_jitter=(0.5, 1.5))
     terms = random_pauli_sum(n, 10, seed=4001)
     ref = O.run_lret(n, ops, r=r)
-    if _min_gap(ref) < 1e-6:
-        pytest.skip("tie at a cut")
+    assert _min_gap(ref) > 1e-6
     v, g = _grad_gpu(lr, n, ops, th, terms, r, dtype, 4)
     g_fd = O.gradient_fd_lret(n, ops, th, terms, r=r, h=1e-4)
     assert abs(v - ref.expect(terms)) < (1e-11 if dtype == "c128" else 1e-5)
     tol = 1e-7 if dtype == "c128" else 2e-4
     assert np.max(np.abs(g - g_fd)) < tol, np.max(np.abs(g - g_fd))
+
+
+def test_gradient_tridiagonal_solver_matches_jacobi(lr):
+    n, r = 5, 12  # 48-column Gram matrices: both solvers apply
+    ops, th = hea(n, 2, seed=4300, noise=("dep", 5e-3), qubit_jitter=(0.5, 1.5))
+    terms = random_pauli_sum(n, 8, seed=4301)
+    ref = O.run_lret(n, ops, r=r)
+    assert _min_gap(ref) > 1e-6
+    import torch
+    out = {}
+    for solver in ("jacobi", "tridiag"):
+        sim = lr.LRSim(n, r, dtype="c128")
+        sim.set_eigensolver(solver)
+        t = torch.tensor(th, requires_grad=True)
+        v = lr.LRExpectation.apply(t, sim, ops, terms, r, 4)
+        v.backward()
+        out[solver] = t.grad.numpy().copy()
+    g_fd = O.gradient_fd_lret(n, ops, th, terms, r=r, h=1e-4)
+    assert np.max(np.abs(out["jacobi"] - g_fd)) < 1e-7
+    assert np.max(np.abs(out["tridiag"] - g_fd)) < 1e-7
 
 
 def test_gradient_full_rank_matches_parameter_shift(lr):
@@ -196,7 +307,7 @@ def test_gradient_full_rank_matches_parameter_shift(lr):
 
 def test_gradient_checkpoint_interval_is_bitwise_invariant(lr):
     n, r = 5, 8
-    ops, th = hea(n, 2, seed=4200, noise=("dep", 5e-3))
+    ops, th = hea(n, 2, seed=4200, noise=("dep", 5e-3), qubit_jitter=(0.5, 1.5))
     terms = random_pauli_sum(n, 8, seed=4201)
     gs = [_grad_gpu(lr, n, ops, th, terms, r, "c64", ck)[1] for ck in (1, 8, 0)]
     assert np.array_equal(gs[0], gs[1]) and np.array_equal(gs[0], gs[2])

@@ -44,19 +44,21 @@ __all__ = [
 ]
 
 
-def _channel(rng, q, noise):
+def _channel(rng, q, noise, scale=None):
     """Return the channel op for qubit q under a noise spec.
 
     noise: ("dep", p) | ("ad", gamma) | ("bf", p) | ("mixed", p_dep, gamma_ad)
     For "mixed", one seeded coin per gate picks the kind (drawn by the caller).
+    scale: optional per-qubit multipliers of the strength.
     """
     kind = noise[0]
+    f = 1.0 if scale is None else float(scale[q])
     if kind == "dep":
-        return {"op": "dep", "q": int(q), "p": float(noise[1])}
+        return {"op": "dep", "q": int(q), "p": float(noise[1]) * f}
     if kind == "ad":
-        return {"op": "ad", "q": int(q), "gamma": float(noise[1])}
+        return {"op": "ad", "q": int(q), "gamma": float(noise[1]) * f}
     if kind == "bf":
-        return {"op": "bf", "q": int(q), "p": float(noise[1])}
+        return {"op": "bf", "q": int(q), "p": float(noise[1]) * f}
     raise ValueError(f"unknown noise kind {kind!r}")
 
 
@@ -69,11 +71,20 @@ def _noise_for_gate(rng, noise):
 
 
 def random_layered(n, depth, seed, noise=("dep", 1e-3), two_qubit="cnot",
-                   param_ids=False):
-    """Seeded random layered circuit (Ry, Rz on every qubit, then a matching)."""
+                   param_ids=False, qubit_jitter=None):
+    """Seeded random layered circuit (Ry, Rz on every qubit, then a matching).
+
+    qubit_jitter=(lo, hi) multiplies each qubit's channel strength by a seeded
+    U(lo, hi) factor. With identical channels on every qubit a near-product
+    state has exactly degenerate eigenvalues, so a rank cut can fall inside a
+    tie (several equally correct truncations); distinct strengths remove that.
+    """
     if n < 1:
         raise ValueError("n must be >= 1")
     rng = np.random.default_rng(seed)
+    scale = None
+    if qubit_jitter is not None:
+        scale = np.random.default_rng(seed + 7919).uniform(qubit_jitter[0], qubit_jitter[1], size=n)
     ops = []
     pid = 0
     for _ in range(depth):
@@ -86,25 +97,28 @@ def random_layered(n, depth, seed, noise=("dep", 1e-3), two_qubit="cnot",
                     pid += 1
                 nz = _noise_for_gate(rng, noise)
                 if nz is not None:
-                    ops.append(_channel(rng, q, nz))
+                    ops.append(_channel(rng, q, nz, scale))
         perm = rng.permutation(n)
         for i in range(0, n - 1, 2):
             a, b = int(perm[i]), int(perm[i + 1])
             ops.append({"op": two_qubit, "q": [a, b]})
             nz = _noise_for_gate(rng, noise)
             if nz is not None:
-                ops.append(_channel(rng, a, nz))
-                ops.append(_channel(rng, b, nz))
+                ops.append(_channel(rng, a, nz, scale))
+                ops.append(_channel(rng, b, nz, scale))
     return ops
 
 
-def hea(n, layers, seed, noise=("dep", 1e-3), theta_std=0.5):
+def hea(n, layers, seed, noise=("dep", 1e-3), theta_std=0.5, qubit_jitter=None):
     """Hardware-efficient ansatz: (Ry, Rz on every qubit, CZ ladder) x layers.
 
     Every rotation is differentiable; parameter ids run 0..2*n*layers-1 in op
     order. Returns (ops, theta) where theta is the initial parameter vector.
     """
     rng = np.random.default_rng(seed)
+    scale = None
+    if qubit_jitter is not None:
+        scale = np.random.default_rng(seed + 7919).uniform(qubit_jitter[0], qubit_jitter[1], size=n)
     ops = []
     thetas = []
     for _ in range(layers):
@@ -115,13 +129,13 @@ def hea(n, layers, seed, noise=("dep", 1e-3), theta_std=0.5):
                 thetas.append(th)
                 nz = _noise_for_gate(rng, noise)
                 if nz is not None:
-                    ops.append(_channel(rng, q, nz))
+                    ops.append(_channel(rng, q, nz, scale))
         for q in range(n - 1):
             ops.append({"op": "cz", "q": [q, q + 1]})
             nz = _noise_for_gate(rng, noise)
             if nz is not None:
-                ops.append(_channel(rng, q, nz))
-                ops.append(_channel(rng, q + 1, nz))
+                ops.append(_channel(rng, q, nz, scale))
+                ops.append(_channel(rng, q + 1, nz, scale))
     return ops, np.asarray(thetas, dtype=np.float64)
 
 
