@@ -175,8 +175,58 @@ int lr_get_info(lr_handle h, lr_info* info);
  * queued work and synchronises. */
 int lr_get_state(lr_handle h, void* out_host);
 
+/* Diagnostics of the last eigensolve: Jacobi sweeps (0 for the tridiagonal
+ * solver) and SM clock cycles spent in its phases (tridiagonal solver:
+ * reduction, bisection, sort/accounting, inverse iteration, back-transform;
+ * six entries, unused ones 0). Synchronises. */
+int lr_last_eig_stats(lr_handle h, int* sweeps_out, long long* cycles_out);
+
 /* Upper bound on the device bytes the handle holds (for capacity planning). */
 int64_t lr_device_bytes(lr_handle h);
+
+/* ---- Batched execution of many independent circuits -------------------------
+ * Not in the paper: many circuits of uneven n, r and depth advance together,
+ * stage s of every circuit in the same launches, the whole schedule captured
+ * in one CUDA graph. Semantics per circuit are those of the single-circuit
+ * calls with a truncation to rank r after every channel (fixed rank). */
+#define LR_OP_RX 0
+#define LR_OP_RY 1
+#define LR_OP_RZ 2
+#define LR_OP_CNOT 3   /* q0 = control, q1 = target */
+#define LR_OP_CZ 4
+#define LR_OP_DEP 5    /* p = depolarizing probability */
+#define LR_OP_AD 6     /* p = amplitude-damping gamma */
+#define LR_OP_BF 7     /* p = bit-flip probability */
+typedef struct lr_op {
+  int kind;
+  int q0, q1;
+  double theta;  /* rotation angle */
+  double p;      /* channel strength */
+} lr_op;
+typedef struct lr_circuit {
+  int n;         /* qubits, 2..30 */
+  int r;         /* rank, 4r <= 256 */
+  int nops;
+  const lr_op* ops;
+} lr_circuit;
+typedef struct lr_batch* lr_batch_handle;
+
+/* Lower, allocate, upload the task tables and (use_graph != 0) capture the
+ * schedule into one CUDA graph. rows_per_split sets the Gram split size
+ * (<= 0: 4096). Every circuit starts in |0...0>. */
+int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_per_split, int use_graph,
+                    void* stream, lr_batch_handle* out);
+/* Run the whole schedule once (one graph launch). Asynchronous. */
+int lr_batch_run(lr_batch_handle b);
+/* Put every circuit back into |0...0> with zero discarded mass. Synchronises. */
+int lr_batch_reset(lr_batch_handle b);
+/* Per-circuit state after a run (columns, discarded mass, truncations). Synchronises. */
+int lr_batch_info(lr_batch_handle b, int i, lr_info* info);
+/* Prob(x) of circuit i into a caller-owned device buffer (float for LR_C64). */
+int lr_batch_probs(lr_batch_handle b, int i, void* out_dev);
+/* Totals: gates, truncations, schedule steps, kernel launches per run. */
+int lr_batch_stats(lr_batch_handle b, int64_t* gates, int64_t* truncations, int64_t* steps, int64_t* launches);
+int lr_batch_free(lr_batch_handle b);
 
 /* Kernel classes for lr_kernel_times. */
 #define LR_K_EXPAND 0   /* gate + Kraus expansion (Eqs. 3-4) */

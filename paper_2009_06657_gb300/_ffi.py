@@ -41,6 +41,17 @@ class lr_info(C.Structure):
                 ("last_gap", C.c_double)]
 
 
+class lr_op(C.Structure):
+    _fields_ = [("kind", C.c_int), ("q0", C.c_int), ("q1", C.c_int), ("theta", C.c_double), ("p", C.c_double)]
+
+
+class lr_circuit(C.Structure):
+    _fields_ = [("n", C.c_int), ("r", C.c_int), ("nops", C.c_int), ("ops", C.POINTER(lr_op))]
+
+
+OP_KIND = {"rx": 0, "ry": 1, "rz": 2, "cnot": 3, "cz": 4, "dep": 5, "ad": 6, "bf": 7}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -79,8 +90,17 @@ _SIGS = {
     "lr_get_info": (C.c_int, [_H, C.POINTER(lr_info)]),
     "lr_get_state": (C.c_int, [_H, _P]),
     "lr_device_bytes": (C.c_int64, [_H]),
+    "lr_last_eig_stats": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "lr_set_timing": (C.c_int, [_H, C.c_int]),
     "lr_kernel_times": (C.c_int, [_H, _D, C.POINTER(C.c_int64)]),
+    "lr_batch_create": (C.c_int, [C.POINTER(lr_circuit), C.c_int, C.c_int, C.c_int, C.c_int, _P, C.POINTER(_H)]),
+    "lr_batch_run": (C.c_int, [_H]),
+    "lr_batch_reset": (C.c_int, [_H]),
+    "lr_batch_info": (C.c_int, [_H, C.c_int, C.POINTER(lr_info)]),
+    "lr_batch_probs": (C.c_int, [_H, C.c_int, _P]),
+    "lr_batch_stats": (C.c_int, [_H, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int64)]),
+    "lr_batch_free": (C.c_int, [_H]),
     "lr_status_string": (C.c_char_p, [C.c_int]),
 }
 

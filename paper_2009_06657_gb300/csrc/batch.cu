@@ -1,0 +1,493 @@
+// Batched execution of many independent noisy circuits (uneven n, r, depth).
+//
+// Each circuit is lowered once on the host into a list of stages with the
+// same semantics as the single-circuit runtime (Alg. 1 with one-qubit Kraus
+// groups, fixed rank): an expansion stage (a gate alone, or a channel whose
+// expanded column count still fits the rank) or a truncation stage (a channel
+// and, folded into it, a one-qubit gate on the same qubit; Gram of the row
+// pairs, eigensolve, projection on the row pairs). Stage s of every circuit
+// runs in the same batched launches: one expansion launch, then the truncation
+// launches (pair Gram + assembly, one eigensolver block per circuit,
+// projection + accounting). Per-step task tables and block-to-task prefix
+// tables are built and uploaded once; the whole schedule is captured into one
+// CUDA graph, so a run is a single graph launch.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+#include "lret.h"
+
+using namespace lret;
+using zc = std::complex<double>;
+
+namespace {
+
+struct Circ {
+  int n = 0, r = 0, cap = 0;
+  int64_t N = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;   // buffer holding the state after the whole schedule
+  int c = 1;     // columns after the whole schedule
+  int splits = 1;
+  double* acc = nullptr;
+  double2 *partials = nullptr, *G = nullptr, *evecs = nullptr, *D = nullptr;
+  double* evals = nullptr;
+  EigOut* eo = nullptr;
+  void* eigwork = nullptr;
+  int64_t gates = 0, truncs = 0;
+};
+
+struct Step {
+  int e_off = 0, e_cnt = 0, e_blocks = 0, eb_off = 0;
+  int t_off = 0, t_cnt = 0, gram_blocks = 0, proj_blocks = 0, gb_off = 0, pb_off = 0, max_m2 = 0, max_d = 0;
+};
+
+thread_local char b_errmsg[256];
+
+void rot(int axis, double th, zc U[4]) {
+  const zc I(0, 1);
+  zc S[4];
+  if (axis == 0) { S[0] = 0; S[1] = 1; S[2] = 1; S[3] = 0; }
+  else if (axis == 1) { S[0] = 0; S[1] = -I; S[2] = I; S[3] = 0; }
+  else { S[0] = 1; S[1] = 0; S[2] = 0; S[3] = -1; }
+  const double cs = std::cos(th / 2), sn = std::sin(th / 2);
+  for (int i = 0; i < 4; ++i) U[i] = ((i == 0 || i == 3) ? cs : 0.0) - I * sn * S[i];
+}
+
+void mm2(const zc* A, const zc* B, zc* C) {
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) C[i * 2 + j] = A[i * 2] * B[j] + A[i * 2 + 1] * B[2 + j];
+}
+
+void put(double2& d, zc v) { d = make_double2(v.real(), v.imag()); }
+
+}  // namespace
+
+struct lr_batch {
+  int count = 0, dtype = 0;
+  cudaStream_t stream = nullptr;
+  size_t esz = 0;
+  std::vector<Circ> circ;
+  std::vector<Step> steps;
+  ExpandTask* d_et = nullptr;
+  TruncTask* d_tt = nullptr;
+  int* d_bs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int use_graph = 1;
+  int64_t launches = 0, gates = 0, truncs = 0, expands = 0;
+  size_t bytes = 0;
+};
+
+#define BCK(call)                                                                      \
+  do {                                                                                 \
+    cudaError_t _e = (call);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      snprintf(b_errmsg, sizeof(b_errmsg), "%s: %s", #call, cudaGetErrorString(_e));   \
+      return LR_ECUDA;                                                                 \
+    }                                                                                  \
+  } while (0)
+
+namespace {
+
+int bmalloc(lr_batch* b, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    *p = nullptr;
+    return LR_ENOMEM;
+  }
+  b->bytes += bytes;
+  return LR_OK;
+}
+
+template <typename F>
+cudaError_t by_dt(int dtype, F f) {
+  if (dtype == LR_C64) return f(float());
+  return f(double());
+}
+
+// Lowered stage of one circuit.
+struct HStage {
+  int type;        // 0 expansion, 1 truncation
+  int G, K, q;     // group rows; Kraus count; qubit (pair bit) for truncation
+  int bits[2];
+  int c_in, c_out;
+  zc M[4][4][4];   // expansion: M[al][a][g]; truncation: M[al][a][b] (2x2)
+};
+
+int lower(const lr_circuit& cd, std::vector<HStage>& out, int64_t* gates) {
+  const int n = cd.n, r = cd.r;
+  int c = 1;
+  bool pend = false;
+  int pnq = 0, pq[2] = {0, 0};
+  zc pU[16];
+  *gates = 0;
+  auto emit_gate = [&]() {
+    HStage st{};
+    st.type = 0;
+    st.G = 1 << pnq;
+    st.K = 1;
+    st.bits[0] = pq[0];
+    st.bits[1] = pnq == 2 ? pq[1] : 0;
+    st.c_in = st.c_out = c;
+    for (int a = 0; a < st.G; ++a)
+      for (int g = 0; g < st.G; ++g) st.M[0][a][g] = pU[a * st.G + g];
+    out.push_back(st);
+    pend = false;
+  };
+  for (int i = 0; i < cd.nops; ++i) {
+    const lr_op& o = cd.ops[i];
+    if (o.kind <= LR_OP_CZ) {
+      if (o.q0 < 0 || o.q0 >= n) return LR_EINVAL;
+      if (o.kind >= LR_OP_CNOT && (o.q1 < 0 || o.q1 >= n || o.q1 == o.q0)) return LR_EINVAL;
+      if (pend) emit_gate();
+      ++*gates;
+      if (o.kind <= LR_OP_RZ) {
+        pnq = 1;
+        pq[0] = o.q0;
+        rot(o.kind - LR_OP_RX, o.theta, pU);
+      } else {
+        pnq = 2;
+        pq[0] = o.q0;
+        pq[1] = o.q1;
+        for (int k = 0; k < 16; ++k) pU[k] = 0;
+        if (o.kind == LR_OP_CNOT) { pU[0] = pU[5] = 1; pU[11] = pU[14] = 1; }
+        else { pU[0] = pU[5] = pU[10] = 1; pU[15] = -1; }
+      }
+      pend = true;
+    } else if (o.kind <= LR_OP_BF) {
+      if (o.q0 < 0 || o.q0 >= n) return LR_EINVAL;
+      double kr[32];
+      int K = 0;
+      const int kind = o.kind == LR_OP_DEP ? LR_DEPOLARIZING : (o.kind == LR_OP_AD ? LR_AMPLITUDE_DAMPING : LR_BIT_FLIP);
+      if (lr_kraus_preset(kind, o.p, kr, &K) != LR_OK) return LR_EINVAL;
+      const int q = o.q0;
+      if (pend && !(pnq == 1 && pq[0] == q)) emit_gate();
+      zc Gm[4] = {1, 0, 0, 1};
+      if (pend) for (int k = 0; k < 4; ++k) Gm[k] = pU[k];
+      HStage st{};
+      st.K = K;
+      st.q = q;
+      st.G = 2;
+      st.bits[0] = q;
+      for (int al = 0; al < K; ++al) {
+        zc Kd[4], M[4];
+        for (int k = 0; k < 4; ++k) Kd[k] = zc(kr[al * 8 + 2 * k], kr[al * 8 + 2 * k + 1]);
+        mm2(Kd, Gm, M);
+        for (int a = 0; a < 2; ++a)
+          for (int g = 0; g < 2; ++g) st.M[al][a][g] = M[a * 2 + g];
+      }
+      st.c_in = c;
+      if (c * K <= r) {
+        st.type = 0;
+        st.c_out = c * K;
+      } else {
+        st.type = 1;
+        st.c_out = r;
+      }
+      c = st.c_out;
+      out.push_back(st);
+      pend = false;
+    } else {
+      return LR_EINVAL;
+    }
+  }
+  if (pend) emit_gate();
+  return LR_OK;
+}
+
+int init_states(lr_batch* b) {
+  for (auto& C : b->circ) {
+    BCK(cudaMemsetAsync(C.buf[0], 0, (size_t)C.N * C.cap * b->esz, b->stream));
+    if (b->dtype == LR_C64) {
+      const float one[2] = {1.f, 0.f};
+      BCK(cudaMemcpyAsync(C.buf[0], one, sizeof(one), cudaMemcpyHostToDevice, b->stream));
+    } else {
+      const double one[2] = {1.0, 0.0};
+      BCK(cudaMemcpyAsync(C.buf[0], one, sizeof(one), cudaMemcpyHostToDevice, b->stream));
+    }
+    BCK(cudaMemsetAsync(C.acc, 0, sizeof(double) * 8, b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  return LR_OK;
+}
+
+int enqueue(lr_batch* b) {
+  const int dt = b->dtype;
+  for (const Step& st : b->steps) {
+    if (st.e_cnt) {
+      BCK(by_dt(dt, [&](auto t) {
+        return launch_expand_batch<decltype(t)>(b->d_et + st.e_off, b->d_bs + st.eb_off, st.e_blocks, st.e_cnt,
+                                                b->stream);
+      }));
+    }
+    if (st.t_cnt) {
+      const TruncTask* tt = b->d_tt + st.t_off;
+      BCK(by_dt(dt, [&](auto t) {
+        return launch_trunc_batch_gemms<decltype(t)>(tt, b->d_bs + st.gb_off, st.gram_blocks, b->d_bs + st.pb_off,
+                                                     st.proj_blocks, st.t_cnt, st.max_m2, st.max_d, 0, b->stream);
+      }));
+      BCK(by_dt(dt, [&](auto t) { return launch_eigh_tri_batch<decltype(t)>(tt, st.t_cnt, b->stream); }));
+      BCK(by_dt(dt, [&](auto t) {
+        return launch_trunc_batch_gemms<decltype(t)>(tt, b->d_bs + st.gb_off, st.gram_blocks, b->d_bs + st.pb_off,
+                                                     st.proj_blocks, st.t_cnt, st.max_m2, st.max_d, 1, b->stream);
+      }));
+    }
+  }
+  return LR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lr_batch_free(lr_batch_handle b) {
+  if (!b) return LR_EINVAL;
+  cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto& C : b->circ) {
+    for (int i = 0; i < 2; ++i) if (C.buf[i]) cudaFree(C.buf[i]);
+    void* ps[] = {C.acc, C.partials, C.G, C.evecs, C.D, C.evals, C.eo, C.eigwork};
+    for (void* p : ps) if (p) cudaFree(p);
+  }
+  if (b->d_et) cudaFree(b->d_et);
+  if (b->d_tt) cudaFree(b->d_tt);
+  if (b->d_bs) cudaFree(b->d_bs);
+  delete b;
+  return LR_OK;
+}
+
+int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_per_split, int use_graph,
+                    void* stream, lr_batch_handle* out) {
+  if (!out || !circuits || count < 1 || (dtype != LR_C64 && dtype != LR_C128)) return LR_EINVAL;
+  *out = nullptr;
+  if (rows_per_split <= 0) rows_per_split = 4096;
+  lr_batch* b = new lr_batch();
+  b->count = count;
+  b->dtype = dtype;
+  b->stream = (cudaStream_t)stream;
+  b->esz = dtype == LR_C64 ? sizeof(float2) : sizeof(double2);
+  b->use_graph = use_graph;
+  b->circ.resize(count);
+  std::vector<std::vector<HStage>> stages(count);
+  size_t max_stages = 0;
+  int rc = LR_OK;
+  for (int i = 0; i < count && !rc; ++i) {
+    const lr_circuit& cd = circuits[i];
+    if (cd.n < 2 || cd.n > 30 || cd.r < 1 || 4 * cd.r > 256 || cd.nops < 0 || (cd.nops > 0 && !cd.ops)) {
+      rc = LR_EINVAL;
+      break;
+    }
+    Circ& C = b->circ[i];
+    C.n = cd.n;
+    C.r = cd.r;
+    C.cap = 4 * cd.r + ((4 * cd.r) & 1);
+    C.N = 1ll << cd.n;
+    rc = lower(cd, stages[i], &C.gates);
+    if (rc) break;
+    b->gates += C.gates;
+    max_stages = std::max(max_stages, stages[i].size());
+    const int64_t N2 = C.N / 2;
+    int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, N2 / rows_per_split));
+    C.splits = splits;
+    const int m = 4 * cd.r, c2 = 2 * cd.r;
+    const size_t slab = (size_t)C.N * C.cap * b->esz;
+    rc = bmalloc(b, &C.buf[0], slab);
+    if (!rc) rc = bmalloc(b, &C.buf[1], slab);
+    if (!rc) rc = bmalloc(b, (void**)&C.acc, sizeof(double) * 8);
+    if (!rc) rc = bmalloc(b, (void**)&C.partials, sizeof(double2) * (size_t)splits * c2 * c2);
+    if (!rc) rc = bmalloc(b, (void**)&C.G, sizeof(double2) * (size_t)m * m);
+    if (!rc) rc = bmalloc(b, (void**)&C.evecs, sizeof(double2) * (size_t)m * m);
+    if (!rc) rc = bmalloc(b, (void**)&C.D, sizeof(double2) * (size_t)c2 * c2);
+    if (!rc) rc = bmalloc(b, (void**)&C.evals, sizeof(double) * m);
+    if (!rc) rc = bmalloc(b, (void**)&C.eo, sizeof(EigOut));
+    if (!rc) rc = bmalloc(b, &C.eigwork, eigh_work_bytes(m, dtype == LR_C128));
+  }
+  if (rc) {
+    lr_batch_free(b);
+    return rc;
+  }
+  // step-major task tables
+  std::vector<ExpandTask> et;
+  std::vector<TruncTask> tt;
+  std::vector<int> bs;
+  b->steps.resize(max_stages);
+  for (size_t s = 0; s < max_stages; ++s) {
+    Step& S = b->steps[s];
+    S.e_off = (int)et.size();
+    S.t_off = (int)tt.size();
+    std::vector<int> eblocks, gblocks, pblocks;
+    for (int i = 0; i < count; ++i) {
+      if (s >= stages[i].size()) continue;
+      const HStage& h = stages[i][s];
+      Circ& C = b->circ[i];
+      if (h.type == 0) {
+        ExpandTask e{};
+        e.V = C.buf[C.cur];
+        e.W = C.buf[C.cur ^ 1];
+        e.total = (C.N / h.G) * (int64_t)h.c_in;
+        e.c = h.c_in;
+        e.ld = C.cap;
+        e.G = h.G;
+        e.K = h.K;
+        e.bits[0] = h.bits[0];
+        e.bits[1] = h.bits[1];
+        for (int al = 0; al < h.K; ++al)
+          for (int a = 0; a < h.G; ++a)
+            for (int g = 0; g < h.G; ++g) put(e.M[(al * h.G + a) * h.G + g], h.M[al][a][g]);
+        et.push_back(e);
+        eblocks.push_back(expand_blocks(e.total));
+        ++b->expands;
+      } else {
+        TruncTask t{};
+        t.V = C.buf[C.cur];
+        t.W = C.buf[C.cur ^ 1];
+        t.N2 = C.N / 2;
+        t.splits = C.splits;
+        t.chunk = trunc_chunk(t.N2, C.splits);
+        t.c = h.c_in;
+        t.ld = C.cap;
+        t.K = h.K;
+        t.k = h.c_out;
+        t.q = h.q;
+        t.tiles = trunc_tiles(h.c_in);
+        t.m = h.K * h.c_in;
+        for (int al = 0; al < h.K; ++al)
+          for (int a = 0; a < 2; ++a)
+            for (int g = 0; g < 2; ++g) put(t.M[al][a][g], h.M[al][a][g]);
+        t.partials = C.partials;
+        t.G = C.G;
+        t.evals = C.evals;
+        t.evecs = C.evecs;
+        t.eo = C.eo;
+        t.eigwork = C.eigwork;
+        t.D = C.D;
+        t.acc = C.acc;
+        tt.push_back(t);
+        gblocks.push_back(t.tiles * t.splits);
+        pblocks.push_back(trunc_proj_blocks(t.N2, t.k));
+        S.max_m2 = std::max(S.max_m2, t.m * t.m);
+        S.max_d = std::max(S.max_d, 4 * t.c * t.k);
+        ++C.truncs;
+        ++b->truncs;
+      }
+      C.cur ^= 1;
+      C.c = h.c_out;
+    }
+    S.e_cnt = (int)et.size() - S.e_off;
+    S.t_cnt = (int)tt.size() - S.t_off;
+    auto prefix = [&](const std::vector<int>& v, int* off, int* total) {
+      *off = (int)bs.size();
+      int acc = 0;
+      for (int x : v) { bs.push_back(acc); acc += x; }
+      bs.push_back(acc);
+      *total = acc;
+    };
+    if (S.e_cnt) prefix(eblocks, &S.eb_off, &S.e_blocks);
+    if (S.t_cnt) {
+      prefix(gblocks, &S.gb_off, &S.gram_blocks);
+      prefix(pblocks, &S.pb_off, &S.proj_blocks);
+    }
+    b->launches += (S.e_cnt ? 1 : 0) + (S.t_cnt ? 6 : 0);
+  }
+  rc = bmalloc(b, (void**)&b->d_et, sizeof(ExpandTask) * std::max<size_t>(1, et.size()));
+  if (!rc) rc = bmalloc(b, (void**)&b->d_tt, sizeof(TruncTask) * std::max<size_t>(1, tt.size()));
+  if (!rc) rc = bmalloc(b, (void**)&b->d_bs, sizeof(int) * std::max<size_t>(1, bs.size()));
+  if (rc) {
+    lr_batch_free(b);
+    return rc;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!et.empty()) e = cudaMemcpy(b->d_et, et.data(), sizeof(ExpandTask) * et.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !tt.empty())
+    e = cudaMemcpy(b->d_tt, tt.data(), sizeof(TruncTask) * tt.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !bs.empty()) e = cudaMemcpy(b->d_bs, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = by_dt(dtype, [&](auto t) { return prepare_eigh_tri_batch<decltype(t)>(); });
+  if (e != cudaSuccess) {
+    snprintf(b_errmsg, sizeof(b_errmsg), "batch setup: %s", cudaGetErrorString(e));
+    lr_batch_free(b);
+    return LR_ECUDA;
+  }
+  rc = init_states(b);
+  if (!rc && use_graph) {
+    // the whole schedule becomes one graph
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = enqueue(b);
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+      if (!rc && e2 == cudaSuccess) {
+        b->graph = g;
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+      } else if (!rc) {
+        e = e2;
+      }
+    }
+    if (!rc && e != cudaSuccess) {
+      snprintf(b_errmsg, sizeof(b_errmsg), "graph capture: %s", cudaGetErrorString(e));
+      rc = LR_ECUDA;
+    }
+  }
+  if (rc) {
+    lr_batch_free(b);
+    return rc;
+  }
+  *out = b;
+  return LR_OK;
+}
+
+int lr_batch_run(lr_batch_handle b) {
+  if (!b) return LR_EINVAL;
+  if (b->exec) {
+    BCK(cudaGraphLaunch(b->exec, b->stream));
+    return LR_OK;
+  }
+  return enqueue(b);
+}
+
+int lr_batch_reset(lr_batch_handle b) {
+  if (!b) return LR_EINVAL;
+  return init_states(b);
+}
+
+int lr_batch_info(lr_batch_handle b, int i, lr_info* info) {
+  if (!b || !info || i < 0 || i >= b->count) return LR_EINVAL;
+  const Circ& C = b->circ[i];
+  double acc[8];
+  BCK(cudaMemcpyAsync(acc, C.acc, sizeof(acc), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  info->n = C.n;
+  info->columns = C.c;
+  info->capacity = C.cap;
+  info->dtype = b->dtype;
+  info->compressions = (int64_t)acc[3];
+  info->stages = C.truncs;
+  info->discarded = acc[0];
+  info->last_gap = acc[1];
+  return acc[2] > 0 ? LR_ENOCONV : LR_OK;
+}
+
+int lr_batch_probs(lr_batch_handle b, int i, void* out_dev) {
+  if (!b || !out_dev || i < 0 || i >= b->count) return LR_EINVAL;
+  const Circ& C = b->circ[i];
+  BCK(by_dt(b->dtype, [&](auto t) {
+    return launch_probs<decltype(t)>(C.buf[C.cur], C.N, C.c, C.cap, out_dev, b->stream);
+  }));
+  return LR_OK;
+}
+
+int lr_batch_stats(lr_batch_handle b, int64_t* gates, int64_t* truncations, int64_t* steps, int64_t* launches) {
+  if (!b || !gates || !truncations || !steps || !launches) return LR_EINVAL;
+  *gates = b->gates;
+  *truncations = b->truncs;
+  *steps = (int64_t)b->steps.size();
+  *launches = b->launches;
+  return LR_OK;
+}
+
+}  // extern "C"

@@ -75,10 +75,10 @@ __device__ int sturm(const T* d, const T* e2, int lo, int hi, T x, T pivmin) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TRI_THREADS) k_eigh_tri(const double2* __restrict__ G, int m, int c_split,
-                                                          cx<T>* gpacked, T* gZ, double* __restrict__ evals,
-                                                          double2* __restrict__ evecs, EigOut* __restrict__ out,
-                                                          int r, double eps, int all_vecs) {
+__device__ __forceinline__ void eigh_tri_body(const double2* __restrict__ G, int m, int c_split,
+                                              cx<T>* gpacked, T* gZ, double* __restrict__ evals,
+                                              double2* __restrict__ evecs, EigOut* __restrict__ out,
+                                              int r, double eps, int all_vecs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ cx<T>* colptr[TRI_MAXM];
   __shared__ cx<T> sv[TRI_MAXM], sp[TRI_MAXM], stau[TRI_MAXM];
@@ -94,6 +94,8 @@ __global__ void __launch_bounds__(TRI_THREADS) k_eigh_tri(const double2* __restr
   __shared__ double dred[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int moff_split = packed_off(c_split, m);
+  long long t_mark = clock64();
+  long long t_ph[6] = {0, 0, 0, 0, 0, 0};
   cx<T>* spk = (cx<T>*)smem_raw;
 
   // ---- 1. load the lower triangle, packed by columns ----------------------
@@ -242,6 +244,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_eigh_tri(const double2* __restr
     if (m >= 1) se[m - 1] = 0;
   }
   __syncthreads();
+  if (tid == 0) { const long long t = clock64(); t_ph[0] = t - t_mark; t_mark = t; }
   // move the shared part of the packed reflectors to global (shared memory is reused below)
   {
     const int total = packed_off(m, m) - moff_split;
@@ -293,6 +296,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_eigh_tri(const double2* __restr
   }
   __syncthreads();
 
+  if (tid == 0) { const long long t = clock64(); t_ph[1] = t - t_mark; t_mark = t; }
   // ---- 3. sort descending, rank choice, FP64 accounting --------------------
   // a NaN (from a non-finite input) sorts last so ranks stay a permutation
   for (int t = tid; t < m; t += blockDim.x)
@@ -360,6 +364,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_eigh_tri(const double2* __restr
   }
   __syncthreads();
   const int nvec = all_vecs ? m : s_k;
+  if (tid == 0) { const long long t = clock64(); t_ph[2] = t - t_mark; t_mark = t; }
 
   // ---- 4. inverse iteration (warp per cluster, lane 0 runs the LU) ---------
   {
@@ -469,6 +474,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_eigh_tri(const double2* __restr
   }
   __syncthreads();
 
+  if (tid == 0) { const long long t = clock64(); t_ph[3] = t - t_mark; t_mark = t; }
   // ---- 5. back-transform: y = H_0 (H_1 (... H_{m-2} z)) ----------------------
   // Each warp owns output columns (ranks); reflectors are staged in shared
   // memory TRI_CHUNK at a time, from the last to the first.
@@ -535,7 +541,59 @@ __global__ void __launch_bounds__(TRI_THREADS) k_eigh_tri(const double2* __restr
       }
     }
   }
+  __syncthreads();
+  if (tid == 0) {
+    const long long t = clock64();
+    t_ph[4] = t - t_mark;
+    for (int p = 0; p < 5; ++p) out->cycles[p] = t_ph[p];
+  }
 }
+
+template <typename T>
+__global__ void __launch_bounds__(TRI_THREADS) k_eigh_tri(const double2* __restrict__ G, int m, int c_split,
+                                                          cx<T>* gpacked, T* gZ, double* __restrict__ evals,
+                                                          double2* __restrict__ evecs, EigOut* __restrict__ out,
+                                                          int r, double eps, int all_vecs) {
+  eigh_tri_body<T>(G, m, c_split, gpacked, gZ, evals, evecs, out, r, eps, all_vecs);
+}
+
+constexpr size_t TRI_DYN_MAX = 180 * 1024;
+
+// smallest c such that packed columns c..m-1 fit in the budget
+__host__ __device__ __forceinline__ int tri_split_for(int m, size_t elem, size_t budget) {
+  for (int c = 0; c < m; ++c)
+    if ((size_t)(packed_off(m, m) - packed_off(c, m)) * elem <= budget) return c;
+  return m;
+}
+
+// one circuit's eigensolve per block; all vectors are not needed (no adjoint)
+template <typename T>
+__global__ void __launch_bounds__(TRI_THREADS) k_eigh_tri_batch(const TruncTask* __restrict__ tasks) {
+  const TruncTask& tk = tasks[blockIdx.x];
+  const int m = tk.m;
+  const int c_split = tri_split_for(m, sizeof(cx<T>), TRI_DYN_MAX);
+  cx<T>* gpacked = (cx<T>*)tk.eigwork;
+  T* gZ = (T*)(gpacked + packed_off(m, m));
+  eigh_tri_body<T>(tk.G, m, c_split, gpacked, gZ, tk.evals, tk.evecs, tk.eo, tk.k, 0.0, 0);
+}
+
+template <typename T>
+cudaError_t prepare_eigh_tri_batch() {
+  return cudaFuncSetAttribute(k_eigh_tri_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TRI_DYN_MAX);
+}
+
+// prepare_eigh_tri_batch<T>() must have run once (it is not a stream operation,
+// so it stays outside graph capture)
+template <typename T>
+cudaError_t launch_eigh_tri_batch(const TruncTask* tasks, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  k_eigh_tri_batch<T><<<ntasks, TRI_THREADS, TRI_DYN_MAX, s>>>(tasks);
+  return cudaGetLastError();
+}
+template cudaError_t prepare_eigh_tri_batch<float>();
+template cudaError_t prepare_eigh_tri_batch<double>();
+template cudaError_t launch_eigh_tri_batch<float>(const TruncTask*, int, cudaStream_t);
+template cudaError_t launch_eigh_tri_batch<double>(const TruncTask*, int, cudaStream_t);
 
 template <typename T>
 static int tri_c_split(int m, size_t budget) {

@@ -61,6 +61,73 @@ __global__ void __launch_bounds__(256) k_expand(const cx<T>* __restrict__ V, cx<
   }
 }
 
+// Batched expansion: block b serves task t with bstart[t] <= b < bstart[t+1].
+__device__ __forceinline__ int expand_task_of_block(const int* __restrict__ bstart, int ntasks, int b) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bstart[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, int G>
+__device__ __forceinline__ void expand_batch_body(const ExpandTask& tk, int lb, int nlb) {
+  __shared__ cx<T> sM[4][G][G];
+  for (int i = threadIdx.x; i < tk.K * G * G; i += blockDim.x) {
+    const int al = i / (G * G), a = (i / G) % G, g = i % G;
+    sM[al][a][g] = from_d2<T>(tk.M[(al * G + a) * G + g]);
+  }
+  __syncthreads();
+  const cx<T>* V = (const cx<T>*)tk.V;
+  cx<T>* W = (cx<T>*)tk.W;
+  const int c = tk.c, ld = tk.ld, K = tk.K;
+  for (int64_t e = (int64_t)lb * blockDim.x + threadIdx.x; e < tk.total; e += (int64_t)nlb * blockDim.x) {
+    const uint64_t grp = (uint64_t)(e / c);
+    const int j = (int)(e - (int64_t)grp * c);
+    uint64_t rows[G];
+    group_rows<G>(grp, tk.bits, rows);
+    cx<T> v[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = V[rows[g] * (uint64_t)ld + j];
+    for (int al = 0; al < K; ++al) {
+#pragma unroll
+      for (int a = 0; a < G; ++a) {
+        cx<T> acc = mk<T>(0, 0);
+#pragma unroll
+        for (int g = 0; g < G; ++g) cfma(acc, sM[al][a][g], v[g]);
+        W[rows[a] * (uint64_t)ld + (uint64_t)al * c + j] = acc;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_expand_batch(const ExpandTask* __restrict__ tasks,
+                                                      const int* __restrict__ bstart, int ntasks) {
+  const int t = expand_task_of_block(bstart, ntasks, blockIdx.x);
+  const ExpandTask& tk = tasks[t];
+  const int lb = blockIdx.x - bstart[t], nlb = bstart[t + 1] - bstart[t];
+  if (tk.G == 2) expand_batch_body<T, 2>(tk, lb, nlb);
+  else expand_batch_body<T, 4>(tk, lb, nlb);
+}
+
+int expand_blocks(int64_t total) {
+  int64_t b = (total + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  return b < 1 ? 1 : (int)b;
+}
+
+template <typename T>
+cudaError_t launch_expand_batch(const ExpandTask* tasks, const int* bstart, int nblocks, int ntasks,
+                                cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  k_expand_batch<T><<<nblocks, 256, 0, s>>>(tasks, bstart, ntasks);
+  return cudaGetLastError();
+}
+template cudaError_t launch_expand_batch<float>(const ExpandTask*, const int*, int, int, cudaStream_t);
+template cudaError_t launch_expand_batch<double>(const ExpandTask*, const int*, int, int, cudaStream_t);
+
 static int grid_for(int64_t total, int threads) {
   int64_t b = (total + threads - 1) / threads;
   const int64_t cap = 152 * 16;  // 16 resident 256-thread blocks per SM, grid-stride beyond

@@ -28,22 +28,23 @@ __device__ __forceinline__ int64_t pair_index(int64_t x, int i, int pairbit, int
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram(const cx<T>* __restrict__ A, int lda, int ma,
-                                              const cx<T>* __restrict__ B, int ldb, int mb, int64_t N,
-                                              int64_t chunk, int tiles_j, int hermitian,
-                                              double2* __restrict__ partials, int pairbit, int chalf) {
+__device__ __forceinline__ void gram_body(const cx<T>* __restrict__ A, int lda, int ma,
+                                          const cx<T>* __restrict__ B, int ldb, int mb, int64_t N,
+                                          int64_t chunk, int tiles_j, int hermitian,
+                                          double2* __restrict__ partials, int pairbit, int chalf, int bx,
+                                          int by) {
   __shared__ cx<T> As[KSTEP][TILE];
   __shared__ cx<T> Bs[KSTEP][TILE];
   int ti, tj;
   if (hermitian) {
     // linear index over the upper triangle of tiles (ti <= tj)
-    int lin = blockIdx.x, row = 0, cnt = tiles_j;
+    int lin = bx, row = 0, cnt = tiles_j;
     while (lin >= cnt) { lin -= cnt; ++row; --cnt; }
     ti = row; tj = row + lin;
   } else {
-    ti = blockIdx.x / tiles_j; tj = blockIdx.x % tiles_j;
+    ti = bx / tiles_j; tj = bx % tiles_j;
   }
-  const int split = blockIdx.y;
+  const int split = by;
   const int64_t x0 = (int64_t)split * chunk;
   int64_t x1 = x0 + chunk; if (x1 > N) x1 = N;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -107,6 +108,15 @@ __global__ void __launch_bounds__(256) k_gram(const cx<T>* __restrict__ A, int l
         P[(int64_t)i * mb + j] = make_double2(dacc[a][b].x + (double)acc[a][b].x,
                                               dacc[a][b].y + (double)acc[a][b].y);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram(const cx<T>* __restrict__ A, int lda, int ma,
+                                              const cx<T>* __restrict__ B, int ldb, int mb, int64_t N,
+                                              int64_t chunk, int tiles_j, int hermitian,
+                                              double2* __restrict__ partials, int pairbit, int chalf) {
+  gram_body<T>(A, lda, ma, B, ldb, mb, N, chunk, tiles_j, hermitian, partials, pairbit, chalf, blockIdx.x,
+               blockIdx.y);
 }
 
 // out[i][j] = sum_s partials[s][i][j] in split order; Hermitian: fill the lower
@@ -175,16 +185,16 @@ cudaError_t launch_gram(const void* A, int lda, int ma, const void* B, int ldb, 
 // Pair mode (pairbit >= 0): rows are pairs as in k_gram, A1 has 2*chalf
 // logical columns and Y has p = 2*phalf logical columns split the same way.
 template <typename T>
-__global__ void __launch_bounds__(256) k_rowmat(const cx<T>* __restrict__ A1, int lda1, int k1,
-                                                const double2* __restrict__ M1, int ldm1,
-                                                const cx<T>* __restrict__ A2, int lda2, int k2,
-                                                const double2* __restrict__ M2, int ldm2,
-                                                cx<T>* __restrict__ Y, int ldy, int p, int64_t N,
-                                                int pairbit, int chalf, int phalf) {
+__device__ __forceinline__ void rowmat_body(const cx<T>* __restrict__ A1, int lda1, int k1,
+                                            const double2* __restrict__ M1, int ldm1,
+                                            const cx<T>* __restrict__ A2, int lda2, int k2,
+                                            const double2* __restrict__ M2, int ldm2,
+                                            cx<T>* __restrict__ Y, int ldy, int p, int64_t N,
+                                            int pairbit, int chalf, int phalf, int bx, int by) {
   __shared__ cx<T> As[TILE][KSTEP + 1];
   __shared__ cx<T> Ms[KSTEP][TILE];
-  const int64_t xbase = (int64_t)blockIdx.x * TILE;
-  const int jbase = blockIdx.y * TILE;
+  const int64_t xbase = (int64_t)bx * TILE;
+  const int jbase = by * TILE;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   cx<T> acc[4][4];
 #pragma unroll
@@ -243,6 +253,17 @@ __global__ void __launch_bounds__(256) k_rowmat(const cx<T>* __restrict__ A1, in
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) k_rowmat(const cx<T>* __restrict__ A1, int lda1, int k1,
+                                                const double2* __restrict__ M1, int ldm1,
+                                                const cx<T>* __restrict__ A2, int lda2, int k2,
+                                                const double2* __restrict__ M2, int ldm2,
+                                                cx<T>* __restrict__ Y, int ldy, int p, int64_t N,
+                                                int pairbit, int chalf, int phalf) {
+  rowmat_body<T>(A1, lda1, k1, M1, ldm1, A2, lda2, k2, M2, ldm2, Y, ldy, p, N, pairbit, chalf, phalf, blockIdx.x,
+                 blockIdx.y);
+}
+
+template <typename T>
 cudaError_t launch_rowmat(const void* A1, int lda1, int k1, const double2* M1, int ldm1,
                           const void* A2, int lda2, int k2, const double2* M2, int ldm2,
                           void* Y, int ldy, int p, int64_t N, cudaStream_t s, int pairbit, int chalf,
@@ -297,6 +318,130 @@ cudaError_t launch_build_proj(const double2* U, int c, int K, int k, const PairQ
   k_build_proj<<<(n + 255) / 256, 256, 0, s>>>(U, c, K, k, q, D);
   return cudaGetLastError();
 }
+
+// ---- batched structured truncation (many circuits per launch) ---------------
+// Each launch serves a list of tasks (one per circuit); blocks map to tasks
+// through a prefix table of per-task block counts.
+__device__ __forceinline__ int task_of_block(const int* __restrict__ bstart, int ntasks, int b) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bstart[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pair_gram_batch(const TruncTask* __restrict__ tasks,
+                                                         const int* __restrict__ bstart, int ntasks) {
+  const int t = task_of_block(bstart, ntasks, blockIdx.x);
+  const TruncTask& tk = tasks[t];
+  const int l = blockIdx.x - bstart[t];
+  const int tiles = tk.tiles;
+  const int c2 = 2 * tk.c;
+  gram_body<T>((const cx<T>*)tk.V, tk.ld, c2, (const cx<T>*)tk.V, tk.ld, c2, tk.N2, tk.chunk,
+               (c2 + TILE - 1) / TILE, 1, tk.partials, tk.q, tk.c, l % tiles, l / tiles);
+}
+
+// G'[al c + i][be c + j] = sum_{b,b'} (M_al^dag M_be)_{bb'} S[b c + i][b' c + j], S summed over splits
+__global__ void __launch_bounds__(256) k_reduce_assemble_batch(const TruncTask* __restrict__ tasks) {
+  const TruncTask& tk = tasks[blockIdx.y];
+  const int c = tk.c, K = tk.K, m = K * c, c2 = 2 * c;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  const int row = e / m, col = e % m;
+  const int al = row / c, i = row % c, be = col / c, j = col % c;
+  const int64_t stride = (int64_t)c2 * c2;
+  double2 acc = make_double2(0, 0);
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int bp = 0; bp < 2; ++bp) {
+      const int si = b * c + i, sj = bp * c + j;
+      const bool upper = (si / TILE) <= (sj / TILE);  // tiles computed by the Gram
+      const int64_t idx = upper ? (int64_t)si * c2 + sj : (int64_t)sj * c2 + si;
+      double sr = 0.0, sim = 0.0;
+      for (int sp = 0; sp < tk.splits; ++sp) {
+        const double2 v = tk.partials[sp * stride + idx];
+        sr += v.x; sim += v.y;
+      }
+      if (!upper) sim = -sim;
+      double2 q = make_double2(0, 0);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) cfmac(q, tk.M[al][a][b], tk.M[be][a][bp]);
+      cfma(acc, q, make_double2(sr, sim));
+    }
+  if (row == col) acc.y = 0.0;
+  tk.G[e] = acc;
+}
+
+// D[b c + i][a k + j] = sum_al M[al][a][b] U[al c + i][j]
+__global__ void __launch_bounds__(256) k_build_proj_batch(const TruncTask* __restrict__ tasks) {
+  const TruncTask& tk = tasks[blockIdx.y];
+  const int c = tk.c, k = tk.k, K = tk.K, m = K * c;
+  const int cols = 2 * k;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * c * cols) return;
+  const int r = e / cols, cl = e % cols;
+  const int b = r / c, i = r % c, a = cl / k, j = cl % k;
+  double2 acc = make_double2(0, 0);
+  for (int al = 0; al < K; ++al) cfma(acc, tk.M[al][a][b], tk.evecs[(int64_t)(al * c + i) * m + j]);
+  tk.D[e] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pair_rowmat_batch(const TruncTask* __restrict__ tasks,
+                                                           const int* __restrict__ bstart, int ntasks) {
+  const int t = task_of_block(bstart, ntasks, blockIdx.x);
+  const TruncTask& tk = tasks[t];
+  const int l = blockIdx.x - bstart[t];
+  const int coltiles = (2 * tk.k + TILE - 1) / TILE;
+  rowmat_body<T>((const cx<T>*)tk.V, tk.ld, 2 * tk.c, tk.D, 2 * tk.k, nullptr, 0, 0, nullptr, 0, (cx<T>*)tk.W,
+                 tk.ld, 2 * tk.k, tk.N2, tk.q, tk.c, tk.k, l / coltiles, l % coltiles);
+}
+
+__global__ void k_accum_batch(const TruncTask* __restrict__ tasks, int ntasks) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntasks) return;
+  const TruncTask& tk = tasks[t];
+  tk.acc[0] += tk.eo->dropped;
+  tk.acc[1] = tk.eo->gap;
+  if ((double)tk.eo->status > tk.acc[2]) tk.acc[2] = (double)tk.eo->status;
+  tk.acc[3] += 1.0;
+}
+
+template <typename T>
+cudaError_t launch_trunc_batch_gemms(const TruncTask* tasks, const int* gram_bstart, int gram_blocks,
+                                     const int* proj_bstart, int proj_blocks, int ntasks, int max_m2,
+                                     int max_d, int phase, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (phase == 0) {
+    k_pair_gram_batch<T><<<gram_blocks, 256, 0, s>>>(tasks, gram_bstart, ntasks);
+    k_reduce_assemble_batch<<<dim3((max_m2 + 255) / 256, ntasks), 256, 0, s>>>(tasks);
+  } else {
+    k_build_proj_batch<<<dim3((max_d + 255) / 256, ntasks), 256, 0, s>>>(tasks);
+    k_pair_rowmat_batch<T><<<proj_blocks, 256, 0, s>>>(tasks, proj_bstart, ntasks);
+    k_accum_batch<<<(ntasks + 127) / 128, 128, 0, s>>>(tasks, ntasks);
+  }
+  return cudaGetLastError();
+}
+
+int trunc_tiles(int c) {
+  const int t = (2 * c + TILE - 1) / TILE;
+  return t * (t + 1) / 2;
+}
+int64_t trunc_chunk(int64_t N2, int splits) {
+  int64_t chunk = (N2 + splits - 1) / splits;
+  return ((chunk + KSTEP - 1) / KSTEP) * KSTEP;
+}
+int trunc_proj_blocks(int64_t N2, int k) {
+  return (int)(((N2 + TILE - 1) / TILE) * ((2 * k + TILE - 1) / TILE));
+}
+
+template cudaError_t launch_trunc_batch_gemms<float>(const TruncTask*, const int*, int, const int*, int, int, int,
+                                                     int, int, cudaStream_t);
+template cudaError_t launch_trunc_batch_gemms<double>(const TruncTask*, const int*, int, const int*, int, int, int,
+                                                      int, int, cudaStream_t);
 
 // ---- truncation adjoint, small FP64 matrices (m <= 256) ----------------------
 // FA[j][i] = F(lam_i - lam_{k+j}) * sum_l conj(U[l][k+j]) C[l][i]   (j < m-k, i < k)

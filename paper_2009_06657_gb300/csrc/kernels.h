@@ -28,6 +28,7 @@ struct EigOut {
   double kept;      // sum of kept eigenvalues, FP64
   double gap;       // (lambda_k - lambda_{k+1}) / lambda_1, inf if nothing dropped
   double trace;     // trace of the Gram matrix (FP64 sum of its diagonal)
+  long long cycles[6];  // SM clock cycles per solver phase (diagnostics)
 };
 
 // ---- expansion (Eqs. 3-4): W[x_a][alpha*c + j] = sum_g M[alpha][a][g] V[x_g][j]
@@ -69,6 +70,49 @@ cudaError_t launch_assemble_gram(const double2* S, int c, int K, const PairQ& q,
 // D (2c x 2k) = pair-projection matrix from the leading k eigenvectors U (m x m)
 cudaError_t launch_build_proj(const double2* U, int c, int K, int k, const PairQ& q, double2* D, cudaStream_t s);
 
+// ---- batched structured truncation: one task per circuit ------------------------
+struct TruncTask {
+  const void* V;      // state (N x ld), pairs on bit q
+  void* W;            // output slab
+  int64_t N2;         // number of row pairs (N / 2)
+  int64_t chunk;      // Gram rows per split
+  int c, ld, K, k, q, splits, tiles, m;
+  double2 M[4][2][2]; // Kt_a G
+  double2* partials;  // splits x (2c)^2
+  double2* G;         // m x m Gram of the implicit V'
+  double* evals;
+  double2* evecs;
+  EigOut* eo;
+  void* eigwork;
+  double2* D;         // 2c x 2k
+  double* acc;        // per-circuit accounting [discarded, gap, status, truncations]
+};
+// phase 0: pair Gram + reduce/assemble G'; phase 1: projection matrix, pair projection, accounting
+template <typename T>
+cudaError_t launch_trunc_batch_gemms(const TruncTask* tasks, const int* gram_bstart, int gram_blocks,
+                                     const int* proj_bstart, int proj_blocks, int ntasks, int max_m2,
+                                     int max_d, int phase, cudaStream_t s);
+int trunc_tiles(int c);
+int64_t trunc_chunk(int64_t N2, int splits);
+int trunc_proj_blocks(int64_t N2, int k);
+template <typename T>
+cudaError_t launch_eigh_tri_batch(const TruncTask* tasks, int ntasks, cudaStream_t s);
+template <typename T>
+cudaError_t prepare_eigh_tri_batch();
+
+struct ExpandTask {
+  const void* V;
+  void* W;
+  int64_t total;  // groups x c
+  int c, ld, G, K;
+  int bits[2];
+  double2 M[16];  // M[(al * G + a) * G + g]
+};
+template <typename T>
+cudaError_t launch_expand_batch(const ExpandTask* tasks, const int* bstart, int nblocks, int ntasks,
+                                cudaStream_t s);
+int expand_blocks(int64_t total);
+
 // ---- Y[x][j] = sum_i A1[x][i] M1[i][j] + sum_i A2[x][i] M2[i][j]  (j < p)
 // M1, M2: complex128 device matrices with leading dimensions ldm1, ldm2. A2 may be null.
 // pairbit >= 0: A1 and Y are read/written as pair matrices (A1: 2*chalf logical
@@ -99,7 +143,8 @@ cudaError_t launch_eigh_tri(const double2* G, int m, void* work, double* evals, 
 cudaError_t launch_trunc_adj_small(const double2* C, const double2* U, const double* lam, int m,
                                    int k, double2* FA, double2* T1, double2* Mcat, cudaStream_t s);
 
-// ---- readouts
+// ---- readouts (grids never exceed kReadoutMaxBlocks blocks)
+constexpr int kReadoutMaxBlocks = 1024;
 template <typename T>
 cudaError_t launch_probs(const void* V, int64_t N, int c, int ld, void* out, cudaStream_t s);
 // out[0..n-1] = <Z_q>, out[n] = trace; partials: workspace of (n+1) * 1024 doubles

@@ -12,7 +12,7 @@ namespace lret {
 
 constexpr int RO_THREADS = 256;
 constexpr int RO_WARPS = RO_THREADS / 32;
-constexpr int RO_MAX_BLOCKS = 1024;
+constexpr int RO_MAX_BLOCKS = kReadoutMaxBlocks;
 
 template <typename T>
 __global__ void __launch_bounds__(RO_THREADS) k_probs(const cx<T>* __restrict__ V, int64_t N, int c, int ld,

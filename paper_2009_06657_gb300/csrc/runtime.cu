@@ -996,6 +996,15 @@ int lr_get_state(lr_handle h, void* out_host) {
 
 int64_t lr_device_bytes(lr_handle h) { return h ? (int64_t)h->bytes : 0; }
 
+int lr_last_eig_stats(lr_handle h, int* sweeps_out, long long* cycles_out) {
+  if (!h || !sweeps_out || !cycles_out) return LR_EINVAL;
+  CK(cudaMemcpyAsync(h->h_eo, h->eo, sizeof(EigOut), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *sweeps_out = h->h_eo->sweeps;
+  for (int i = 0; i < 6; ++i) cycles_out[i] = h->h_eo->cycles[i];
+  return LR_OK;
+}
+
 int lr_set_timing(lr_handle h, int on) {
   if (!h) return LR_EINVAL;
   if (on && h->ev.empty()) {

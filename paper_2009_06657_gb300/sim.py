@@ -189,6 +189,12 @@ class LRSim:
               "lr_kernel_times")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(_ffi.KCLASSES)}
 
+    def last_eig_stats(self):
+        sw = C.c_int(0)
+        cyc = (C.c_longlong * 6)()
+        check(lib.lr_last_eig_stats(self.h, C.byref(sw), cyc), "lr_last_eig_stats")
+        return sw.value, list(cyc)
+
     def device_bytes(self):
         return int(lib.lr_device_bytes(self.h))
 
@@ -237,3 +243,73 @@ class LRExpectation(torch.autograd.Function):
         g = ctx.sim.backward(ctx.terms, ctx.nparams)
         ctx.sim.set_record(False)
         return torch.from_numpy(g) * grad_out, None, None, None, None, None
+
+
+class LRBatch:
+    """Many independent circuits advanced together (one CUDA graph per run).
+
+    circuits: list of dicts {"n", "r", "ops"} in the shared op-list format.
+    Semantics per circuit: truncation to rank r after every channel.
+    """
+
+    def __init__(self, circuits, dtype="c64", rows_per_split=0, use_graph=True, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblret needs a CUDA device")
+        self.dtype = _ffi.LR_C64 if dtype in ("c64", "complex64", _ffi.LR_C64) else _ffi.LR_C128
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.circuits = circuits
+        self._keep = []
+        arr = (_ffi.lr_circuit * len(circuits))()
+        for i, cd in enumerate(circuits):
+            ops = (_ffi.lr_op * max(1, len(cd["ops"])))()
+            for j, o in enumerate(cd["ops"]):
+                qs = o["q"] if isinstance(o["q"], list) else [o["q"]]
+                ops[j].kind = _ffi.OP_KIND[o["op"]]
+                ops[j].q0 = int(qs[0])
+                ops[j].q1 = int(qs[1]) if len(qs) > 1 else -1
+                ops[j].theta = float(o.get("theta", 0.0))
+                ops[j].p = float(o.get("p", o.get("gamma", 0.0)))
+            self._keep.append(ops)
+            arr[i].n, arr[i].r, arr[i].nops = int(cd["n"]), int(cd["r"]), len(cd["ops"])
+            arr[i].ops = C.cast(ops, C.POINTER(_ffi.lr_op))
+        h = C.c_void_p()
+        check(lib.lr_batch_create(arr, len(circuits), self.dtype, int(rows_per_split), 1 if use_graph else 0,
+                                  C.c_void_p(self.stream.cuda_stream), C.byref(h)), "lr_batch_create")
+        self.h = h
+
+    def run(self):
+        check(lib.lr_batch_run(self.h), "lr_batch_run")
+
+    def reset(self):
+        check(lib.lr_batch_reset(self.h), "lr_batch_reset")
+
+    def info(self, i):
+        inf = _ffi.lr_info()
+        st = lib.lr_batch_info(self.h, int(i), C.byref(inf))
+        if st not in (_ffi.LR_OK, _ffi.LR_ENOCONV):
+            check(st, "lr_batch_info")
+        return {"n": inf.n, "columns": inf.columns, "compressions": inf.compressions,
+                "discarded": inf.discarded, "converged": st == _ffi.LR_OK}
+
+    def probs(self, i):
+        n = int(self.circuits[i]["n"])
+        dt = torch.float32 if self.dtype == _ffi.LR_C64 else torch.float64
+        out = torch.empty(1 << n, dtype=dt, device="cuda")
+        check(lib.lr_batch_probs(self.h, int(i), C.c_void_p(out.data_ptr())), "lr_batch_probs")
+        return out
+
+    def stats(self):
+        v = [C.c_int64() for _ in range(4)]
+        check(lib.lr_batch_stats(self.h, *[C.byref(x) for x in v]), "lr_batch_stats")
+        return dict(zip(["gates", "truncations", "steps", "launches"], [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.lr_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

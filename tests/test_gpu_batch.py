@@ -1,0 +1,93 @@
+"""Batched execution (many circuits of uneven n, r and depth in one CUDA graph)
+against one-at-a-time runs of the same circuits and against the oracle."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import lret as O  # noqa: E402
+from workloads import batch_circuits, random_layered  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def lr():
+    import paper_2009_06657_gb300 as m
+    return m
+
+
+def _small_batch():
+    out = []
+    specs = [(3, 2, 2), (5, 4, 2), (7, 8, 1), (4, 2, 3), (6, 16, 1), (8, 4, 1)]
+    for i, (n, r, d) in enumerate(specs):
+        out.append({"n": n, "r": r, "ops": random_layered(n, d, seed=5100 + i, noise=("mixed", 2e-2, 4e-2),
+                                                           qubit_jitter=(0.5, 1.5))})
+    return out
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_batch_matches_single_runs(lr, dtype):
+    circs = _small_batch()
+    b = lr.LRBatch(circs, dtype=dtype)
+    b.run()
+    tol = 1e-11 if dtype == "c128" else 1e-5
+    for i, cd in enumerate(circs):
+        sim = lr.LRSim(cd["n"], cd["r"], dtype=dtype)
+        sim.set_eigensolver("tridiag")
+        lr.run_ops(sim, cd["ops"], r=cd["r"])
+        p1 = sim.probs().double().cpu().numpy()
+        pb = b.probs(i).double().cpu().numpy()
+        assert np.sum(np.abs(p1 - pb)) < tol, i
+        assert abs(b.info(i)["discarded"] - sim.info()["discarded"]) < tol
+        sim.close()
+    b.close()
+
+
+def test_batch_matches_oracle_fp64(lr):
+    circs = _small_batch()
+    b = lr.LRBatch(circs, dtype="c128")
+    b.run()
+    for i, cd in enumerate(circs):
+        ref = O.run_lret(cd["n"], cd["ops"], r=cd["r"])
+        pb = b.probs(i).cpu().numpy()
+        assert np.sum(np.abs(pb - ref.probs())) < 1e-10, i
+        assert abs(b.info(i)["discarded"] - ref.discarded) < 1e-10
+    b.close()
+
+
+def test_graph_and_direct_launches_agree_and_rerun_is_reproducible(lr):
+    circs = _small_batch()
+    outs = []
+    for use_graph in (True, False):
+        b = lr.LRBatch(circs, dtype="c64", use_graph=use_graph)
+        b.run()
+        first = [b.probs(i).cpu().numpy() for i in range(len(circs))]
+        b.reset()
+        b.run()
+        second = [b.probs(i).cpu().numpy() for i in range(len(circs))]
+        for x, y in zip(first, second):
+            assert np.array_equal(x, y)
+        outs.append(first)
+        b.close()
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
+
+
+def test_heterogeneous_batch_workload_miniature(lr):
+    # the 256-circuit family (n in 8..18, r in {8,16,32,64}) at 2% depth: every
+    # circuit keeps trace + discarded mass = 1 and matches its own single run
+    circs = batch_circuits(count=24, depth_scale=0.02)
+    b = lr.LRBatch(circs, dtype="c64")
+    b.run()
+    st = b.stats()
+    assert st["gates"] > 0 and st["truncations"] > 0
+    for i in (0, 5, 11, 23):
+        cd = circs[i]
+        pb = b.probs(i).double()
+        inf = b.info(i)
+        assert abs(float(pb.sum()) - (1.0 - inf["discarded"])) < 1e-5
+        sim = lr.LRSim(cd["n"], cd["r"], dtype="c64")
+        sim.set_eigensolver("tridiag")
+        lr.run_ops(sim, cd["ops"], r=cd["r"])
+        assert float((sim.probs().double() - pb).abs().sum()) < 1e-5
+        sim.close()
+    b.close()
