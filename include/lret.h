@@ -184,6 +184,32 @@ int lr_last_eig_stats(lr_handle h, int* sweeps_out, long long* cycles_out);
 /* Upper bound on the device bytes the handle holds (for capacity planning). */
 int64_t lr_device_bytes(lr_handle h);
 
+/* Allocation-free <H> for callers that cannot allocate device memory when they
+ * read out (a server that reserved all device memory for its own pool up front,
+ * code running while a CUDA graph capture is open on the device, or a thread
+ * that must not take the device-wide synchronisation cudaMalloc/cudaFree
+ * imply). The paper has no counterpart: this is an interface variant of
+ * lr_expect that computes the same sum_t coeff_t Tr(V^dag P_t V).
+ *
+ * V_dev: caller-owned device state, 2^n x c complex (row-major, leading
+ * dimension ld >= c elements, interleaved complex64 for LR_C64 or complex128 for
+ * LR_C128). xmask/zmask/coeff: T host values (Pauli encoding as above).
+ * out_host: one double. stream: cudaStream_t (NULL = legacy default stream).
+ *
+ * Scratch (term masks and partial sums, about 2 MB) lives in one fixed device
+ * array of this library, held by every GPU that loads it until the process
+ * exits; the call allocates and frees nothing. The first call on a device looks
+ * up that array's device address, so make the first call on each device before
+ * any stream capture. All calls share the array, and the last call's contents
+ * stay in it (every value a call reads is written by that call first): calls
+ * that overlap on the GPU, from different streams or threads, race and must be
+ * serialised by the caller. T > LR_STATIC_MAX_TERMS returns LR_ECAPACITY.
+ * Synchronises the stream. */
+#define LR_STATIC_MAX_TERMS 256
+int lr_expect_static(const void* V_dev, int n, int c, int ld, int dtype, int T,
+                     const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+                     double* out_host, void* stream);
+
 /* ---- Batched execution of many independent circuits -------------------------
  * Not in the paper: many circuits of uneven n, r and depth advance together,
  * stage s of every circuit in the same launches, the whole schedule captured

@@ -25,6 +25,7 @@ LR_C128 = 1
 LR_DEPOLARIZING = 0
 LR_AMPLITUDE_DAMPING = 1
 LR_BIT_FLIP = 2
+LR_STATIC_MAX_TERMS = 256
 KCLASSES = ["expand", "gram", "eigh", "project", "readout", "pauli"]
 LR_NKCLASS = 8
 
@@ -93,6 +94,7 @@ _SIGS = {
     "lr_last_eig_stats": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "lr_set_timing": (C.c_int, [_H, C.c_int]),
     "lr_kernel_times": (C.c_int, [_H, _D, C.POINTER(C.c_int64)]),
+    "lr_expect_static": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _U64, _U64, _D, _D, _P]),
     "lr_batch_create": (C.c_int, [C.POINTER(lr_circuit), C.c_int, C.c_int, C.c_int, C.c_int, _P, C.POINTER(_H)]),
     "lr_batch_run": (C.c_int, [_H]),
     "lr_batch_reset": (C.c_int, [_H]),
