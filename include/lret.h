@@ -239,7 +239,9 @@ typedef struct lr_batch* lr_batch_handle;
 
 /* Lower, allocate, upload the task tables and (use_graph != 0) capture the
  * schedule into one CUDA graph. rows_per_split sets the Gram split size
- * (<= 0: 4096). Every circuit starts in |0...0>. */
+ * (<= 0: 4096). Every circuit starts in |0...0>. A NULL stream with
+ * use_graph != 0 gets a stream of the batch's own (the legacy default stream
+ * cannot be captured); the batch calls synchronise it. */
 int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_per_split, int use_graph,
                     void* stream, lr_batch_handle* out);
 /* Run the whole schedule once (one graph launch). Asynchronous. */
@@ -248,7 +250,8 @@ int lr_batch_run(lr_batch_handle b);
 int lr_batch_reset(lr_batch_handle b);
 /* Per-circuit state after a run (columns, discarded mass, truncations). Synchronises. */
 int lr_batch_info(lr_batch_handle b, int i, lr_info* info);
-/* Prob(x) of circuit i into a caller-owned device buffer (float for LR_C64). */
+/* Prob(x) of circuit i into a caller-owned device buffer (float for LR_C64).
+ * Synchronises the batch's stream. */
 int lr_batch_probs(lr_batch_handle b, int i, void* out_dev);
 /* Totals: gates, truncations, schedule steps, kernel launches per run. */
 int lr_batch_stats(lr_batch_handle b, int64_t* gates, int64_t* truncations, int64_t* steps, int64_t* launches);

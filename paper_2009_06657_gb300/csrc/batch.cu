@@ -46,7 +46,7 @@ struct Step {
   int t_off = 0, t_cnt = 0, gram_blocks = 0, proj_blocks = 0, gb_off = 0, pb_off = 0, max_m2 = 0, max_d = 0;
 };
 
-thread_local char b_errmsg[256];
+
 
 void rot(int axis, double th, zc U[4]) {
   const zc I(0, 1);
@@ -70,6 +70,7 @@ void put(double2& d, zc v) { d = make_double2(v.real(), v.imag()); }
 struct lr_batch {
   int count = 0, dtype = 0;
   cudaStream_t stream = nullptr;
+  bool own_stream = false;  // created here: the legacy default stream cannot be captured
   size_t esz = 0;
   std::vector<Circ> circ;
   std::vector<Step> steps;
@@ -87,7 +88,7 @@ struct lr_batch {
   do {                                                                                 \
     cudaError_t _e = (call);                                                           \
     if (_e != cudaSuccess) {                                                           \
-      snprintf(b_errmsg, sizeof(b_errmsg), "%s: %s", #call, cudaGetErrorString(_e));   \
+      lret::set_error("%s: %s", #call, cudaGetErrorString(_e));                        \
       return LR_ECUDA;                                                                 \
     }                                                                                  \
   } while (0)
@@ -258,6 +259,7 @@ int lr_batch_free(lr_batch_handle b) {
   if (b->d_et) cudaFree(b->d_et);
   if (b->d_tt) cudaFree(b->d_tt);
   if (b->d_bs) cudaFree(b->d_bs);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
   return LR_OK;
 }
@@ -271,6 +273,13 @@ int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_p
   b->count = count;
   b->dtype = dtype;
   b->stream = (cudaStream_t)stream;
+  if (!b->stream && use_graph) {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return LR_ECUDA;
+    }
+    b->own_stream = true;
+  }
   b->esz = dtype == LR_C64 ? sizeof(float2) : sizeof(double2);
   b->use_graph = use_graph;
   b->circ.resize(count);
@@ -409,7 +418,7 @@ int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_p
   if (e == cudaSuccess && !bs.empty()) e = cudaMemcpy(b->d_bs, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = by_dt(dtype, [&](auto t) { return prepare_eigh_tri_batch<decltype(t)>(); });
   if (e != cudaSuccess) {
-    snprintf(b_errmsg, sizeof(b_errmsg), "batch setup: %s", cudaGetErrorString(e));
+    lret::set_error("%s: %s", "batch setup", cudaGetErrorString(e));
     lr_batch_free(b);
     return LR_ECUDA;
   }
@@ -429,7 +438,7 @@ int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_p
       }
     }
     if (!rc && e != cudaSuccess) {
-      snprintf(b_errmsg, sizeof(b_errmsg), "graph capture: %s", cudaGetErrorString(e));
+      lret::set_error("%s: %s", "graph capture", cudaGetErrorString(e));
       rc = LR_ECUDA;
     }
   }
@@ -478,6 +487,7 @@ int lr_batch_probs(lr_batch_handle b, int i, void* out_dev) {
   BCK(by_dt(b->dtype, [&](auto t) {
     return launch_probs<decltype(t)>(C.buf[C.cur], C.N, C.c, C.cap, out_dev, b->stream);
   }));
+  BCK(cudaStreamSynchronize(b->stream));
   return LR_OK;
 }
 
