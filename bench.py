@@ -189,8 +189,9 @@ def run_ours(args, rank, world):
     # FP64 comparators at the same size (few truncations; rate per noisy gate-step)
     fp64 = bench_fp64(args, layers, dev, stream) if (rank == 0 and not args.no_fp64) else None
     adj = bench_adjoint(dev, stream) if (rank == 0 and not args.no_adjoint) else None
+    bat = bench_batch(dev, stream, scale=args.batch_scale) if (rank == 0 and not args.no_batch) else None
     return dict(ms=ms, g_per=g_per, c_per=c_per, ktimes=ktimes, clk=clk, e2e_s=e2e_s, fp64=fp64, info=info,
-                adjoint=adj)
+                adjoint=adj, batch=bat)
 
 
 def bench_fp64(args, layers, dev, stream):
@@ -296,6 +297,52 @@ def bench_adjoint(dev, stream, reps=2):
             "adjoint_over_forward": b / f, "grad_norm": float(sum(x * x for x in g) ** 0.5)}
 
 
+def bench_batch(dev, stream, scale=0.05, sample_single=12):
+    """256 seeded circuits (n ~ U{8..18}, r in {8,16,32,64}, depth ~ U{40..200}
+    layers scaled by `scale`, mixed depolarizing 1e-3 / amplitude damping 2e-3),
+    complex64, advanced together by one CUDA-graph launch; against the same
+    circuits run one at a time through the single-circuit path (a sample of
+    them, rate per gate-step)."""
+    import torch
+
+    import paper_2009_06657_gb300 as lr
+    from workloads import batch_circuits
+    circs = batch_circuits(count=256, depth_scale=scale)
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        b = lr.LRBatch(circs, dtype="c64", stream=stream)
+        t_build = time.perf_counter() - t0
+        st = b.stats()
+        b.run()  # warm-up
+        torch.cuda.synchronize()
+        b.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_batch = e0.elapsed_time(e1) / 1e3
+        b.close()
+        # one at a time (sample)
+        gates = 0
+        t1 = time.perf_counter()
+        for cd in circs[:sample_single]:
+            sim = lr.LRSim(cd["n"], cd["r"], dtype="c64", stream=stream)
+            lr.run_ops(sim, cd["ops"], r=cd["r"])
+            sim.info()
+            gates += sum(1 for o in cd["ops"] if o["op"] in ("rx", "ry", "rz", "cnot", "cz"))
+            sim.close()
+        torch.cuda.synchronize()
+        t_single = time.perf_counter() - t1
+    return {"workload": f"256 random circuits, n U{{8..18}}, r in {{8,16,32,64}}, depth U{{40..200}} x {scale}, "
+                        "mixed depolarizing 1e-3 / amplitude damping 2e-3, complex64",
+            "gates": st["gates"], "truncations": st["truncations"], "schedule_steps": st["steps"],
+            "launches_per_run": st["launches"], "build_s": t_build, "batch_s": t_batch,
+            "batch_gate_steps_per_s": st["gates"] / t_batch,
+            "single_gate_steps_per_s": gates / t_single, "single_sample_circuits": sample_single,
+            "speedup": (st["gates"] / t_batch) / (gates / t_single)}
+
+
 def algorithmic(kclass, info_c):
     """(bound, bytes_or_flops per launch) of a steady-state launch of a kernel class."""
     N, r, K, esz = 1 << N_QUBITS, RANK, 4, 8
@@ -322,6 +369,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-scale", type=float, default=0.05)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -367,7 +416,7 @@ def main():
         "clocks": res["clk"],
         "e2e": {"value": res["g_per"] / res["e2e_s"], "unit": "noisy gate-steps/s",
                 "h2d_bytes_per_step": h2d_bytes(get_layers()[0]), "d2h_bytes_per_step": (1 << N_QUBITS) * 4 + 8},
-        "fp64": None, "cpu_baseline": None, "adjoint": res.get("adjoint"),
+        "fp64": None, "cpu_baseline": None, "adjoint": res.get("adjoint"), "batch": res.get("batch"),
     }
     launches = sum(v[1] for v in kt.values())
     out["gpu_launches"] = launches * args.steps

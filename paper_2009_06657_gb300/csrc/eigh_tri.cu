@@ -18,9 +18,9 @@
 //     negligible; Sturm-count bisection gives each eigenvalue of each block.
 //  3. Eigenvalues are sorted descending; the kept count and the FP64
 //     kept/discarded sums are formed.
-//  4. Inverse iteration with a pivoted tridiagonal LU gives eigenvectors of
-//     T; eigenvalues of one block closer than 1e-3 ||T|| form a cluster whose
-//     vectors are re-orthogonalised against each other (modified Gram-Schmidt).
+//  4. Inverse iteration with a pivoted tridiagonal LU (one warp per vector, all
+//     vectors in parallel) gives eigenvectors of T; a modified Gram-Schmidt
+//     pass in rank order makes the set exactly orthonormal.
 //  5. Back-transform y = H_0 H_1 ... H_{m-2} z, reflectors staged through
 //     shared memory in chunks shared by all warps.
 #include <float.h>
@@ -36,7 +36,7 @@ template <> struct TEps<double> { static constexpr double v = DBL_EPSILON; stati
 
 constexpr int TRI_THREADS = 1024;
 constexpr int TRI_MAXM = 256;
-template <typename T> struct LuWarps { static constexpr int v = sizeof(T) == 4 ? 16 : 8; };
+template <typename T> struct LuWarps { static constexpr int v = sizeof(T) == 4 ? 24 : 12; };
 constexpr int TRI_CHUNK = 8;  // reflectors staged per back-transform chunk
 
 __host__ __device__ __forceinline__ int packed_off(int c, int m) { return c * m - (c * (c - 1)) / 2; }
@@ -59,6 +59,11 @@ __device__ __forceinline__ cx<T> cdiv(cx<T> a, cx<T> b) {
   return mk<T>((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
 }
 
+// Division in the Sturm recurrence: only the signs of the pivots are used, so a
+// fast FP32 quotient (a few ulp) is enough there.
+__device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
+
 // Sturm count: number of eigenvalues of the block [lo, hi] smaller than x.
 template <typename T>
 __device__ int sturm(const T* d, const T* e2, int lo, int hi, T x, T pivmin) {
@@ -67,7 +72,7 @@ __device__ int sturm(const T* d, const T* e2, int lo, int hi, T x, T pivmin) {
   if (fabs(q) < pivmin) q = -pivmin;
   if (q < 0) ++cnt;
   for (int i = lo + 1; i <= hi; ++i) {
-    q = d[i] - x - e2[i - 1] / q;
+    q = d[i] - x - sdiv(e2[i - 1], q);
     if (fabs(q) < pivmin) q = -pivmin;
     if (q < 0) ++cnt;
   }
@@ -85,9 +90,8 @@ __device__ __forceinline__ void eigh_tri_body(const double2* __restrict__ G, int
   __shared__ T sd[TRI_MAXM], se[TRI_MAXM], se2[TRI_MAXM], slam[TRI_MAXM];
   __shared__ short sblo[TRI_MAXM], sbhi[TRI_MAXM];  // block range of position / sorted eigenvalue
   __shared__ short sorder[TRI_MAXM];                  // sorted rank -> position index
-  __shared__ short snext[TRI_MAXM], shead[TRI_MAXM];  // clusters: linked lists over ranks
-  __shared__ int s_ncl, s_k;
-  __shared__ T red[32];
+  __shared__ int s_k;
+  __shared__ T red[32], red2[32];
   __shared__ cx<T> s_tau, s_scale;
   __shared__ T s_c;
   __shared__ double s_trace;
@@ -129,25 +133,34 @@ __device__ __forceinline__ void eigh_tri_body(const double2* __restrict__ G, int
     cx<T>* colj = colptr[j];
     // norms are taken on values scaled by the column's largest magnitude, so
     // squares of tiny entries cannot underflow to zero (which would give beta = 0)
-    T amax = 0;
+    // one pass: largest magnitude and unscaled sum of squares of x[1:]; the
+    // scaled sum is recomputed serially only when the plain one underflowed
+    T amax = 0, part = 0;
     for (int i = tid + 1; i <= n1; i += blockDim.x) {
       const cx<T> x = colj[i];
       amax = fmax(amax, fmax(fabs(x.x), fabs(x.y)));
+      if (i >= 2) part += x.x * x.x + x.y * x.y;
     }
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      part += __shfl_xor_sync(0xffffffffu, part, o);
+    }
     __syncthreads();
-    if (lane == 0) red[warp] = amax;
+    if (lane == 0) { red[warp] = amax; red2[warp] = part; }
     __syncthreads();
     amax = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) amax = fmax(amax, red[w]);
+    T xn2 = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { amax = fmax(amax, red[w]); xn2 += red2[w]; }
     const T inv_amax = amax > (T)0 ? (T)1 / amax : (T)0;
-    T part = 0;
-    for (int i = tid + 2; i <= n1; i += blockDim.x) {
-      const cx<T> x = colj[i];
-      const T a = x.x * inv_amax, b = x.y * inv_amax;
-      part += a * a + b * b;
+    T xn2s = xn2 * inv_amax * inv_amax;  // ||x[1:]||^2 / amax^2
+    if (tid == 0 && amax > (T)0 && xn2 < (T)1e-30 && xn2s > (T)0) {
+      T sacc = 0;
+      for (int i = 2; i <= n1; ++i) {
+        const T a = colj[i].x * inv_amax, b = colj[i].y * inv_amax;
+        sacc += a * a + b * b;
+      }
+      xn2s = sacc;
     }
-    const T xn2s = block_reduce(part, red);  // ||x[1:]||^2 / amax^2
     if (tid == 0) {
       const cx<T> alpha = colj[1];
       T beta;
@@ -194,6 +207,7 @@ __device__ __forceinline__ void eigh_tri_body(const double2* __restrict__ G, int
       const int row = j + 1 + rr;
       cx<T> acc = mk<T>(0, 0);
       if (rr < n1) {
+#pragma unroll 4
         for (int col = j + 1 + sub; col < m; col += 4) {
           const cx<T> a = (col <= row) ? colptr[col][row - col] : conjg(colptr[row][col - row]);
           cfma(acc, a, sv[col]);
@@ -206,7 +220,7 @@ __device__ __forceinline__ void eigh_tri_body(const double2* __restrict__ G, int
       if (rr < n1 && sub == 0) sp[row] = cmul(tau, acc);
     }
     __syncthreads();
-    // c = (1/2) Re(conj(tau) * (v^dag p))
+    // c = (1/2) Re(conj(tau) * (v^dag p)), both parts in one reduction
     {
       T pr = 0, pi = 0;
       for (int t = tid; t < n1; t += blockDim.x) {
@@ -215,9 +229,17 @@ __device__ __forceinline__ void eigh_tri_body(const double2* __restrict__ G, int
         pr += v.x * p.x + v.y * p.y;
         pi += v.x * p.y - v.y * p.x;
       }
-      const T dr = block_reduce(pr, red);
-      const T di = block_reduce(pi, red);
-      if (tid == 0) s_c = (T)0.5 * (tau.x * dr + tau.y * di);
+      for (int o = 16; o > 0; o >>= 1) {
+        pr += __shfl_xor_sync(0xffffffffu, pr, o);
+        pi += __shfl_xor_sync(0xffffffffu, pi, o);
+      }
+      if (lane == 0) { red[warp] = pr; red2[warp] = pi; }
+      __syncthreads();
+      if (tid == 0) {
+        T dr = 0, di = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { dr += red[w]; di += red2[w]; }
+        s_c = (T)0.5 * (tau.x * dr + tau.y * di);
+      }
       __syncthreads();
     }
     const T cc = s_c;
@@ -341,32 +363,16 @@ __device__ __forceinline__ void eigh_tri_body(const double2* __restrict__ G, int
     out->gap = k < m ? (evals[k - 1] - evals[k]) / l1 : __longlong_as_double(0x7ff0000000000000ll);
     out->trace = s_trace;
     s_k = k;
-    // clusters among the ranks whose vectors are needed
-    const int nvec = all_vecs ? m : k;
-    const T ortol = (T)1e-3 * tnorm;
-    int ncl = 0;
-    for (int i = 0; i < nvec; ++i) snext[i] = -1;
-    // last rank seen per block start, to chain close eigenvalues of one block
-    short lastr[TRI_MAXM];
-    for (int i = 0; i < m; ++i) lastr[i] = -1;
-    for (int i = 0; i < nvec; ++i) {
-      const int pos = sorder[i];
-      const int lo = sblo[pos];
-      const int prev = lastr[lo];
-      if (prev >= 0 && slam[sorder[prev]] - slam[pos] <= ortol) {
-        snext[prev] = (short)i;
-      } else {
-        shead[ncl++] = (short)i;
-      }
-      lastr[lo] = (short)i;
-    }
-    s_ncl = ncl;
   }
   __syncthreads();
   const int nvec = all_vecs ? m : s_k;
   if (tid == 0) { const long long t = clock64(); t_ph[2] = t - t_mark; t_mark = t; }
 
-  // ---- 4. inverse iteration (warp per cluster, lane 0 runs the LU) ---------
+  // ---- 4. inverse iteration: one warp per needed eigenvector, all in parallel ----
+  // Each vector starts from its own pseudo-random vector, so vectors of nearly
+  // equal eigenvalues span their joint invariant subspace; the orthonormalisation
+  // below then gives an exact orthonormal basis of the kept (and, when needed,
+  // discarded) subspaces, which is what the truncation uses.
   {
     T* ws = (T*)smem_raw;  // per-warp scratch: dl, dd, du, du2, x (5 * m) + piv
     constexpr int NLU = LuWarps<T>::v;
@@ -377,104 +383,120 @@ __device__ __forceinline__ void eigh_tri_body(const double2* __restrict__ G, int
       T* du2 = du + TRI_MAXM;
       T* x = du2 + TRI_MAXM;
       unsigned char* piv = (unsigned char*)(x + TRI_MAXM);
-      for (int cl = warp; cl < s_ncl; cl += NLU) {
-        for (int i = shead[cl]; i >= 0; i = snext[i]) {
-          const int pos = sorder[i];
-          const int lo = sblo[pos], hi = sbhi[pos], s = hi - lo + 1;
-          T* z = gZ + (size_t)i * m;  // column i of Z, stored contiguously
-          for (int t = lane; t < m; t += 32) z[t] = 0;
+      for (int i = warp; i < nvec; i += NLU) {
+        const int pos = sorder[i];
+        const int lo = sblo[pos], hi = sbhi[pos], s = hi - lo + 1;
+        T* z = gZ + (size_t)i * m;  // column i of Z, stored contiguously
+        for (int t = lane; t < m; t += 32) z[t] = 0;
+        __syncwarp();
+        if (s == 1) {
+          if (lane == 0) z[lo] = 1;
           __syncwarp();
-          if (s == 1) {
-            if (lane == 0) z[lo] = 1;
-            __syncwarp();
-            continue;
+          continue;
+        }
+        const T lam = slam[pos];
+        if (lane == 0) {
+          // LU with partial pivoting of (T_block - lam I)
+          const T tiny = TEps<T>::v * tnorm;
+          for (int t = 0; t < s; ++t) {
+            dd[t] = sd[lo + t] - lam;
+            if (t < s - 1) { dl[t] = se[lo + t]; du[t] = se[lo + t]; du2[t] = 0; }
           }
-          const T lam = slam[pos];
+          for (int t = 0; t < s - 1; ++t) {
+            if (fabs(dd[t]) >= fabs(dl[t])) {
+              if (dd[t] == (T)0) dd[t] = tiny;
+              const T l = dl[t] / dd[t];
+              dl[t] = l;
+              dd[t + 1] -= l * du[t];
+              piv[t] = 0;
+            } else {
+              const T l = dd[t] / dl[t];
+              dd[t] = dl[t];
+              dl[t] = l;
+              const T tmp = du[t];
+              du[t] = dd[t + 1];
+              dd[t + 1] = tmp - l * dd[t + 1];
+              if (t < s - 2) {
+                du2[t] = du[t + 1];
+                du[t + 1] = -l * du[t + 1];
+              }
+              piv[t] = 1;
+            }
+          }
+          if (dd[s - 1] == (T)0) dd[s - 1] = tiny;
+        }
+        // pseudo-random start vector (integer hash of vector and row index)
+        for (int t = lane; t < s; t += 32) {
+          unsigned h = (unsigned)(t + 1) * 2654435761u ^ ((unsigned)(i + 7) * 40503u + 0x9e3779b9u);
+          h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12; h *= 0x297a2d39u; h ^= h >> 15;
+          const T u = (T)(h & 0xffffu) * (T)(1.0 / 65536.0) + (T)0.5;
+          x[t] = (h & 0x10000u) ? -u : u;
+        }
+        __syncwarp();
+        for (int it = 0; it < 2; ++it) {
           if (lane == 0) {
-            // LU with partial pivoting of (T_block - lam I)
-            const T tiny = TEps<T>::v * tnorm;
-            for (int t = 0; t < s; ++t) {
-              dd[t] = sd[lo + t] - lam;
-              if (t < s - 1) { dl[t] = se[lo + t]; du[t] = se[lo + t]; du2[t] = 0; }
-            }
             for (int t = 0; t < s - 1; ++t) {
-              if (fabs(dd[t]) >= fabs(dl[t])) {
-                if (dd[t] == (T)0) dd[t] = tiny;
-                const T l = dl[t] / dd[t];
-                dl[t] = l;
-                dd[t + 1] -= l * du[t];
-                piv[t] = 0;
+              if (piv[t] == 0) {
+                x[t + 1] -= dl[t] * x[t];
               } else {
-                const T l = dd[t] / dl[t];
-                dd[t] = dl[t];
-                dl[t] = l;
-                const T tmp = du[t];
-                du[t] = dd[t + 1];
-                dd[t + 1] = tmp - l * dd[t + 1];
-                if (t < s - 2) {
-                  du2[t] = du[t + 1];
-                  du[t + 1] = -l * du[t + 1];
-                }
-                piv[t] = 1;
+                const T tmp = x[t];
+                x[t] = x[t + 1];
+                x[t + 1] = tmp - dl[t] * x[t + 1];
               }
             }
-            if (dd[s - 1] == (T)0) dd[s - 1] = tiny;
+            x[s - 1] /= dd[s - 1];
+            x[s - 2] = (x[s - 2] - du[s - 2] * x[s - 1]) / dd[s - 2];
+            for (int t = s - 3; t >= 0; --t) x[t] = (x[t] - du[t] * x[t + 1] - du2[t] * x[t + 2]) / dd[t];
           }
-          // deterministic start vector
-          for (int t = lane; t < s; t += 32) x[t] = (T)1 + (T)0.25 * (T)((t * 7 + i * 3) % 11) / (T)11;
           __syncwarp();
-          for (int it = 0; it < 3; ++it) {
-            if (lane == 0) {
-              for (int t = 0; t < s - 1; ++t) {
-                if (piv[t] == 0) {
-                  x[t + 1] -= dl[t] * x[t];
-                } else {
-                  const T tmp = x[t];
-                  x[t] = x[t + 1];
-                  x[t + 1] = tmp - dl[t] * x[t + 1];
-                }
-              }
-              x[s - 1] /= dd[s - 1];
-              x[s - 2] = (x[s - 2] - du[s - 2] * x[s - 1]) / dd[s - 2];
-              for (int t = s - 3; t >= 0; --t) x[t] = (x[t] - du[t] * x[t + 1] - du2[t] * x[t + 2]) / dd[t];
-            }
-            __syncwarp();
-            // normalise (max-scaled first, so squares cannot overflow), then
-            // orthogonalise against earlier members of the cluster
-            for (int pass = 0; pass < 2; ++pass) {
-              T xmax = 0;
-              for (int t = lane; t < s; t += 32) xmax = fmax(xmax, fabs(x[t]));
-              for (int o = 16; o > 0; o >>= 1) xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-              if (!(xmax <= (T)3e38)) xmax = 0;  // inf or NaN: restart from a unit vector below
-              const T sx = xmax > (T)0 ? (T)1 / xmax : (T)0;
-              for (int t = lane; t < s; t += 32) x[t] = xmax > (T)0 ? x[t] * sx : (T)(t == 0);
-              __syncwarp();
-              T nrm = 0;
-              for (int t = lane; t < s; t += 32) nrm += x[t] * x[t];
-              for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-              const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)1;
-              for (int t = lane; t < s; t += 32) x[t] *= inv;
-              __syncwarp();
-              if (pass == 1) break;
-              for (int q = shead[cl]; q != i; q = snext[q]) {
-                const T* zq = gZ + (size_t)q * m + lo;
-                T dot = 0;
-                for (int t = lane; t < s; t += 32) dot += zq[t] * x[t];
-                for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-                for (int t = lane; t < s; t += 32) x[t] -= dot * zq[t];
-                __syncwarp();
-              }
-            }
-          }
-          for (int t = lane; t < s; t += 32) z[lo + t] = x[t];
+          // max-scale (squares cannot overflow), then unit norm
+          T xmax = 0;
+          for (int t = lane; t < s; t += 32) xmax = fmax(xmax, fabs(x[t]));
+          for (int o = 16; o > 0; o >>= 1) xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+          if (!(xmax <= (T)3e38)) xmax = 0;  // inf or NaN: restart from a unit vector
+          const T sx = xmax > (T)0 ? (T)1 / xmax : (T)0;
+          for (int t = lane; t < s; t += 32) x[t] = xmax > (T)0 ? x[t] * sx : (T)(t == 0);
+          __syncwarp();
+          T nrm = 0;
+          for (int t = lane; t < s; t += 32) nrm += x[t] * x[t];
+          for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+          const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)1;
+          for (int t = lane; t < s; t += 32) x[t] *= inv;
           __syncwarp();
         }
+        for (int t = lane; t < s; t += 32) z[lo + t] = x[t];
+        __syncwarp();
       }
     }
   }
   __syncthreads();
+  // ---- 4b. modified Gram-Schmidt over the needed vectors, in rank order --------
+  // Vectors of one block and well-separated eigenvalues are orthogonal already
+  // (the projections are at rounding level); near-equal eigenvalues get an
+  // orthonormal basis of their common invariant subspace.
+  {
+    __shared__ T s_inv;
+    for (int i = 0; i < nvec; ++i) {
+      T* zi = gZ + (size_t)i * m;
+      T part = 0;
+      for (int t = tid; t < m; t += blockDim.x) part += zi[t] * zi[t];
+      const T nrm = block_reduce(part, red);
+      if (tid == 0) s_inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)0;
+      __syncthreads();
+      const T inv = s_inv;
+      for (int t = tid; t < m; t += blockDim.x) zi[t] *= inv;
+      __syncthreads();
+      for (int j = i + 1 + warp; j < nvec; j += (blockDim.x >> 5)) {
+        T* zj = gZ + (size_t)j * m;
+        T dot = 0;
+        for (int t = lane; t < m; t += 32) dot += zi[t] * zj[t];
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        for (int t = lane; t < m; t += 32) zj[t] -= dot * zi[t];
+      }
+      __syncthreads();
+    }
+  }
 
-  if (tid == 0) { const long long t = clock64(); t_ph[3] = t - t_mark; t_mark = t; }
   // ---- 5. back-transform: y = H_0 (H_1 (... H_{m-2} z)) ----------------------
   // Each warp owns output columns (ranks); reflectors are staged in shared
   // memory TRI_CHUNK at a time, from the last to the first.

@@ -6,6 +6,9 @@
 
 namespace lret {
 
+// Last error text of this thread (read back by lr_status_string).
+void set_error(const char* fmt, const char* a, const char* b);
+
 // A row-group operator: G = 2 (one qubit) or 4 (two qubits) rows of V are
 // mixed by K matrices M[alpha] (G x G). The matrix index of a row is
 // 2*b(bits[0]) + b(bits[1]) for G = 4 and b(bits[0]) for G = 2.

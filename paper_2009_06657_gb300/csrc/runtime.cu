@@ -18,9 +18,12 @@
 using namespace lret;
 using zc = std::complex<double>;
 
-namespace {
-
+namespace lret {
 thread_local char g_errmsg[256];
+void set_error(const char* fmt, const char* a, const char* b) { snprintf(g_errmsg, sizeof(g_errmsg), fmt, a, b); }
+}  // namespace lret
+
+namespace {
 
 struct Stage {
   int type = 0;  // 0 = expansion, 1 = truncation
