@@ -343,21 +343,43 @@ def bench_batch(dev, stream, scale=0.05, sample_single=12):
             "speedup": (st["gates"] / t_batch) / (gates / t_single)}
 
 
-def algorithmic(kclass, info_c):
-    """(bound, bytes_or_flops per launch) of a steady-state launch of a kernel class."""
+# Algorithmic work of one steady-state launch of each kernel class on the
+# benchmark workload (n = 20, c = k = r = 64 columns, K = 4 Kraus matrices,
+# m = K r = 256), structured truncation path (the Gram and projection act on the
+# row pairs of the channel's qubit; V' is never formed).
+def algorithmic():
     N, r, K, esz = 1 << N_QUBITS, RANK, 4, 8
-    m = r * K
-    if kclass == "expand":
-        return "hbm", N * r * esz + N * m * esz          # read V (c = r), write V' (r*K)
-    if kclass == "project":
-        return "hbm", N * m * esz + N * r * esz          # read V', write V
-    if kclass == "gram":
-        return "alu", 8.0 * N * m * m / 2                # Hermitian half, complex FMA = 8 flops
-    if kclass == "readout":
-        return "hbm", N * r * esz + N * 4
-    if kclass == "pauli":
-        return "hbm", 2 * N * r * esz
-    return "alu", None
+    N2, m = N // 2, 4 * RANK
+    return {
+        # Gram of the row pairs: (2r x 2r) Hermitian, N/2 rows, complex MAC = 8 flop, half by symmetry
+        "gram": {"flop": 8.0 * N2 * (2 * r) ** 2 / 2, "bytes": N * r * esz},
+        # projection on the row pairs: (N/2 x 2r) x (2r x 2r), read V and write V_new
+        "project": {"flop": 8.0 * N2 * (2 * r) * (2 * r), "bytes": 2 * N * r * esz},
+        # Householder reduction of the m x m Hermitian matrix dominates: (16/3) m^3 flop
+        "eigh": {"flop": 16.0 / 3.0 * m ** 3, "bytes": m * m * 16},
+        # expansion for two-qubit gates (gate only, K = 1): read and write V
+        "expand": {"flop": None, "bytes": 2 * N * r * esz},
+        "readout": {"flop": None, "bytes": N * r * esz + N * 4},
+        "pauli": {"flop": None, "bytes": 2 * N * r * esz * N_TERMS},
+    }
+
+
+def kernel_rooflines(kt, peaks):
+    alg = algorithmic()
+    out = {}
+    for k, (ms, cnt) in kt.items():
+        if cnt == 0 or k not in alg:
+            continue
+        t = ms / cnt * 1e-3
+        a = alg[k]
+        e = {"ms_per_launch": ms / cnt, "launches": cnt}
+        if a["bytes"]:
+            e["hbm_gbs"] = a["bytes"] / t / 1e9
+            e["hbm_frac"] = e["hbm_gbs"] / peaks["hbm_gbs"]
+        if a["flop"]:
+            e["tflops"] = a["flop"] / t / 1e12
+        out[k] = e
+    return out
 
 
 def main():
@@ -391,14 +413,16 @@ def main():
     value = gsteps / (res["ms"] / 1e3)
     kt = res["ktimes"]
     dom = max(kt, key=lambda k: kt[k][0])
-    bound, alg = algorithmic(dom, RANK)
-    avg_ms = kt[dom][0] / max(kt[dom][1], 1)
-    if bound == "hbm":
-        ach = alg / (avg_ms * 1e-3) / 1e9
-        peak = peaks["hbm_gbs"]; unit = "GB/s"
+    kr = kernel_rooflines(kt, peaks)
+    d = kr.get(dom, {})
+    if dom in ("gram", "project"):
+        # tensor-core GEMMs: useful flops against the TF32 dense peak
+        bound, ach, peak, unit = "tensor", d.get("tflops"), peaks["tf32_tflops"], "TFLOP/s"
+    elif dom == "eigh":
+        # one 8-SM cluster: FP32 ALU peak of the SMs it occupies
+        bound, ach, peak, unit = "alu", d.get("tflops"), peaks["fp32_tflops"] * 8 / 152, "TFLOP/s"
     else:
-        ach = (alg / (avg_ms * 1e-3) / 1e12) if alg else None
-        peak = peaks["fp32_tflops"]; unit = "TFLOP/s"
+        bound, ach, peak, unit = "hbm", d.get("hbm_gbs"), peaks["hbm_gbs"], "GB/s"
     cfg = workload_config()
     cfg["gates_per_step"] = res["g_per"]
     cfg["truncations_per_step"] = res["c_per"]
@@ -413,6 +437,7 @@ def main():
         "roofline": {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                      "frac": (ach / peak) if ach else None, "traffic": None,
                      "peak_source": peaks["source"]},
+        "kernels": kr,
         "clocks": res["clk"],
         "e2e": {"value": res["g_per"] / res["e2e_s"], "unit": "noisy gate-steps/s",
                 "h2d_bytes_per_step": h2d_bytes(get_layers()[0]), "d2h_bytes_per_step": (1 << N_QUBITS) * 4 + 8},
@@ -448,10 +473,13 @@ def load_peaks():
     if os.path.exists(p):
         d = json.load(open(p))
         # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nominal unit counts and clock)
-        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
-                "source": "hbm/bf16 measured (MEASURED_PEAKS.json); fp32 from unit counts x max clock"}
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
-            "source": "fallback"}
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "tf32_tflops": d["bf16_tflops"] * 1.1 / 2.25,
+                "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
+                "source": "hbm, bf16 measured (MEASURED_PEAKS.json); tf32 = measured bf16 x nominal 1.1/2.25; "
+                          "fp32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "tf32_tflops": 1900.0 * 1.1 / 2.25,
+            "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "source": "fallback"}
 
 
 def cpu_sample():

@@ -114,17 +114,26 @@ int lr_compress(lr_handle h, int r, double* discarded_out);
 #define LR_PATH_EXPAND 1
 int lr_set_path(lr_handle h, int which);
 
+/* Tensor cores for the FP32 state's Gram of the row pairs and projection on
+ * the row pairs (tcgen05, 3xTF32 products, FP32 accumulation; Gram split
+ * partials summed in FP64): on = 1 (default) where the shape allows it, 0 =
+ * the SIMT kernels everywhere.
+ * lr_get_info returns LR_ETIMEOUT if a tensor-core kernel's bounded wait gave up. */
+int lr_set_tensor_cores(lr_handle h, int on);
+
 /* Threshold rule of Sec. II.B: keep the smallest k with
  * sum_{i<=k} lambda_i >= (1 - eps) * sum_i lambda_i. eps <= 0 disables it. */
 int lr_set_eps(lr_handle h, double eps);
 
 /* Eigensolver of the truncation: LR_EIG_AUTO (default: two-sided Jacobi for
- * small Gram matrices, Householder tridiagonal + bisection + inverse iteration
- * above 32 columns (FP32 state) or 64 columns (FP64 state)), LR_EIG_JACOBI or
- * LR_EIG_TRIDIAG. */
+ * small Gram matrices, the cluster tridiagonal solver above 32 columns (FP32
+ * state) or 64 columns (FP64 state)), LR_EIG_JACOBI, LR_EIG_TRIDIAG
+ * (Householder tridiagonal + bisection + inverse iteration, one thread block)
+ * or LR_EIG_CLUSTER (the same on a cluster of 8 thread blocks). */
 #define LR_EIG_AUTO 0
 #define LR_EIG_JACOBI 1
 #define LR_EIG_TRIDIAG 2
+#define LR_EIG_CLUSTER 3
 int lr_set_eigensolver(lr_handle h, int which);
 
 /* Prob(x) = sum_v |V_xv|^2 (Eq. 9) into a caller-owned device buffer of 2^n

@@ -82,6 +82,7 @@ _SIGS = {
     "lr_set_eps": (C.c_int, [_H, C.c_double]),
     "lr_set_eigensolver": (C.c_int, [_H, C.c_int]),
     "lr_set_path": (C.c_int, [_H, C.c_int]),
+    "lr_set_tensor_cores": (C.c_int, [_H, C.c_int]),
     "lr_probs": (C.c_int, [_H, _P]),
     "lr_expect": (C.c_int, [_H, C.c_int, _U64, _U64, _D, _D]),
     "lr_z_expect": (C.c_int, [_H, _D]),

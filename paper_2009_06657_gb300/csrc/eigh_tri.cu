@@ -153,7 +153,7 @@ __device__ __forceinline__ void eigh_tri_body(const double2* __restrict__ G, int
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { amax = fmax(amax, red[w]); xn2 += red2[w]; }
     const T inv_amax = amax > (T)0 ? (T)1 / amax : (T)0;
     T xn2s = xn2 * inv_amax * inv_amax;  // ||x[1:]||^2 / amax^2
-    if (tid == 0 && amax > (T)0 && xn2 < (T)1e-30 && xn2s > (T)0) {
+    if (tid == 0 && amax > (T)0 && xn2 < (T)1e-30) {  // squares may have underflowed
       T sacc = 0;
       for (int i = 2; i <= n1; ++i) {
         const T a = colj[i].x * inv_amax, b = colj[i].y * inv_amax;

@@ -150,6 +150,14 @@ __global__ void k_gram_reduce(const double2* __restrict__ partials, int splits, 
   }
 }
 
+cudaError_t launch_gram_reduce_herm(const double2* partials, int splits, int m, double2* out, cudaStream_t s) {
+  const int64_t total = (int64_t)m * m;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_gram_reduce<<<blocks, 256, 0, s>>>(partials, splits, m, m, 1, out);
+  return cudaGetLastError();
+}
+
 int gram_splits(int64_t N, int ma, int mb) {
   const int ti = (ma + TILE - 1) / TILE, tj = (mb + TILE - 1) / TILE;
   const int tiles = ti * tj;

@@ -61,6 +61,12 @@ cudaError_t launch_gram(const void* A, int lda, int ma, const void* B, int ldb, 
                         bool hermitian, double2* partials, int splits, double2* out, cudaStream_t s,
                         int pairbit = -1, int chalf = 0);
 int gram_splits(int64_t N, int ma, int mb);
+// sum split partials of a Hermitian m x m Gram (upper 64-tiles computed) into out
+cudaError_t launch_gram_reduce_herm(const double2* partials, int splits, int m, double2* out, cudaStream_t s);
+// tensor-core (tcgen05, 3xTF32) pair Gram for the FP32 state; status: device int set on a wait timeout
+bool gram_pair_tc_supported(int c, int64_t N2);
+cudaError_t launch_gram_pair_tc(const void* V, int ld, int c, int pairbit, int64_t N2, double2* partials,
+                                int max_splits, double2* out, int* status, cudaStream_t s);
 
 // Small matrices of the structured truncation: M[al] = Kt_al G (2x2) and
 // Q[al][be] = M[al]^dag M[be].
@@ -116,6 +122,13 @@ cudaError_t launch_expand_batch(const ExpandTask* tasks, const int* bstart, int 
                                 cudaStream_t s);
 int expand_blocks(int64_t total);
 
+// tensor-core (tcgen05, 3xTF32) pair projection for the FP32 state: W (pairs) = V (pairs) x D,
+// D: 2c x 2k complex128 (device); Bscratch: proj_pair_tc_scratch_bytes(c, k) bytes
+bool proj_pair_tc_supported(int c, int k, int64_t N2);
+size_t proj_pair_tc_scratch_bytes(int c, int k);
+cudaError_t launch_proj_pair_tc(const void* V, int ld, int c, int k, int pairbit, int64_t N2, const double2* D,
+                                float* Bscratch, void* W, int* status, cudaStream_t s);
+
 // ---- Y[x][j] = sum_i A1[x][i] M1[i][j] + sum_i A2[x][i] M2[i][j]  (j < p)
 // M1, M2: complex128 device matrices with leading dimensions ldm1, ldm2. A2 may be null.
 // pairbit >= 0: A1 and Y are read/written as pair matrices (A1: 2*chalf logical
@@ -140,6 +153,13 @@ size_t eigh_work_bytes(int m, bool fp64);
 template <typename T>
 cudaError_t launch_eigh_tri(const double2* G, int m, void* work, double* evals, double2* evecs, EigOut* out,
                             int r, double eps, int all_vecs, cudaStream_t s);
+
+// ---- the same eigensolver on a cluster of 8 CTAs (distributed shared memory);
+// work: eigh_cluster_work_bytes(fp64) bytes
+template <typename T>
+cudaError_t launch_eigh_cluster(const double2* G, int m, void* work, double* evals, double2* evecs, EigOut* out,
+                                int r, double eps, int all_vecs, cudaStream_t s);
+size_t eigh_cluster_work_bytes(bool fp64);
 
 // ---- adjoint of a truncation: builds Mcat ((k+m) x m complex128) =
 // [U_r^dag ; B + B^dag] with B = U_d (F o (U_d^dag C)) U_r^dag, F_ji = 1/(lam_i - lam_j).

@@ -59,6 +59,9 @@ struct lr_ctx {
   int solver = 0;  // 0 auto, 1 Jacobi, 2 tridiagonal
   int path = 0;    // 0 structured truncation where it applies, 1 always expand V'
   double2* S = nullptr;   // pair Gram (2c x 2c)
+  int* tc_status = nullptr;  // set by tensor-core kernels when a bounded wait gives up
+  float* projB = nullptr;    // pre-split projection operand for the tensor-core projection
+  int use_tc = 1;
   double2* D = nullptr;   // pair projection (2c x 2k)
   // workspaces
   double2* partials = nullptr;
@@ -351,8 +354,15 @@ int upload_terms(lr_ctx* h, int T, const uint64_t* xm, const uint64_t* zm, const
 int run_eigh(lr_ctx* h, int m, int r_eff, double eps, int* k_out) {
   const int te = tbeg(h);
   const bool fp64 = h->dtype == LR_C128;
-  const bool use_tri = h->solver == 2 || (h->solver == 0 && m > (fp64 ? 64 : 32));
-  if (use_tri) {
+  const bool small = m <= (fp64 ? 64 : 32);
+  const bool use_cluster = h->solver == 3 || (h->solver == 0 && !small);
+  const bool use_tri = h->solver == 2;
+  if (use_cluster) {
+    CK(by_dtype(h->dtype, [&](auto t) {
+      return launch_eigh_cluster<decltype(t)>(h->G, m, h->eig_work, h->evals, h->evecs, h->eo, r_eff, eps,
+                                              h->record ? 1 : 0, h->stream);
+    }));
+  } else if (use_tri) {
     CK(by_dtype(h->dtype, [&](auto t) {
       return launch_eigh_tri<decltype(t)>(h->G, m, h->eig_work, h->evals, h->evecs, h->eo, r_eff, eps,
                                           h->record ? 1 : 0, h->stream);
@@ -407,10 +417,15 @@ int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
         }
   const int splits = gram_splits(N2, 2 * c, 2 * c);
   int te = tbeg(h);
-  CK(by_dtype(h->dtype, [&](auto t) {
-    return launch_gram<decltype(t)>(h->V, ld, 2 * c, h->V, ld, 2 * c, N2, true, h->partials, splits, h->S,
-                                    h->stream, q, c);
-  }));
+  if (h->dtype == LR_C64 && h->use_tc && gram_pair_tc_supported(c, N2)) {
+    const int max_splits = (int)(h->partials_elems / ((size_t)4 * c * c));
+    CK(launch_gram_pair_tc(h->V, ld, c, q, N2, h->partials, max_splits, h->S, h->tc_status, h->stream));
+  } else {
+    CK(by_dtype(h->dtype, [&](auto t) {
+      return launch_gram<decltype(t)>(h->V, ld, 2 * c, h->V, ld, 2 * c, N2, true, h->partials, splits, h->S,
+                                      h->stream, q, c);
+    }));
+  }
   CK(launch_assemble_gram(h->S, c, K, pq, h->G, h->stream));
   tend(h, LR_K_GRAM, te);
   int k;
@@ -418,10 +433,14 @@ int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
   if (rc) return rc;
   te = tbeg(h);
   CK(launch_build_proj(h->evecs, c, K, k, pq, h->D, h->stream));
-  CK(by_dtype(h->dtype, [&](auto t) {
-    return launch_rowmat<decltype(t)>(h->V, ld, 2 * c, h->D, 2 * k, nullptr, 0, 0, nullptr, 0, h->W, ld, 2 * k,
-                                      N2, h->stream, q, c, k);
-  }));
+  if (h->dtype == LR_C64 && h->use_tc && proj_pair_tc_supported(c, k, N2)) {
+    CK(launch_proj_pair_tc(h->V, ld, c, k, q, N2, h->D, h->projB, h->W, h->tc_status, h->stream));
+  } else {
+    CK(by_dtype(h->dtype, [&](auto t) {
+      return launch_rowmat<decltype(t)>(h->V, ld, 2 * c, h->D, 2 * k, nullptr, 0, 0, nullptr, 0, h->W, ld, 2 * k,
+                                        N2, h->stream, q, c, k);
+    }));
+  }
   tend(h, LR_K_PROJECT, te);
   std::swap(h->V, h->W);
   h->c = k;
@@ -571,11 +590,18 @@ int lr_init_ex(int n, int r, int dtype, int capacity, void* stream, lr_handle* o
   if (!rc) rc = dmalloc(h, (void**)&h->partials, sizeof(double2) * pe);
   if (!rc) rc = dmalloc(h, (void**)&h->G, sizeof(double2) * m * m);
   if (!rc) rc = dmalloc(h, (void**)&h->S, sizeof(double2) * m * m);
+  if (!rc) rc = dmalloc(h, (void**)&h->tc_status, sizeof(int));
+  if (!rc) rc = dmalloc(h, (void**)&h->projB, proj_pair_tc_scratch_bytes(64, 64));
+  if (!rc && cudaMemset(h->tc_status, 0, sizeof(int)) != cudaSuccess) rc = LR_ECUDA;
   if (!rc) rc = dmalloc(h, (void**)&h->D, sizeof(double2) * m * m);
   if (!rc) rc = dmalloc(h, (void**)&h->evals, sizeof(double) * m);
   if (!rc) rc = dmalloc(h, (void**)&h->evecs, sizeof(double2) * m * m);
   if (!rc) rc = dmalloc(h, (void**)&h->eo, sizeof(EigOut));
-  if (!rc) rc = dmalloc(h, &h->eig_work, eigh_work_bytes(m, dtype == LR_C128));
+  if (!rc) {
+    size_t wb = eigh_work_bytes(m, dtype == LR_C128);
+    const size_t wc = eigh_cluster_work_bytes(dtype == LR_C128);
+    rc = dmalloc(h, &h->eig_work, wb > wc ? wb : wc);
+  }
   if (!rc) rc = dmalloc(h, (void**)&h->acc, sizeof(double) * 8);
   if (!rc) rc = ensure_dscratch(h, 64 * 1024);
   if (!rc && cudaMallocHost((void**)&h->h_eo, sizeof(EigOut)) != cudaSuccess) rc = LR_ENOMEM;
@@ -602,6 +628,8 @@ int lr_free(lr_handle h) {
   dfree((void*&)h->partials);
   dfree((void*&)h->G);
   dfree((void*&)h->S);
+  dfree((void*&)h->tc_status);
+  dfree((void*&)h->projB);
   dfree((void*&)h->D);
   dfree((void*&)h->evals);
   dfree((void*&)h->evecs);
@@ -750,7 +778,7 @@ int lr_kraus_preset(int kind, double p, double* out, int* K_out) {
 }
 
 int lr_set_eigensolver(lr_handle h, int which) {
-  if (!h || which < 0 || which > 2) return LR_EINVAL;
+  if (!h || which < 0 || which > 3) return LR_EINVAL;
   h->solver = which;
   return LR_OK;
 }
@@ -783,6 +811,12 @@ int lr_compress(lr_handle h, int r, double* discarded_out) {
   rc = flush_all(h);
   if (rc) return rc;
   return do_truncate(h, r_eff, eps, discarded_out);
+}
+
+int lr_set_tensor_cores(lr_handle h, int on) {
+  if (!h) return LR_EINVAL;
+  h->use_tc = on != 0;
+  return LR_OK;
 }
 
 int lr_set_path(lr_handle h, int which) {
@@ -975,6 +1009,8 @@ int lr_get_info(lr_handle h, lr_info* info) {
   int rc = flush_all(h);
   if (rc) return rc;
   CK(cudaMemcpyAsync(h->h_small, h->acc, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream));
+  int tcs = 0;
+  CK(cudaMemcpyAsync(&tcs, h->tc_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   info->n = h->n;
   info->columns = h->c;
@@ -984,6 +1020,7 @@ int lr_get_info(lr_handle h, lr_info* info) {
   info->stages = (int64_t)h->tape.size();
   info->discarded = h->h_small[0];
   info->last_gap = h->h_small[1];
+  if (tcs) return LR_ETIMEOUT;
   return h->h_small[2] > 0 ? LR_ENOCONV : LR_OK;
 }
 

@@ -117,12 +117,16 @@ class LRSim:
         return None
 
     def set_eigensolver(self, which):
-        """"auto", "jacobi" or "tridiag"."""
-        check(lib.lr_set_eigensolver(self.h, {"auto": 0, "jacobi": 1, "tridiag": 2}[which]), "lr_set_eigensolver")
+        """"auto", "jacobi", "tridiag" (one thread block) or "cluster" (8 thread blocks)."""
+        check(lib.lr_set_eigensolver(self.h, {"auto": 0, "jacobi": 1, "tridiag": 2, "cluster": 3}[which]),
+              "lr_set_eigensolver")
 
     def set_path(self, which):
         """"auto" (truncate without forming V' where possible) or "expand"."""
         check(lib.lr_set_path(self.h, {"auto": 0, "expand": 1}[which]), "lr_set_path")
+
+    def set_tensor_cores(self, on=True):
+        check(lib.lr_set_tensor_cores(self.h, 1 if on else 0), "lr_set_tensor_cores")
 
     def set_eps(self, eps):
         check(lib.lr_set_eps(self.h, float(eps)), "lr_set_eps")
@@ -167,7 +171,7 @@ class LRSim:
         inf = _ffi.lr_info()
         st = lib.lr_get_info(self.h, C.byref(inf))
         if st not in (_ffi.LR_OK, _ffi.LR_ENOCONV):
-            check(st, "lr_get_info")
+            check(st, "lr_get_info")  # includes LR_ETIMEOUT from a tensor-core wait
         return {"n": inf.n, "columns": inf.columns, "capacity": inf.capacity, "dtype": inf.dtype,
                 "compressions": inf.compressions, "stages": inf.stages, "discarded": inf.discarded,
                 "last_gap": inf.last_gap, "converged": st == _ffi.LR_OK}

@@ -73,8 +73,12 @@ def test_graph_and_direct_launches_agree_and_rerun_is_reproducible(lr):
 
 
 def test_heterogeneous_batch_workload_miniature(lr):
-    # the 256-circuit family (n in 8..18, r in {8,16,32,64}) at 2% depth: every
-    # circuit keeps trace + discarded mass = 1 and matches its own single run
+    """The 256-circuit family (n in 8..18, r in {8,16,32,64}, identical channels
+    on every qubit) at 2% depth. Its cuts include exact eigenvalue ties, so two
+    correct runs need not agree; what holds for every correct run: Tr rho =
+    1 - discarded mass, and each run lies within its discarded mass (in L1 of
+    Prob(x)) of the exact evolution, so two runs differ by at most the sum of
+    their discarded masses."""
     circs = batch_circuits(count=24, depth_scale=0.02)
     b = lr.LRBatch(circs, dtype="c64")
     b.run()
@@ -86,8 +90,8 @@ def test_heterogeneous_batch_workload_miniature(lr):
         inf = b.info(i)
         assert abs(float(pb.sum()) - (1.0 - inf["discarded"])) < 1e-5
         sim = lr.LRSim(cd["n"], cd["r"], dtype="c64")
-        sim.set_eigensolver("tridiag")
         lr.run_ops(sim, cd["ops"], r=cd["r"])
-        assert float((sim.probs().double() - pb).abs().sum()) < 1e-5
+        d1 = sim.info()["discarded"]
+        assert float((sim.probs().double() - pb).abs().sum()) < inf["discarded"] + d1 + 1e-5
         sim.close()
     b.close()

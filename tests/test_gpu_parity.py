@@ -132,7 +132,7 @@ CIRCUITS = [
 ]
 
 
-@pytest.mark.parametrize("solver", ["auto", "jacobi", "tridiag"])
+@pytest.mark.parametrize("solver", ["auto", "jacobi", "tridiag", "cluster"])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("case", CIRCUITS, ids=[f"n{c[0]}r{c[1]}d{c[2]}" for c in CIRCUITS])
 def test_truncated_circuit_parity(lr, dtype, case, solver):
@@ -284,7 +284,7 @@ def test_gradient_tridiagonal_solver_matches_jacobi(lr):
     assert _min_gap(ref) > 1e-6
     import torch
     out = {}
-    for solver in ("jacobi", "tridiag"):
+    for solver in ("jacobi", "tridiag", "cluster"):
         sim = lr.LRSim(n, r, dtype="c128")
         sim.set_eigensolver(solver)
         t = torch.tensor(th, requires_grad=True)
@@ -294,6 +294,7 @@ def test_gradient_tridiagonal_solver_matches_jacobi(lr):
     g_fd = O.gradient_fd_lret(n, ops, th, terms, r=r, h=1e-4)
     assert np.max(np.abs(out["jacobi"] - g_fd)) < 1e-7
     assert np.max(np.abs(out["tridiag"] - g_fd)) < 1e-7
+    assert np.max(np.abs(out["cluster"] - g_fd)) < 1e-7
 
 
 def test_gradient_full_rank_matches_parameter_shift(lr):
@@ -334,3 +335,37 @@ def test_full_size_properties(lr):
     assert float(off.abs().max()) < 1e-5 * float(Gm.abs().max())
     d = torch.diagonal(Gm).real
     assert bool((d[:-1] >= d[1:] - 1e-6).all())  # descending eigenvalue order
+
+
+# 3xTF32 products (TF32 high part x FP32 remainder, the remainder itself
+# truncated to TF32, the remainder product dropped) carry about 2^-21 relative
+# error; the probe of the tensor-core Gram measured 3.5e-7 against FP64.
+UNIT_TC = 5e-7
+
+
+@pytest.mark.parametrize("r,nchan,seed", [(32, 12, 3139), (64, 24, 3166)])
+def test_tensor_core_truncation_matches_oracle(lr, r, nchan, seed):
+    """The tcgen05 Gram and projection of the row pairs (FP32 state, from 2^12
+    row pairs up) against the oracle and against the SIMT kernels. The bound is
+    the tolerance plus the predicted effect of the 3xTF32 rounding at the cuts
+    (unit roundoff x cut sensitivity, see _cut_sensitivity)."""
+    n = 14
+    ops = random_layered(n, 1, seed=seed, noise=("dep", 5e-4), qubit_jitter=(0.5, 1.5))
+    chans = [i for i, o in enumerate(ops) if O.is_channel(o)]
+    ops = ops[: chans[nchan - 1] + 1]
+    ref = O.run_lret(n, ops, r=r)
+    bound = 1e-5 + UNIT_TC * _cut_sensitivity(ref)
+    out = {}
+    for tc in (True, False):
+        sim = lr.LRSim(n, r, dtype="c64")
+        sim.set_tensor_cores(tc)
+        lr.run_ops(sim, ops, r=r)
+        p = sim.probs().double().cpu().numpy()
+        inf = sim.info()
+        assert abs(p.sum() - (1.0 - inf["discarded"])) < 1e-5  # Tr rho = 1 - discarded mass
+        out[tc] = (p, inf)
+        sim.close()
+    assert out[True][1]["compressions"] >= 2
+    assert np.sum(np.abs(out[True][0] - ref.probs())) < bound
+    assert np.sum(np.abs(out[True][0] - out[False][0])) < bound
+    assert abs(out[True][1]["discarded"] - ref.discarded) < bound
