@@ -66,6 +66,26 @@ def count(ops):
     return count_ops(ops)
 
 
+def max_over_ranks(ms, world, device=None):
+    """Slowest rank's time (replicas run independent circuits; the job ends when
+    the last one does). Barrier on both sides so no rank starts the next phase
+    early."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def aggregate_value(units_per_rank, world, ms_max):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -156,12 +176,7 @@ def run_ours(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-            torch.distributed.barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
 
         # per-kernel device time over one more step (CUDA events on the handle's stream)
         sim.set_timing(True)
@@ -409,8 +424,7 @@ def main():
         return
     import json as _j
     peaks = load_peaks()
-    gsteps = res["g_per"] * args.steps * world
-    value = gsteps / (res["ms"] / 1e3)
+    value = aggregate_value(res["g_per"] * args.steps, world, res["ms"])
     kt = res["ktimes"]
     dom = max(kt, key=lambda k: kt[k][0])
     kr = kernel_rooflines(kt, peaks)
