@@ -169,11 +169,13 @@ def run_ours(args, rank, world):
         clocks.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        n_launch0 = lr.launch_count()
         e0.record(stream)
         for i in range(args.steps):
             step(args.warmup + i)
         sim.expect_masks(xm, zm, cf)  # readout of <H> at the end of the timed region
         e1.record(stream)
+        n_launch = lr.launch_count() - n_launch0
         torch.cuda.synchronize()
         clk = clocks.stop()
         ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
@@ -206,7 +208,7 @@ def run_ours(args, rank, world):
     adj = bench_adjoint(dev, stream) if (rank == 0 and not args.no_adjoint) else None
     bat = bench_batch(dev, stream, scale=args.batch_scale) if (rank == 0 and not args.no_batch) else None
     return dict(ms=ms, g_per=g_per, c_per=c_per, ktimes=ktimes, clk=clk, e2e_s=e2e_s, fp64=fp64, info=info,
-                adjoint=adj, batch=bat)
+                adjoint=adj, batch=bat, launches=n_launch)
 
 
 def bench_fp64(args, layers, dev, stream):
@@ -397,8 +399,27 @@ def kernel_rooflines(kt, peaks):
     return out
 
 
+def profile_case(n):
+    """A short run for profilers: the first 12 ops of the benchmark's circuit
+    family on n qubits (r = 64), which reach 64 columns and then truncate the
+    256-column Gram matrix through the tensor-core Gram, the cluster
+    eigensolver and the tensor-core projection."""
+    import torch
+
+    import paper_2009_06657_gb300 as lr
+    from workloads import random_layered
+    ops = random_layered(n, 1, seed=SEED, noise=("dep", P_DEP))
+    sim = lr.LRSim(n, RANK, dtype="c64")
+    lr.run_ops(sim, ops[:12], r=RANK)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": n, "info": {k: v for k, v in sim.info().items() if isinstance(v, (int, float))}}))
+    sim.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", type=int, default=0,
+                    help="run only a short n-qubit case for profilers (no timing) and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -409,6 +430,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-scale", type=float, default=0.05)
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
@@ -457,8 +481,7 @@ def main():
                 "h2d_bytes_per_step": h2d_bytes(get_layers()[0]), "d2h_bytes_per_step": (1 << N_QUBITS) * 4 + 8},
         "fp64": None, "cpu_baseline": None, "adjoint": res.get("adjoint"), "batch": res.get("batch"),
     }
-    launches = sum(v[1] for v in kt.values())
-    out["gpu_launches"] = launches * args.steps
+    out["gpu_launches"] = res["launches"]  # the library's own launch counter over the timed region
     if res["fp64"]:
         f = res["fp64"]
         tps = res["c_per"] / res["g_per"]  # truncations per gate-step

@@ -118,7 +118,8 @@ int lr_set_path(lr_handle h, int which);
  * the row pairs (tcgen05, 3xTF32 products, FP32 accumulation; Gram split
  * partials summed in FP64): on = 1 (default) where the shape allows it, 0 =
  * the SIMT kernels everywhere.
- * lr_get_info returns LR_ETIMEOUT if a tensor-core kernel's bounded wait gave up. */
+ * lr_get_info returns LR_ETIMEOUT if a bounded wait in a tensor-core kernel or
+ * in the cluster eigensolver gave up. */
 int lr_set_tensor_cores(lr_handle h, int on);
 
 /* Threshold rule of Sec. II.B: keep the smallest k with
@@ -284,6 +285,12 @@ int lr_set_timing(lr_handle h, int on);
 int lr_kernel_times(lr_handle h, double* ms_out, int64_t* counts_out);
 
 const char* lr_status_string(int status);
+
+/* Number of GPU kernels this library has launched in this process, over all
+ * handles and batches (a replay of a batch's CUDA graph adds the kernels in
+ * the graph). For counting launches inside a measured region: read it before
+ * and after. Never fails. */
+int64_t lr_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -5,4 +5,4 @@ Gram, eigensolve, projection and readouts run in the CUDA library liblret
 (C ABI in include/lret.h). This package is its Python binding.
 """
 from ._ffi import LIB_PATH, LRError, exported_symbols  # noqa: F401
-from .sim import LRBatch, LRExpectation, LRSim, kraus_preset, pauli_masks, run_ops  # noqa: F401
+from .sim import LRBatch, LRExpectation, LRSim, kraus_preset, launch_count, pauli_masks, run_ops  # noqa: F401

@@ -105,6 +105,7 @@ _SIGS = {
                                  C.POINTER(C.c_int64)]),
     "lr_batch_free": (C.c_int, [_H]),
     "lr_status_string": (C.c_char_p, [C.c_int]),
+    "lr_launch_count": (C.c_int64, []),
 }
 
 for _name, (_res, _args) in _SIGS.items():

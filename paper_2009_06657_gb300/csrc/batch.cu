@@ -80,6 +80,7 @@ struct lr_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int use_graph = 1;
+  long long graph_kernels = 0;  // kernels in the captured graph
   int64_t launches = 0, gates = 0, truncs = 0, expands = 0;
   size_t bytes = 0;
 };
@@ -427,7 +428,11 @@ int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_p
     // the whole schedule becomes one graph
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+      const long long before = lret::launches_total();
       rc = enqueue(b);
+      // captured launches run on each replay, not now
+      b->graph_kernels = lret::launches_total() - before;
+      lret::note_launches(-b->graph_kernels);
       cudaGraph_t g = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
       if (!rc && e2 == cudaSuccess) {
@@ -454,6 +459,7 @@ int lr_batch_run(lr_batch_handle b) {
   if (!b) return LR_EINVAL;
   if (b->exec) {
     BCK(cudaGraphLaunch(b->exec, b->stream));
+    lret::note_launches(b->graph_kernels);
     return LR_OK;
   }
   return enqueue(b);

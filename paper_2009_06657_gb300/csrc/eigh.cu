@@ -237,6 +237,7 @@ cudaError_t launch_eigh(const double2* G, int m, void* work, double* evals, doub
     if (e != cudaSuccess) return e;
   }
   k_eigh_jacobi<T><<<1, EIG_THREADS, dyn, s>>>(G, m, (cx<T>*)work, use_smem, evals, evecs, out, r, eps);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -4,27 +4,43 @@
 // back-transform), spread over CL = 8 CTAs (8 SMs) with distributed shared
 // memory.
 //
-// Data layout: the full Hermitian matrix (G / trace, both triangles) is held in
-// shared memory by rows, row i in CTA i % CL (m / CL rows per CTA, at most
-// 32 x 256 complex). Step j of the reduction:
-//   * the owner of row j forms x = conj(A[j][j+1:]) (= column j below the
-//     diagonal), the reflector H_j = I - tau v v^dag with H_j^dag x = beta e_1,
-//     and writes v and tau into every CTA's shared memory;           [barrier]
-//   * every CTA forms p_i = tau sum_c A[i][c] v_c for its rows, writes them and
-//     its share of v^dag p into every CTA;                           [barrier]
-//   * every CTA forms w = p - (1/2) conj(tau) (v^dag p) v and updates its rows,
-//     A[i][c] -= v_i conj(w_c) + w_i conj(v_c).
-// v and p live in two alternating buffers, so two cluster barriers per step
-// suffice. The reflectors are also written to global memory for the
-// back-transform. Eigenvalue bisection, inverse iteration and the
-// back-transform are divided over the CTAs by eigenvalue / vector index; the
-// orthonormalisation of the kept vectors (modified Gram-Schmidt, sequential in
-// the vector index) runs on CTA 0.
+// Data layout during the reduction: the Hermitian matrix G / trace (both
+// triangles) is distributed by rows, row i in CTA i % CL, and held in registers:
+// warp w of a CTA holds its local rows w and w + 16, lane l the columns l + 32 e
+// (at most 32 rows x 256 columns per CTA). Every CTA holds the current reflector
+// v_j, tau_j (H_j = I - tau v v^dag, H_j^dag x = beta e_1 for x = conj(A[j][j+1:])).
+// Step j:
+//   * every CTA forms p_i = tau sum_c A[i][c] v_c for its rows and sends them,
+//     with one partial of v^dag p per warp, to every CTA           [barrier]
+//   * every warp updates its rows, A[i][c] -= v_i conj(w_c) + w_i conj(v_c) with
+//     w = p - (1/2) conj(tau)(v^dag p) v; the warp holding row j + 3 also stores
+//     it in global memory;
+//   * warps 0-3 (the reflector group) form v_{j+1}, tau_{j+1} from their shared-
+//     memory copy of row j + 1 (stored by its owner two steps earlier, copied with
+//     cp.async one step earlier) after applying the updates of steps j - 1 and j
+//     to it, then start the copy of row j + 2. Every CTA computes the same
+//     reflector, so there is no second exchange: one cluster barrier per step.
+// The step state (v, p, partials, tau) rotates through three slots because a
+// CTA may run one step ahead of another. One CTA also writes each reflector to
+// global memory for the back-transform.
+//
+// Eigenvalues: multisection (each eigenvalue is bracketed by 16 threads that
+// evaluate the Sturm count at 16 interior points, a 17-fold shrink per round).
+// Eigenvectors of T: inverse iteration, one warp per vector (the serial LU and
+// solves carry their running values in registers); then modified Gram-Schmidt
+// of the needed vectors on CTA 0 with the vectors held in registers (one
+// barrier per vector). Back-transform y = H_0 (H_1 (... H_{m-2} z)): one warp per column,
+// the column in registers, reflectors staged in shared memory 32 at a time (one
+// bulk asynchronous copy per block) and
+// applied in groups of 4 (FP32) or 2 (FP64): the group's inner products
+// v_k^dag y are reduced together and corrected with the reflectors' own inner
+// products v_k^dag v_l.
 #include <cooperative_groups.h>
 #include <float.h>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -34,8 +50,15 @@ namespace {
 
 constexpr int CL = 8;
 constexpr int CL_THREADS = 512;
+constexpr int CL_NW = CL_THREADS / 32;
 constexpr int CL_MAXM = 256;
 constexpr int CL_ROWS = CL_MAXM / CL;  // rows per CTA at most
+constexpr int MS = 16;                 // threads (and interior points) per eigenvalue in multisection
+constexpr int BT_STAGE = 32;           // reflectors staged per shared-memory block in the back-transform
+template <typename T> struct BtGroup { static constexpr int v = 4; };  // reflectors applied together
+template <> struct BtGroup<double> { static constexpr int v = 2; };  // (register budget of 512 threads)
+template <typename T> struct MgsSlots { static constexpr int v = 4; };  // vectors per warp held in registers
+template <> struct MgsSlots<double> { static constexpr int v = 2; };
 
 template <typename T> struct CEps;
 template <> struct CEps<float> { static constexpr float v = FLT_EPSILON; static constexpr float tiny = 1e-30f; };
@@ -66,17 +89,158 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 template <typename T>
 struct ClusterShared {
-  cx<T> A[CL_ROWS][CL_MAXM];  // this CTA's rows (row i = CL * li + rank)
-  cx<T> v[2][CL_MAXM];        // reflector of step j in buffer j & 1 (rows j+1..m-1)
-  cx<T> p[2][CL_MAXM];
-  T dotp[2][CL][2];           // per-CTA shares of v^dag p (re, im)
-  cx<T> tau[2];
+  cx<T> A[CL_ROWS][CL_MAXM];  // this CTA's rows (row i = CL * li + rank); later scratch
+  // state of step j in slot j % 3 (a step reads the slots of j and j - 1 while
+  // faster CTAs already write slot j + 1)
+  cx<T> v[3][CL_MAXM];        // reflector (rows j+1..m-1)
+  cx<T> p[3][CL_MAXM];        // p = tau A v, all rows (each CTA sends its own)
+  cx<T> dpart[3][CL * CL_NW]; // per-warp partials of v^dag p, all CTAs
+  cx<T> tau[3];
+  T ccs[3];                   // (1/2) Re(conj(tau) v^dag p)
+  __align__(16) cx<T> nrow[2][CL_MAXM];  // prefetched copy of a future step's row
+  T gred[4][2];               // reflector group: per-warp max and sum of squares
+  cx<T> gscl;                 // reflector group: alpha
+  T zb[2][CL_MAXM];           // orthonormalisation: the vector being projected out
+  cx<T> gram[BT_STAGE / BtGroup<T>::v][BtGroup<T>::v][BtGroup<T>::v];  // v_k^dag v_l, staged reflectors
+  cx<T> btau[BT_STAGE];
   T d[CL_MAXM], e[CL_MAXM], e2[CL_MAXM], lam[CL_MAXM];
   short sblo[CL_MAXM], sbhi[CL_MAXM], order[CL_MAXM];
-  T red[32];
   int k;
   double trace, dred[32];
+  unsigned long long mbar;    // back-transform staging (bulk copy completion)
+#ifdef LRET_EIG_PROFILE
+  long long gdbg[4];          // diagnostic build: reflector-group sub-steps
+#endif
 };
+
+// The reflector group (warps 0-3) of every CTA forms the same v_{j+1},
+// tau_{j+1} from row j + 1. The row's owner stored it in global memory during
+// step j - 2 (as updated through that step); the group copied it into shared
+// memory during step j - 1 (cp.async), and at step j applies the updates of
+// steps j - 1 and j to it and forms H = I - tau v v^dag with H^dag x = beta e_1,
+// x = conj(row[j+2:]) (scaled norms, no underflow).
+constexpr int RG = 128;  // reflector group threads
+
+__device__ __forceinline__ void bar_group() { asm volatile("barrier.sync 2, %0;" ::"n"(RG) : "memory"); }
+
+// copy of columns [c0, m) of a stored row into shared memory, 16 bytes per cp.async
+template <typename T>
+__device__ __forceinline__ void prefetch_row(cx<T>* dst, const cx<T>* src, int c0, int m, int gt) {
+  constexpr int PER = 16 / sizeof(cx<T>);
+  for (int g = c0 / PER + gt; g < (m + PER - 1) / PER; g += RG) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + g * PER);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + g * PER) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// row r's update of step s: a -= v_r conj(w_c) + w_r conj(v_c), w = p - cc v
+template <typename T>
+__device__ __forceinline__ cx<T> upd1(const ClusterShared<T>& sh, int sl, T cc, int r, int col, cx<T> a) {
+  const cx<T> vr = sh.v[sl][r], vc = sh.v[sl][col];
+  const cx<T> wr = csub(sh.p[sl][r], cscale(vr, cc)), wc = csub(sh.p[sl][col], cscale(vc, cc));
+  return csub(a, cadd(cmul(vr, conjg(wc)), cmul(wr, conjg(vc))));
+}
+
+template <typename T>
+__device__ void group_reflector(ClusterShared<T>& sh, const cx<T>* __restrict__ row, int jr, int m, int slv,
+                                int sl0, bool up0, int sl1, bool up1, bool store, cx<T>* __restrict__ gref,
+                                int gt) {
+  const int lane = gt & 31, w = gt >> 5;
+#ifdef LRET_EIG_PROFILE
+  long long gq = clock64();
+#define LRET_GSTEP(k) if (gt == 0) { const long long g2 = clock64(); sh.gdbg[k] += g2 - gq; gq = g2; }
+#else
+#define LRET_GSTEP(k)
+#endif
+  // this thread's entries of row jr: columns jr + gt and jr + gt + RG (the
+  // diagonal, column jr, is entry 0)
+  cx<T> x[2];
+  T amax = 0, part = 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int col = jr + gt + h * RG;
+    cx<T> a = mk<T>(0, 0);
+    if (col < m) {
+      a = row[col];
+      if (up0) a = upd1(sh, sl0, sh.ccs[sl0], jr, col, a);
+      if (up1) a = upd1(sh, sl1, sh.ccs[sl1], jr, col, a);
+      if (col == jr) a.y = 0;
+      if (col > jr) {
+        amax = fmax(amax, fmax(fabs(a.x), fabs(a.y)));
+        if (col > jr + 1) part += a.x * a.x + a.y * a.y;
+      }
+    }
+    x[h] = a;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    part += __shfl_xor_sync(0xffffffffu, part, o);
+  }
+  if (lane == 0) { sh.gred[w][0] = amax; sh.gred[w][1] = part; }
+  if (gt == 0) sh.d[jr] = x[0].x;
+  if (gt == 1) sh.gscl = conjg(x[0]);  // alpha = conj(A[jr][jr+1]) (entry 1)
+  LRET_GSTEP(0)
+  bar_group();
+  LRET_GSTEP(1)
+  const T am = fmax(fmax(sh.gred[0][0], sh.gred[1][0]), fmax(sh.gred[2][0], sh.gred[3][0]));
+  const T x2 = (sh.gred[0][1] + sh.gred[1][1]) + (sh.gred[2][1] + sh.gred[3][1]);
+  const T inv = am > (T)0 ? (T)1 / am : (T)0;
+  T xn2s = x2 * inv * inv;
+  const cx<T> alpha = sh.gscl;
+  if (am > (T)0 && x2 < (T)1e-30) {  // squares may have underflowed: sum scaled values
+    T sacc = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int col = jr + gt + h * RG;
+      if (col > jr + 1 && col < m) sacc += (x[h].x * inv) * (x[h].x * inv) + (x[h].y * inv) * (x[h].y * inv);
+    }
+    sacc = warp_sum(sacc);
+    bar_group();
+    if (lane == 0) sh.gred[w][1] = sacc;
+    bar_group();
+    xn2s = (sh.gred[0][1] + sh.gred[1][1]) + (sh.gred[2][1] + sh.gred[3][1]);
+  }
+  cx<T> tau, scale;
+  T beta;
+  if (am <= (T)1e-30 || (xn2s == (T)0 && alpha.y == (T)0)) {
+    tau = mk<T>(0, 0);
+    beta = alpha.x;
+    scale = mk<T>(0, 0);
+  } else {
+    const T ar = alpha.x * inv, ai = alpha.y * inv;
+    const T bs = -copysign(sqrt(ar * ar + ai * ai + xn2s), ar);
+    beta = am * bs;
+    tau = mk<T>((bs - ar) / bs, -ai / bs);
+    const T den = (ar - bs) * (ar - bs) + ai * ai;
+    scale = mk<T>((ar - bs) / den * inv, -ai / den * inv);
+  }
+  LRET_GSTEP(2)
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int col = jr + gt + h * RG;
+    if (col > jr && col < m) sh.v[slv][col] = col == jr + 1 ? mk<T>(1, 0) : cmul(conjg(x[h]), scale);
+  }
+  if (store) {  // full-length row of the reflector store: zero outside jr+1..m-1
+    cx<T>* gv = gref + (size_t)jr * CL_MAXM;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int col = jr + gt + h * RG;
+      if (col > jr && col < m) gv[col] = col == jr + 1 ? mk<T>(1, 0) : cmul(conjg(x[h]), scale);
+    }
+    for (int rr = gt; rr <= jr; rr += RG) gv[rr] = mk<T>(0, 0);
+    for (int rr = m + gt; rr < CL_MAXM; rr += RG) gv[rr] = mk<T>(0, 0);
+    if (gt == 0) reinterpret_cast<cx<T>*>(gref + (size_t)(CL_MAXM - 1) * CL_MAXM)[jr] = tau;  // tau row
+  }
+  if (gt == 0) {
+    sh.tau[slv] = tau;
+    sh.e[jr] = beta;
+  }
+  LRET_GSTEP(3)
+#undef LRET_GSTEP
+}
+
+__device__ __forceinline__ long long phase_clock() { return clock64(); }
 
 }  // namespace
 
@@ -90,11 +254,14 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nw = CL_THREADS / 32;
   const int nrows = (m - rank + CL - 1) / CL;  // rows rank, rank + CL, ...
-  ClusterShared<T>* peer[CL];
-#pragma unroll
-  for (int q = 0; q < CL; ++q) peer[q] = cluster.map_shared_rank(&sh, q);
+  // peer(q): CTA q's shared block (mapped on use; holding 8 pointers costs 16 registers)
+  auto peer = [&](int q) { return cluster.map_shared_rank(&sh, q); };
+  __shared__ long long t_ph[6];
+#ifdef LRET_EIG_PROFILE
+  if (tid < 4) sh.gdbg[tid] = 0;
+#endif
+  long long t0 = phase_clock();
 
   // ---- load G / trace (every CTA its rows) --------------------------------
   double tr = 0.0;
@@ -104,242 +271,332 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
   __syncthreads();
   const double gscale = sh.trace > 0.0 ? sh.trace : 1.0;
   const double ginv = 1.0 / gscale;
-  for (int e = tid; e < nrows * m; e += CL_THREADS) {
-    const int li = e / m, col = e % m;
-    const int i = li * CL + rank;
-    const double2 g = G[(size_t)i * m + col];
-    sh.A[li][col] = mk<T>((T)(g.x * ginv), (T)(g.y * ginv));
-  }
-  cluster.sync();
-
-  // ---- reduction to tridiagonal form ----------------------------------------
-  for (int j = 0; j < m - 1; ++j) {
-    const int n1 = m - j - 1;
-    const int buf = j & 1;
-    const int owner = j % CL;
-    if (rank == owner) {
-      // x = conj(A[j][j+1:]), alpha = x_0; scaled norms (no underflow)
-      const int lj = j / CL;
-      T amax = 0, part = 0;
-      for (int t = tid; t < n1; t += CL_THREADS) {
-        const cx<T> a = sh.A[lj][j + 1 + t];
-        amax = fmax(amax, fmax(fabs(a.x), fabs(a.y)));
-        if (t >= 1) part += a.x * a.x + a.y * a.y;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-        part += __shfl_xor_sync(0xffffffffu, part, o);
-      }
-      __syncthreads();
-      if (lane == 0) { sh.red[warp] = amax; sh.lam[warp] = part; }  // lam used as scratch here
-      __syncthreads();
-      __shared__ cx<T> s_tau, s_scale;
-      __shared__ T s_beta;
-      if (tid == 0) {
-        T am = 0, x2 = 0;
-        for (int w = 0; w < nw; ++w) { am = fmax(am, sh.red[w]); x2 += sh.lam[w]; }
-        const cx<T> alpha = conjg(sh.A[lj][j + 1]);
-        const T inv = am > (T)0 ? (T)1 / am : (T)0;
-        T xn2s = x2 * inv * inv;
-        if (am > (T)0 && x2 < (T)1e-30) {  // squares may have underflowed
-          T sacc = 0;
-          for (int t = 1; t < n1; ++t) {
-            const cx<T> a = sh.A[lj][j + 1 + t];
-            sacc += (a.x * inv) * (a.x * inv) + (a.y * inv) * (a.y * inv);
-          }
-          xn2s = sacc;
-        }
-        cx<T> tau, scale;
-        T beta;
-        if (am <= (T)1e-30 || (xn2s == (T)0 && alpha.y == (T)0)) {
-          tau = mk<T>(0, 0);
-          beta = alpha.x;
-          scale = mk<T>(0, 0);
-        } else {
-          const T ar = alpha.x * inv, ai = alpha.y * inv;
-          const T bs = -copysign(sqrt(ar * ar + ai * ai + xn2s), ar);
-          beta = am * bs;
-          tau = mk<T>((bs - ar) / bs, -ai / bs);
-          const T den = (ar - bs) * (ar - bs) + ai * ai;
-          scale = mk<T>((ar - bs) / den * inv, -ai / den * inv);
-        }
-        s_tau = tau;
-        s_scale = scale;
-        s_beta = beta;
-      }
-      __syncthreads();
-      const cx<T> tau = s_tau, scale = s_scale;
-      // v (rows j+1..m-1; v_{j+1} = 1) to every CTA and to global memory
-      cx<T>* gv = gref + (size_t)j * CL_MAXM;
-      for (int t = tid; t < n1; t += CL_THREADS) {
-        const cx<T> vt = t == 0 ? mk<T>(1, 0) : cmul(conjg(sh.A[lj][j + 1 + t]), scale);
-        gv[t] = vt;
+  // This CTA's rows live in registers during the reduction: warp w holds local
+  // rows w and w + 16 (rows CL w + rank, CL (w + 16) + rank), lane l columns
+  // l + 32 e.
+  constexpr int E = CL_MAXM / 32;
+  const int li0 = warp, li1 = warp + CL_NW;
+  const int i0 = li0 * CL + rank, i1 = li1 * CL + rank;
+  cx<T> A0[E], A1[E];
 #pragma unroll
-        for (int q = 0; q < CL; ++q) peer[q]->v[buf][j + 1 + t] = vt;
+  for (int e = 0; e < E; ++e) {
+    const int c = lane + 32 * e;
+    A0[e] = mk<T>(0, 0);
+    A1[e] = mk<T>(0, 0);
+    if (c < m) {
+      if (li0 < nrows) {
+        const double2 g = G[(size_t)i0 * m + c];
+        A0[e] = mk<T>((T)(g.x * ginv), (T)(g.y * ginv));
       }
-      if (tid < CL) peer[tid]->tau[buf] = tau;
-      if (tid == 0) {
-        // diagonal, off-diagonal and tau of T for every CTA
-        const T dj = sh.A[lj][j].x, be = s_beta;
-        for (int q = 0; q < CL; ++q) {
-          peer[q]->d[j] = dj;
-          peer[q]->e[j] = be;
-        }
-        reinterpret_cast<cx<T>*>(gref + (size_t)(CL_MAXM - 1) * CL_MAXM)[j] = tau;  // tau row of gref
+      if (li1 < nrows) {
+        const double2 g = G[(size_t)i1 * m + c];
+        A1[e] = mk<T>((T)(g.x * ginv), (T)(g.y * ginv));
       }
     }
-    cluster.sync();
-    const cx<T> tau = sh.tau[buf];
+  }
+  if (tid == 0) { const long long t1 = phase_clock(); t_ph[0] = t1 - t0; t0 = t1; }
+
+  // ---- reduction to tridiagonal form ----------------------------------------
+  // Every CTA holds v_j and tau_j. Step j: every CTA forms p_i = tau sum_c
+  // A[i][c] v_c for its rows and sends them, with one partial of v^dag p per
+  // warp, to every CTA [cluster barrier]. Then warps 4-15 update this CTA's rows,
+  // A[i][c] -= v_i conj(w_c) + w_i conj(v_c), w = p - (1/2) conj(tau)(v^dag p) v
+  // (the owner of row j + 3 also stores it in global memory), while warps 0-3
+  // form v_{j+1}, tau_{j+1} from their prefetched copy of row j + 1 and start the
+  // copy of row j + 2. Every CTA computes the same reflector, so one barrier per
+  // step suffices.
+  cx<T>* grow = reinterpret_cast<cx<T>*>(gZ + (size_t)CL_MAXM * CL_MAXM);  // three row buffers
+  // a warp's row into row buffer rb (columns from c0)
+  auto store_row = [&](const cx<T>(&R)[E], int rb, int c0) {
+    cx<T>* dst = grow + (size_t)rb * CL_MAXM;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int c = lane + 32 * e;
+      if (c >= c0 && c < m) dst[c] = R[e];
+    }
+  };
+  if (rank < 3 && rank < m && warp == 0) store_row(A0, rank, 0);  // rows 0, 1, 2 as loaded
+  cluster.sync();
+  if (tid < RG) {
+    // reflector 0 from row 0; row 1 into the prefetch buffer
+    prefetch_row<T>(sh.nrow[0], grow, 0, m, tid);
+    prefetch_row<T>(sh.nrow[1], grow + CL_MAXM, 1, m, tid);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    bar_group();
+    group_reflector<T>(sh, sh.nrow[0], 0, m, 0, 0, false, 0, false, rank == 0, gref, tid);
+  }
+  __syncthreads();
+#ifdef LRET_EIG_PROFILE
+  // diagnostic build: cycles of the reduction's sub-steps on CTA 0, thread 0
+  long long sp[6] = {0, 0, 0, 0, 0, 0}, tq = clock64();
+#define LRET_SUBSTEP(k) { const long long t2 = clock64(); sp[k] += t2 - tq; tq = t2; }
+#else
+#define LRET_SUBSTEP(k)
+#endif
+  for (int j = 0; j < m - 1; ++j) {
+    const int sl = j % 3, slp = (j + 2) % 3, sln = (j + 1) % 3;  // slots of steps j, j - 1, j + 1
+    const int nx = j + 1;
+    const cx<T> tau = sh.tau[sl];
     const bool skip = (tau.x == (T)0 && tau.y == (T)0);
-    // p_i = tau sum_c A[i][c] v_c for local rows i > j; v^dag p share
-    T dr = 0, di = 0;
-    if (!skip) {
-      for (int li = warp; li < nrows; li += nw) {
-        const int i = li * CL + rank;
-        if (i <= j) continue;
-        cx<T> acc = mk<T>(0, 0);
-        for (int col = j + 1 + lane; col < m; col += 32) cfma(acc, sh.A[li][col], sh.v[buf][col]);
-        acc.x = warp_sum(acc.x);
-        acc.y = warp_sum(acc.y);
-        const cx<T> pi = cmul(tau, acc);
-        if (lane < CL) peer[lane]->p[buf][i] = pi;
-        if (lane == 0) {
-          const cx<T> vi = sh.v[buf][i];
+    const bool a0 = li0 < nrows && i0 > j, a1 = li1 < nrows && i1 > j;
+    {
+      // p_i = tau sum_c A[i][c] v_c for this warp's rows (two, reduced together)
+      T dr = 0, di = 0;
+      if (!skip && (a0 || a1)) {
+        cx<T> acc0 = mk<T>(0, 0), acc1 = mk<T>(0, 0);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int c = lane + 32 * e;
+          if (c > j && c < m) {
+            const cx<T> vc = sh.v[sl][c];
+            cfma(acc0, A0[e], vc);
+            cfma(acc1, A1[e], vc);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          acc0.x += __shfl_xor_sync(0xffffffffu, acc0.x, o);
+          acc0.y += __shfl_xor_sync(0xffffffffu, acc0.y, o);
+          acc1.x += __shfl_xor_sync(0xffffffffu, acc1.x, o);
+          acc1.y += __shfl_xor_sync(0xffffffffu, acc1.y, o);
+        }
+        if (a0) {
+          const cx<T> pi = cmul(tau, acc0);
+          if (lane < CL) peer(lane)->p[sl][i0] = pi;
+          const cx<T> vi = sh.v[sl][i0];
           dr += vi.x * pi.x + vi.y * pi.y;  // Re conj(v_i) p_i
           di += vi.x * pi.y - vi.y * pi.x;  // Im conj(v_i) p_i
         }
+        if (a1) {
+          const cx<T> pi = cmul(tau, acc1);
+          if (lane < CL) peer(lane)->p[sl][i1] = pi;
+          const cx<T> vi = sh.v[sl][i1];
+          dr += vi.x * pi.x + vi.y * pi.y;
+          di += vi.x * pi.y - vi.y * pi.x;
+        }
       }
+      if (lane < CL) peer(lane)->dpart[sl][rank * CL_NW + warp] = mk<T>(dr, di);
     }
-    if (lane == 0) { sh.red[warp] = dr; sh.lam[warp] = di; }
-    __syncthreads();
-    if (tid == 0) {
-      T sr = 0, si = 0;
-      for (int w = 0; w < nw; ++w) { sr += sh.red[w]; si += sh.lam[w]; }
-      for (int q = 0; q < CL; ++q) {
-        peer[q]->dotp[buf][rank][0] = sr;
-        peer[q]->dotp[buf][rank][1] = si;
-      }
-    }
+    LRET_SUBSTEP(0)
     cluster.sync();
+    LRET_SUBSTEP(1)
+    T cc = 0;
     if (!skip) {
-      T sr = 0, si = 0;
+      cx<T> sp4 = mk<T>(0, 0);
+      for (int q = lane; q < CL * CL_NW; q += 32) sp4 = cadd(sp4, sh.dpart[sl][q]);
+      const T sr = warp_sum(sp4.x), si = warp_sum(sp4.y);
+      cc = (T)0.5 * (tau.x * sr + tau.y * si);
+      // rank-2 update of this warp's rows: A[i][c] -= v_i conj(w_c) + w_i conj(v_c)
+      const cx<T> v0 = a0 ? sh.v[sl][i0] : mk<T>(0, 0), v1 = a1 ? sh.v[sl][i1] : mk<T>(0, 0);
+      const cx<T> w0 = a0 ? csub(sh.p[sl][i0], cscale(v0, cc)) : mk<T>(0, 0);
+      const cx<T> w1 = a1 ? csub(sh.p[sl][i1], cscale(v1, cc)) : mk<T>(0, 0);
 #pragma unroll
-      for (int q = 0; q < CL; ++q) { sr += sh.dotp[buf][q][0]; si += sh.dotp[buf][q][1]; }
-      const T cc = (T)0.5 * (tau.x * sr + tau.y * si);
-      // w = p - c v (full vector, every CTA); kept in p[buf]
-      for (int t = tid; t < n1; t += CL_THREADS) {
-        const int col = j + 1 + t;
-        sh.p[buf][col] = csub(sh.p[buf][col], cscale(sh.v[buf][col], cc));
-      }
-      __syncthreads();
-      // rank-2 update of local rows i > j (full rows, columns > j)
-      for (int li = warp; li < nrows; li += nw) {
-        const int i = li * CL + rank;
-        if (i <= j) continue;
-        const cx<T> vi = sh.v[buf][i], wi = sh.p[buf][i];
-        for (int col = j + 1 + lane; col < m; col += 32) {
-          cx<T> a = sh.A[li][col];
-          a = csub(a, cadd(cmul(vi, conjg(sh.p[buf][col])), cmul(wi, conjg(sh.v[buf][col]))));
-          if (col == i) a.y = 0;
-          sh.A[li][col] = a;
+      for (int e = 0; e < E; ++e) {
+        const int c = lane + 32 * e;
+        if (c > j && c < m) {
+          const cx<T> vc = sh.v[sl][c];
+          const cx<T> wc = csub(sh.p[sl][c], cscale(vc, cc));
+          if (a0) {
+            A0[e] = csub(A0[e], cadd(cmul(v0, conjg(wc)), cmul(w0, conjg(vc))));
+            if (c == i0) A0[e].y = 0;
+          }
+          if (a1) {
+            A1[e] = csub(A1[e], cadd(cmul(v1, conjg(wc)), cmul(w1, conjg(vc))));
+            if (c == i1) A1[e].y = 0;
+          }
         }
       }
     }
-    __syncthreads();
-  }
-  if (rank == (m - 1) % CL && tid == 0) {
-    const T dl = sh.A[(m - 1) / CL][m - 1].x;
-    for (int q = 0; q < CL; ++q) {
-      peer[q]->d[m - 1] = dl;
-      peer[q]->e[m - 1] = 0;
+    if (tid == 0) sh.ccs[sl] = cc;
+    // row j + 3 (as updated through this step) for the reflector group two steps ahead
+    if (j + 3 < m && rank == (j + 3) % CL) {
+      const int lst = (j + 3) / CL;
+      if (lst == li0) store_row(A0, (j + 3) % 3, j + 1);
+      else if (lst == li1) store_row(A1, (j + 3) % 3, j + 1);
     }
-  }
-  cluster.sync();
-
-  // ---- split, bisection (eigenvalues t = rank, rank + CL, ...) ---------------
-  __shared__ T s_tnorm, s_pivmin;
-  if (tid == 0) {
-    T tn = 0, emax2 = 0;
-    for (int i = 0; i < m; ++i) {
-      const T a = fabs(sh.d[i]) + (i > 0 ? fabs(sh.e[i - 1]) : (T)0) + (i < m - 1 ? fabs(sh.e[i]) : (T)0);
-      tn = a > tn ? a : tn;
-    }
-    for (int i = 0; i < m - 1; ++i) {
-      if (fabs(sh.e[i]) <= CEps<T>::v * (fabs(sh.d[i]) + fabs(sh.d[i + 1])) ||
-          fabs(sh.e[i]) <= CEps<T>::v * CEps<T>::v * tn)
-        sh.e[i] = 0;
-      sh.e2[i] = sh.e[i] * sh.e[i];
-      emax2 = sh.e2[i] > emax2 ? sh.e2[i] : emax2;
-    }
-    int lo = 0;
-    for (int i = 0; i < m; ++i)
-      if (i == m - 1 || sh.e[i] == (T)0) {
-        for (int t = lo; t <= i; ++t) { sh.sblo[t] = (short)lo; sh.sbhi[t] = (short)i; }
-        lo = i + 1;
+    LRET_SUBSTEP(2)
+    if (tid < RG) {
+      const bool up0 = j >= 1 && !(sh.tau[slp].x == (T)0 && sh.tau[slp].y == (T)0);
+      asm volatile("cp.async.wait_group 0;" ::: "memory");  // row nx, copied during step j - 1
+      bar_group();                                          // (also publishes ccs[sl])
+      const cx<T>* row = sh.nrow[nx & 1];
+      if (nx < m - 1) {
+        group_reflector<T>(sh, row, nx, m, sln, slp, up0, sl, !skip, rank == nx % CL, gref, tid);
+      } else if (tid == 0) {  // last diagonal entry
+        cx<T> a = row[nx];
+        if (up0) a = upd1(sh, slp, sh.ccs[slp], nx, nx, a);
+        if (!skip) a = upd1(sh, sl, cc, nx, nx, a);
+        sh.d[m - 1] = a.x;
+        sh.e[m - 1] = 0;
       }
-    s_tnorm = tn > (T)0 ? tn : (T)1;
-    s_pivmin = CEps<T>::tiny * (emax2 > (T)1 ? emax2 : (T)1);
+      // row j + 2 (stored during step j - 1) for the next step
+      if (nx + 1 < m) prefetch_row<T>(sh.nrow[(nx + 1) & 1], grow + (size_t)((nx + 1) % 3) * CL_MAXM, nx + 1, m, tid);
+      LRET_SUBSTEP(3)
+    }
+    __syncthreads();
+    LRET_SUBSTEP(4)
+  }
+#undef LRET_SUBSTEP
+  cluster.sync();
+  if (tid == 0) { const long long t1 = phase_clock(); t_ph[1] = t1 - t0; t0 = t1; }
+
+  // ---- split, multisection (eigenvalues t = rank + CL * group) ----------------
+  __shared__ T s_red[CL_NW];
+  __shared__ T s_tnorm, s_pivmin;
+  {
+    // ||T||_inf, then negligible off-diagonals set to zero, then unreduced blocks
+    T tn = 0;
+    for (int i = tid; i < m; i += CL_THREADS)
+      tn = fmax(tn, fabs(sh.d[i]) + (i > 0 ? fabs(sh.e[i - 1]) : (T)0) + (i < m - 1 ? fabs(sh.e[i]) : (T)0));
+    for (int o = 16; o > 0; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    if (lane == 0) s_red[warp] = tn;
+    __syncthreads();
+    if (tid == 0) {
+      T v = 0;
+      for (int w = 0; w < CL_NW; ++w) v = fmax(v, s_red[w]);
+      s_tnorm = v;
+    }
+    __syncthreads();
+    tn = s_tnorm;
+    T emax2 = 0;
+    for (int i = tid; i < m - 1; i += CL_THREADS) {
+      T ei = sh.e[i];
+      if (fabs(ei) <= CEps<T>::v * (fabs(sh.d[i]) + fabs(sh.d[i + 1])) || fabs(ei) <= CEps<T>::v * CEps<T>::v * tn)
+        ei = 0;
+      sh.e[i] = ei;
+      sh.e2[i] = ei * ei;
+      emax2 = fmax(emax2, ei * ei);
+    }
+    for (int o = 16; o > 0; o >>= 1) emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
+    __syncthreads();
+    if (lane == 0) s_red[warp] = emax2;
+    __syncthreads();
+    if (warp == 0) {
+      // block boundaries: sblo = last start <= i (prefix max), sbhi = first end >= i (suffix min);
+      // lane l holds i = 8 l .. 8 l + 7
+      int run = -1, lov[8], hiv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int i = lane * 8 + q;
+        if (i < m && (i == 0 || sh.e[i - 1] == (T)0)) run = i;
+        lov[q] = run;
+      }
+      int carry = run;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, carry, o);
+        if (lane >= o) carry = max(carry, t);
+      }
+      int prev = __shfl_up_sync(0xffffffffu, carry, 1);
+      if (lane == 0) prev = -1;
+      constexpr int BIG = 1 << 20;
+      run = BIG;
+#pragma unroll
+      for (int q = 7; q >= 0; --q) {
+        const int i = lane * 8 + q;
+        if (i < m && (i == m - 1 || sh.e[i] == (T)0)) run = i;
+        hiv[q] = run;
+      }
+      carry = run;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_down_sync(0xffffffffu, carry, o);
+        if (lane + o < 32) carry = min(carry, t);
+      }
+      int next = __shfl_down_sync(0xffffffffu, carry, 1);
+      if (lane == 31) next = BIG;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int i = lane * 8 + q;
+        if (i < m) {
+          sh.sblo[i] = (short)max(lov[q], prev);
+          sh.sbhi[i] = (short)min(hiv[q], next);
+        }
+      }
+      if (lane == 0) {
+        T v = 0;
+        for (int w = 0; w < CL_NW; ++w) v = fmax(v, s_red[w]);
+        s_tnorm = tn > (T)0 ? tn : (T)1;
+        s_pivmin = CEps<T>::tiny * (v > (T)1 ? v : (T)1);
+      }
+    }
   }
   __syncthreads();
   const T tnorm = s_tnorm, pivmin = s_pivmin;
-  for (int t = rank + CL * tid; t < m; t += CL * CL_THREADS) {
-    const int lo = sh.sblo[t], hi = sh.sbhi[t], li = t - lo;
-    T gl = sh.d[lo], gu = sh.d[lo];
-    for (int i = lo; i <= hi; ++i) {
-      const T rad = (i > lo ? fabs(sh.e[i - 1]) : (T)0) + (i < hi ? fabs(sh.e[i]) : (T)0);
-      gl = fmin(gl, sh.d[i] - rad);
-      gu = fmax(gu, sh.d[i] + rad);
+  {
+    const int grp = tid / MS, sub = tid % MS;
+    const unsigned hmask = 0xffffu << (lane & 16);
+    for (int t = rank + CL * grp; t < m; t += CL * (CL_THREADS / MS)) {
+      const int lo = sh.sblo[t], hi = sh.sbhi[t], li = t - lo;
+      T gl = sh.d[lo], gu = sh.d[lo];
+      for (int i = lo + sub; i <= hi; i += MS) {
+        const T rad = (i > lo ? fabs(sh.e[i - 1]) : (T)0) + (i < hi ? fabs(sh.e[i]) : (T)0);
+        gl = fmin(gl, sh.d[i] - rad);
+        gu = fmax(gu, sh.d[i] + rad);
+      }
+      for (int o = MS / 2; o > 0; o >>= 1) {
+        gl = fmin(gl, __shfl_xor_sync(hmask, gl, o));
+        gu = fmax(gu, __shfl_xor_sync(hmask, gu, o));
+      }
+      T a = gl - CEps<T>::v * tnorm * 2 - pivmin, b = gu + CEps<T>::v * tnorm * 2 + pivmin;
+      for (int it = 0; it < 48; ++it) {
+        if (b - a <= (T)2 * CEps<T>::v * fmax(fabs(a), fabs(b)) + CEps<T>::v * tnorm * (T)1e-3) break;
+        const T h = (b - a) / (T)(MS + 1);
+        const T x = a + h * (T)(sub + 1);
+        const bool below = sturm_count<T>(sh.d, sh.e2, lo, hi, x, pivmin) <= li;  // lambda_li >= x
+        const unsigned bal = (__ballot_sync(hmask, below) >> (lane & 16)) & 0xffffu;
+        const int nt = bal == 0xffffu ? MS : __ffs(~bal) - 1;  // first point with lambda_li < x
+        const T na = nt > 0 ? a + h * (T)nt : a;
+        const T nb = nt < MS ? a + h * (T)(nt + 1) : b;
+        if (na == a && nb == b) break;  // no progress at this precision
+        a = na;
+        b = nb > na ? nb : na;
+      }
+      T lt = (T)0.5 * (a + b);
+      if (!(lt == lt)) lt = -INFINITY;
+      if (sub < CL) peer(sub)->lam[t] = lt;
     }
-    T a = gl - CEps<T>::v * tnorm * 2 - pivmin, b = gu + CEps<T>::v * tnorm * 2 + pivmin;
-    for (int it = 0; it < 100; ++it) {
-      const T mid = (T)0.5 * (a + b);
-      if (b - a <= (T)2 * CEps<T>::v * fmax(fabs(a), fabs(b)) + CEps<T>::v * tnorm * (T)1e-3 || mid == a || mid == b)
-        break;
-      if (sturm_count<T>(sh.d, sh.e2, lo, hi, mid, pivmin) <= li) a = mid; else b = mid;
-    }
-    T lt = (T)0.5 * (a + b);
-    if (!(lt == lt)) lt = -INFINITY;
-    for (int q = 0; q < CL; ++q) peer[q]->lam[t] = lt;
   }
   cluster.sync();
 
-  // ---- sort (every CTA), rank choice and accounting (CTA 0) -------------------
-  for (int t = tid; t < m; t += CL_THREADS) {
-    const T lt = sh.lam[t];
-    int rk = 0;
-    for (int u = 0; u < m; ++u) {
-      const T lu = sh.lam[u];
-      rk += (lu > lt) || (lu == lt && u < t);
-    }
-    sh.order[rk] = (short)t;
-    if (rank == 0) evals[rk] = (double)lt * gscale;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int k;
-    double total = 0.0;
-    for (int i = 0; i < m; ++i) {
-      const double v = (double)sh.lam[sh.order[i]] * gscale;
-      total += v > 0 ? v : 0.0;
-    }
-    if (r > 0) {
-      k = r < m ? r : m;
-    } else {
-      double cs = 0.0;
-      k = m;
-      for (int i = 0; i < m; ++i) {
-        const double v = (double)sh.lam[sh.order[i]] * gscale;
-        cs += v > 0 ? v : 0.0;
-        if (cs >= (1.0 - eps) * total) { k = i + 1; break; }
+  // ---- sort (every CTA), rank choice and accounting ---------------------------
+  {
+    const int t = tid;  // m <= CL_THREADS: one eigenvalue per thread
+    T lt = 0;
+    int rk = CL_MAXM;
+    if (t < m) {
+      lt = sh.lam[t];
+      rk = 0;
+      for (int u = 0; u < m; ++u) {
+        const T lu = sh.lam[u];
+        rk += (lu > lt) || (lu == lt && u < t);
       }
+      sh.order[rk] = (short)t;
+      if (rank == 0) evals[rk] = (double)lt * gscale;
     }
-    sh.k = k;
-    if (rank == 0) {
-      double kept = 0.0, dropped = 0.0;
-      for (int i = 0; i < m; ++i) {
-        const double v = (double)sh.lam[sh.order[i]] * gscale;
-        if (i < k) kept += v > 0 ? v : 0.0; else dropped += v > 0 ? v : 0.0;
+    const double vpos = (t < m && lt > (T)0) ? (double)lt * gscale : 0.0;
+    const double total = block_sum(vpos, sh.dred);  // valid in thread 0; the call synchronises
+    __shared__ double s_total;
+    if (tid == 0) s_total = total;
+    __syncthreads();
+    if (tid == 0) {
+      int k;
+      if (r > 0) {
+        k = r < m ? r : m;
+      } else {
+        double cs = 0.0;
+        k = m;
+        for (int i = 0; i < m; ++i) {
+          const double v = (double)sh.lam[sh.order[i]] * gscale;
+          cs += v > 0 ? v : 0.0;
+          if (cs >= (1.0 - eps) * s_total) { k = i + 1; break; }
+        }
       }
+      sh.k = k;
+    }
+    __syncthreads();
+    const int k = sh.k;
+    const double kept = block_sum(rk < k ? vpos : 0.0, sh.dred);
+    const double dropped = block_sum(rk < k ? 0.0 : vpos, sh.dred);
+    if (rank == 0 && tid == 0) {
       const double l1v = (double)sh.lam[sh.order[0]] * gscale;
       const double l1 = fabs(l1v) > 0 ? fabs(l1v) : 1.0;
       out->k = k;
@@ -354,6 +611,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
   }
   __syncthreads();
   const int nvec = all_vecs ? m : sh.k;
+  if (tid == 0) { const long long t1 = phase_clock(); t_ph[2] = t1 - t0; t0 = t1; }
 
   // ---- inverse iteration: vectors i = rank + CL * (warp + nw * ...) ---------
   {
@@ -363,12 +621,12 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     const int nlu = (int)(sizeof(sh.A) / (SLOT * sizeof(T)));
     if (warp < nlu) {
       T* dl = ws + (size_t)warp * SLOT;
-      T* dd = dl + CL_MAXM;
+      T* dd = dl + CL_MAXM;  // reciprocals of the LU diagonal
       T* du = dd + CL_MAXM;
       T* du2 = du + CL_MAXM;
       T* x = du2 + CL_MAXM;
       unsigned char* piv = reinterpret_cast<unsigned char*>(x + CL_MAXM);
-      const int wn = nlu < nw ? nlu : nw;
+      const int wn = nlu < CL_NW ? nlu : CL_NW;
       for (int i = rank + CL * warp; i < nvec; i += CL * wn) {
         const int pos = sh.order[i];
         const int lo = sh.sblo[pos], hi = sh.sbhi[pos], s = hi - lo + 1;
@@ -382,30 +640,30 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
         }
         const T lam = sh.lam[pos];
         if (lane == 0) {
+          // LU with partial pivoting of T - lam I on rows lo..hi; the running
+          // diagonal and superdiagonal stay in registers (the recurrence is serial)
           const T tiny = CEps<T>::v * tnorm;
-          for (int t = 0; t < s; ++t) {
-            dd[t] = sh.d[lo + t] - lam;
-            if (t < s - 1) { dl[t] = sh.e[lo + t]; du[t] = sh.e[lo + t]; du2[t] = 0; }
-          }
+          T cd = sh.d[lo] - lam, cu = sh.e[lo];
+#pragma unroll 4
           for (int t = 0; t < s - 1; ++t) {
-            if (fabs(dd[t]) >= fabs(dl[t])) {
-              if (dd[t] == (T)0) dd[t] = tiny;
-              const T l = dl[t] / dd[t];
-              dl[t] = l;
-              dd[t + 1] -= l * du[t];
-              piv[t] = 0;
+            const T sub = sh.e[lo + t];
+            const T nd = sh.d[lo + t + 1] - lam;
+            const T nu = t < s - 2 ? sh.e[lo + t + 1] : (T)0;
+            if (fabs(cd) >= fabs(sub)) {
+              if (cd == (T)0) cd = tiny;
+              const T l = sub / cd;
+              dl[t] = l; dd[t] = (T)1 / cd; du[t] = cu; du2[t] = 0; piv[t] = 0;
+              cd = nd - l * cu;
+              cu = nu;
             } else {
-              const T l = dd[t] / dl[t];
-              dd[t] = dl[t];
-              dl[t] = l;
-              const T tmp = du[t];
-              du[t] = dd[t + 1];
-              dd[t + 1] = tmp - l * dd[t + 1];
-              if (t < s - 2) { du2[t] = du[t + 1]; du[t + 1] = -l * du[t + 1]; }
-              piv[t] = 1;
+              const T l = cd / sub;
+              dl[t] = l; dd[t] = (T)1 / sub; du[t] = nd; du2[t] = nu; piv[t] = 1;
+              cd = cu - l * nd;
+              cu = -l * nu;
             }
           }
-          if (dd[s - 1] == (T)0) dd[s - 1] = tiny;
+          if (cd == (T)0) cd = tiny;
+          dd[s - 1] = (T)1 / cd;
         }
         for (int t = lane; t < s; t += 32) {
           unsigned h = (unsigned)(t + 1) * 2654435761u ^ ((unsigned)(i + 7) * 40503u + 0x9e3779b9u);
@@ -416,18 +674,29 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
         __syncwarp();
         for (int it = 0; it < 2; ++it) {
           if (lane == 0) {
+            // forward (L with row swaps), then backward (U); carried values in registers
+            T xt = x[0];
+#pragma unroll 4
             for (int t = 0; t < s - 1; ++t) {
+              const T xn = x[t + 1], l = dl[t];
               if (piv[t] == 0) {
-                x[t + 1] -= dl[t] * x[t];
+                x[t] = xt;
+                xt = xn - l * xt;
               } else {
-                const T tmp = x[t];
-                x[t] = x[t + 1];
-                x[t + 1] = tmp - dl[t] * x[t + 1];
+                x[t] = xn;
+                xt = xt - l * xn;
               }
             }
-            x[s - 1] /= dd[s - 1];
-            x[s - 2] = (x[s - 2] - du[s - 2] * x[s - 1]) / dd[s - 2];
-            for (int t = s - 3; t >= 0; --t) x[t] = (x[t] - du[t] * x[t + 1] - du2[t] * x[t + 2]) / dd[t];
+            T x1 = xt * dd[s - 1];  // x[t + 1]
+            x[s - 1] = x1;
+            T x2 = 0;               // x[t + 2]
+#pragma unroll 4
+            for (int t = s - 2; t >= 0; --t) {
+              const T xv = (x[t] - du[t] * x1 - du2[t] * x2) * dd[t];
+              x[t] = xv;
+              x2 = x1;
+              x1 = xv;
+            }
           }
           __syncwarp();
           T xmax = 0;
@@ -451,75 +720,250 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
   }
   __threadfence();
   cluster.sync();
+  if (tid == 0) { const long long t1 = phase_clock(); t_ph[3] = t1 - t0; t0 = t1; }
 
   // ---- modified Gram-Schmidt of the needed vectors (CTA 0) --------------------
   if (rank == 0) {
-    __shared__ T s_inv;
-    for (int i = 0; i < nvec; ++i) {
-      T* zi = gZ + (size_t)i * m;
-      T part = 0;
-      for (int t = tid; t < m; t += CL_THREADS) part += zi[t] * zi[t];
-      part = warp_sum(part);
-      if (lane == 0) sh.red[warp] = part;
+    constexpr int E = CL_MAXM / 32;
+    constexpr int NSL = MgsSlots<T>::v;
+    if (nvec <= CL_NW * NSL) {
+      // vector i lives in registers of warp i % 16 (slot i / 16), rows lane + 32 e;
+      // at step i the finished z_i is published in shared memory and every warp
+      // removes it from its later vectors; the warp holding z_{i+1} normalises it
+      T z[NSL][E];
+#pragma unroll
+      for (int sl = 0; sl < NSL; ++sl) {
+        const int vec = warp + CL_NW * sl;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int row = lane + 32 * e;
+          z[sl][e] = (vec < nvec && row < m) ? gZ[(size_t)vec * m + row] : (T)0;
+        }
+      }
+      auto publish = [&](int sl_pub, int vec_pub) {
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl) {
+          if (sl != sl_pub) continue;
+          T nrm = 0;
+#pragma unroll
+          for (int e = 0; e < E; ++e) nrm += z[sl][e] * z[sl][e];
+          nrm = warp_sum(nrm);
+          const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)0;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            z[sl][e] *= inv;
+            const int row = lane + 32 * e;
+            if (row < m) sh.zb[vec_pub & 1][row] = z[sl][e];
+          }
+        }
+      };
+      if (warp == 0 && nvec > 0) publish(0, 0);
       __syncthreads();
-      if (tid == 0) {
+      for (int i = 0; i + 1 < nvec; ++i) {
+        T qv[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int row = lane + 32 * e;
+          qv[e] = row < m ? sh.zb[i & 1][row] : (T)0;
+        }
+        T dot[NSL];
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl) {
+          dot[sl] = 0;
+#pragma unroll
+          for (int e = 0; e < E; ++e) dot[sl] += qv[e] * z[sl][e];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int sl = 0; sl < NSL; ++sl) dot[sl] += __shfl_xor_sync(0xffffffffu, dot[sl], o);
+        }
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl) {
+          const int vec = warp + CL_NW * sl;
+          if (vec > i && vec < nvec) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) z[sl][e] -= dot[sl] * qv[e];
+          }
+        }
+        if (warp == (i + 1) % CL_NW) publish((i + 1) / CL_NW, i + 1);
+        __syncthreads();
+      }
+#pragma unroll
+      for (int sl = 0; sl < NSL; ++sl) {
+        const int vec = warp + CL_NW * sl;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int row = lane + 32 * e;
+          if (vec < nvec && row < m) gZ[(size_t)vec * m + row] = z[sl][e];
+        }
+      }
+    } else {
+      // many vectors (all of them, for the adjoint): in global memory, one warp per later vector
+      T* Z = gZ;
+      if (warp == 0) {
         T nrm = 0;
-        for (int w = 0; w < nw; ++w) nrm += sh.red[w];
-        s_inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)0;
+        for (int t = lane; t < m; t += 32) nrm += Z[t] * Z[t];
+        nrm = warp_sum(nrm);
+        const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)0;
+        for (int t = lane; t < m; t += 32) Z[t] *= inv;
       }
       __syncthreads();
-      const T inv = s_inv;
-      for (int t = tid; t < m; t += CL_THREADS) zi[t] *= inv;
-      __syncthreads();
-      for (int jv = i + 1 + warp; jv < nvec; jv += nw) {
-        T* zj = gZ + (size_t)jv * m;
-        T dot = 0;
-        for (int t = lane; t < m; t += 32) dot += zi[t] * zj[t];
-        dot = warp_sum(dot);
-        for (int t = lane; t < m; t += 32) zj[t] -= dot * zi[t];
+      for (int i = 0; i + 1 < nvec; ++i) {
+        const T* zi = Z + (size_t)i * m;
+        for (int jv = i + 1 + warp; jv < nvec; jv += CL_NW) {
+          T* zj = Z + (size_t)jv * m;
+          T dot = 0;
+          for (int t = lane; t < m; t += 32) dot += zi[t] * zj[t];
+          dot = warp_sum(dot);
+          T nrm = 0;
+          for (int t = lane; t < m; t += 32) {
+            const T u = zj[t] - dot * zi[t];
+            zj[t] = u;
+            nrm += u * u;
+          }
+          if (jv == i + 1) {  // final: normalise before it is used
+            nrm = warp_sum(nrm);
+            const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)0;
+            for (int t = lane; t < m; t += 32) zj[t] *= inv;
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
     __threadfence();
   }
   cluster.sync();
+  if (tid == 0) { const long long t1 = phase_clock(); t_ph[4] = t1 - t0; t0 = t1; }
 
-  // ---- back-transform y = H_0 (... (H_{m-2} z)); columns i = rank + CL * w ------
+  // ---- back-transform y = H_0 (... (H_{m-2} z)); column rank + CL * warp -----
   {
     const cx<T>* taus = reinterpret_cast<const cx<T>*>(gref + (size_t)(CL_MAXM - 1) * CL_MAXM);
-    cx<T>* y = reinterpret_cast<cx<T>*>(&sh.A[0][0]) + (size_t)warp * CL_MAXM;  // per-warp column
-    for (int col = rank + CL * warp; col < nvec; col += CL * nw) {
-      const T* zc = gZ + (size_t)col * m;
-      for (int t = lane; t < m; t += 32) y[t] = mk<T>(zc[t], 0);
-      __syncwarp();
-      for (int jj = m - 2; jj >= 0; --jj) {
-        const cx<T> tau = taus[jj];
-        if (tau.x == (T)0 && tau.y == (T)0) continue;
-        const cx<T>* v = gref + (size_t)jj * CL_MAXM;  // v[t] for row jj + 1 + t
-        T sr = 0, si = 0;
-        for (int t = lane; t < m - jj - 1; t += 32) {
-          const cx<T> a = v[t], b = y[jj + 1 + t];
-          sr += a.x * b.x + a.y * b.y;
-          si += a.x * b.y - a.y * b.x;
-        }
-        sr = warp_sum(sr);
-        si = warp_sum(si);
-        const cx<T> f = cmul(tau, mk<T>(sr, si));
-        for (int t = lane; t < m - jj - 1; t += 32) y[jj + 1 + t] = csub(y[jj + 1 + t], cmul(f, v[t]));
-        __syncwarp();
-      }
-      double nrm = 0.0;
-      for (int t = lane; t < m; t += 32) nrm += (double)y[t].x * y[t].x + (double)y[t].y * y[t].y;
-      for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-      const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 1.0;
-      for (int t = lane; t < m; t += 32) {
-        const double2 vv = to_d2(y[t]);
-        evecs[(size_t)t * m + col] = make_double2(vv.x * inv, vv.y * inv);
-      }
-      __syncwarp();
+    cx<T>* stage = reinterpret_cast<cx<T>*>(&sh.A[0][0]);  // BT_STAGE full-length reflectors
+    static_assert(BT_STAGE * CL_MAXM <= CL_ROWS * CL_MAXM, "staging buffer");
+    constexpr int E = CL_MAXM / 32;
+    constexpr int BT_GROUP = BtGroup<T>::v;
+    const int nref = m - 1;
+    const int npass = (nvec + CL * CL_NW - 1) / (CL * CL_NW);
+    if (tid == 0) {
+      tc::mbar_init(tc::smem_u32(&sh.mbar), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    __syncthreads();
+    bool bt_ok = true;
+    int bt_phase = 0;
+    for (int pass = 0; pass < npass; ++pass) {
+      const int col = rank + CL * (warp + CL_NW * pass);
+      const bool has = col < nvec;
+      cx<T> y[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int row = lane + 32 * e;
+        y[e] = mk<T>(has && row < m ? gZ[(size_t)col * m + row] : (T)0, 0);
+      }
+      // reflector blocks from the last one down: [b0, b0 + nb)
+      for (int top = nref; top > 0; top -= BT_STAGE) {
+        const int b0 = top - BT_STAGE > 0 ? top - BT_STAGE : 0;
+        const int nb = top - b0;
+        __syncthreads();  // the previous block is no longer read
+        if (tid == 0 && bt_ok) {
+          // rows b0 .. b0 + nb - 1 of the reflector store are full-length rows (zero
+          // outside each reflector's support): one bulk copy
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          tc::bulk_load(tc::smem_u32(stage), gref + (size_t)b0 * CL_MAXM,
+                        (uint32_t)(nb * CL_MAXM * sizeof(cx<T>)), tc::smem_u32(&sh.mbar));
+        }
+        if (tid < BT_STAGE) sh.btau[tid] = tid < nb ? taus[b0 + tid] : mk<T>(0, 0);
+        if (bt_ok) bt_ok = tc::mbar_wait(tc::smem_u32(&sh.mbar), (uint32_t)(bt_phase & 1));
+        ++bt_phase;
+        bt_ok = __syncthreads_and(bt_ok) != 0;
+        if (!bt_ok) continue;
+        if (nb < BT_STAGE) {  // rows past the last reflector: zero, not stale
+          for (int e = nb * CL_MAXM + tid; e < BT_STAGE * CL_MAXM; e += CL_THREADS) stage[e] = mk<T>(0, 0);
+          __syncthreads();
+        }
+        // inner products of the reflectors within each group of BT_GROUP
+        for (int pr = warp; pr < (BT_STAGE / BT_GROUP) * BT_GROUP * BT_GROUP; pr += CL_NW) {
+          const int g = pr / (BT_GROUP * BT_GROUP), kk = (pr / BT_GROUP) % BT_GROUP, ll = pr % BT_GROUP;
+          if (ll <= kk) continue;
+          const cx<T>* vk = stage + (size_t)(g * BT_GROUP + kk) * CL_MAXM;
+          const cx<T>* vl = stage + (size_t)(g * BT_GROUP + ll) * CL_MAXM;
+          cx<T> acc = mk<T>(0, 0);
+          for (int t = lane; t < m; t += 32) cfmac(acc, vk[t], vl[t]);
+          acc.x = warp_sum(acc.x);
+          acc.y = warp_sum(acc.y);
+          if (lane == 0) sh.gram[g][kk][ll] = acc;
+        }
+        __syncthreads();
+        if (has) {
+          for (int g = BT_STAGE / BT_GROUP - 1; g >= 0; --g) {
+            // s_k = v_k^dag y for the group's reflectors, reduced together
+            T sre[BT_GROUP], sim[BT_GROUP];
+#pragma unroll
+            for (int kk = 0; kk < BT_GROUP; ++kk) {
+              const cx<T>* vk = stage + (size_t)(g * BT_GROUP + kk) * CL_MAXM;
+              cx<T> acc = mk<T>(0, 0);
+#pragma unroll
+              for (int e = 0; e < E; ++e) cfmac(acc, vk[lane + 32 * e], y[e]);
+              sre[kk] = acc.x;
+              sim[kk] = acc.y;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+              for (int kk = 0; kk < BT_GROUP; ++kk) {
+                sre[kk] += __shfl_xor_sync(0xffffffffu, sre[kk], o);
+                sim[kk] += __shfl_xor_sync(0xffffffffu, sim[kk], o);
+              }
+            }
+            // f_k = tau_k (s_k - sum_{l > k} (v_k^dag v_l) f_l), k descending
+            cx<T> f[BT_GROUP];
+#pragma unroll
+            for (int kk = BT_GROUP - 1; kk >= 0; --kk) {
+              cx<T> sk = mk<T>(sre[kk], sim[kk]);
+#pragma unroll
+              for (int ll = kk + 1; ll < BT_GROUP; ++ll) sk = csub(sk, cmul(sh.gram[g][kk][ll], f[ll]));
+              f[kk] = cmul(sh.btau[g * BT_GROUP + kk], sk);
+            }
+#pragma unroll
+            for (int kk = 0; kk < BT_GROUP; ++kk) {
+              const cx<T>* vk = stage + (size_t)(g * BT_GROUP + kk) * CL_MAXM;
+#pragma unroll
+              for (int e = 0; e < E; ++e) y[e] = csub(y[e], cmul(f[kk], vk[lane + 32 * e]));
+            }
+          }
+        }
+      }
+      if (has && bt_ok) {
+        double nrm = 0.0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) nrm += (double)y[e].x * y[e].x + (double)y[e].y * y[e].y;
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 1.0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int row = lane + 32 * e;
+          if (row < m) {
+            const double2 vv = to_d2(y[e]);
+            evecs[(size_t)row * m + col] = make_double2(vv.x * inv, vv.y * inv);
+          }
+        }
+      }
+    }
+    if (!bt_ok && tid == 0) out->status = 3;  // a bounded wait gave up
   }
   cluster.sync();
+  if (rank == 0 && tid == 0) {
+    t_ph[5] = phase_clock() - t0;
+    for (int q = 0; q < 6; ++q) out->cycles[q] = t_ph[q];
+#ifdef LRET_EIG_PROFILE
+    for (int q = 0; q < 6; ++q) out->cycles[q] = sp[q];
+    out->cycles[2] = sh.gdbg[0];  // x and its updates
+    out->cycles[3] = sh.gdbg[1];  // first group barrier
+    out->cycles[4] = sh.gdbg[2];  // norms and scalars
+    out->cycles[5] = sh.gdbg[3];  // v, store
+#endif
+  }
 }
 
 template <typename T>
@@ -553,12 +997,15 @@ cudaError_t launch_eigh_cluster(const double2* G, int m, void* work, double* eva
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_eigh_cluster<T>, G, m, gref, gZ, evals, evecs, out, r, eps, all_vecs);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_eigh_cluster<T>, G, m, gref, gZ, evals, evecs, out, r, eps, all_vecs);
+  note_launches(1);
+  return e;
 }
 
 size_t eigh_cluster_work_bytes(bool fp64) {
   const size_t e = fp64 ? sizeof(double) : sizeof(float);
-  return (size_t)CL_MAXM * CL_MAXM * 2 * e + (size_t)CL_MAXM * CL_MAXM * e;
+  // reflectors (complex, last row tau), Z (real), three row buffers (complex)
+  return (size_t)CL_MAXM * CL_MAXM * 2 * e + (size_t)CL_MAXM * CL_MAXM * e + (size_t)3 * CL_MAXM * 2 * e;
 }
 
 template cudaError_t launch_eigh_cluster<float>(const double2*, int, void*, double*, double2*, EigOut*, int, double,

@@ -610,6 +610,7 @@ template <typename T>
 cudaError_t launch_eigh_tri_batch(const TruncTask* tasks, int ntasks, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
   k_eigh_tri_batch<T><<<ntasks, TRI_THREADS, TRI_DYN_MAX, s>>>(tasks);
+  note_launches(1);
   return cudaGetLastError();
 }
 template cudaError_t prepare_eigh_tri_batch<float>();
@@ -649,6 +650,7 @@ cudaError_t launch_eigh_tri(const double2* G, int m, void* work, double* evals, 
   cx<T>* gpacked = (cx<T>*)work;
   T* gZ = (T*)(gpacked + packed_off(m, m));
   k_eigh_tri<T><<<1, TRI_THREADS, dyn, s>>>(G, m, c_split, gpacked, gZ, evals, evecs, out, r, eps, all_vecs);
+  note_launches(1);
   return cudaGetLastError();
 }
 

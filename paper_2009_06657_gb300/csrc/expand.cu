@@ -123,6 +123,7 @@ cudaError_t launch_expand_batch(const ExpandTask* tasks, const int* bstart, int 
                                 cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
   k_expand_batch<T><<<nblocks, 256, 0, s>>>(tasks, bstart, ntasks);
+  note_launches(1);
   return cudaGetLastError();
 }
 template cudaError_t launch_expand_batch<float>(const ExpandTask*, const int*, int, int, cudaStream_t);
@@ -146,6 +147,7 @@ cudaError_t launch_expand(const void* V, void* W, int64_t N, int c, int ld, cons
     k_expand<T, 2><<<blocks, 256, 0, s>>>((const cx<T>*)V, (cx<T>*)W, total, c, ld, op);
   else
     k_expand<T, 4><<<blocks, 256, 0, s>>>((const cx<T>*)V, (cx<T>*)W, total, c, ld, op);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -215,6 +217,7 @@ cudaError_t launch_expand_adj(const void* Wbar, const void* Vin, void* Vbar, int
   else
     k_expand_adj<T, 4><<<blocks, 256, 0, s>>>((const cx<T>*)Wbar, (const cx<T>*)Vin, (cx<T>*)Vbar,
                                               total, c, ld, op, grad_partials);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -261,6 +264,7 @@ cudaError_t launch_pauli_apply(const void* V, void* out, int64_t N, int c, int l
   const int blocks = grid_for(total, 256);
   k_pauli_apply<T><<<blocks, 256, 0, s>>>((const cx<T>*)V, (cx<T>*)out, total, c, ld, T_terms, xm, zm,
                                           coeff);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -275,6 +279,7 @@ __global__ void k_sum(const double* in, int count, double* out, int accumulate) 
 
 cudaError_t launch_sum(const double* in, int count, double* out, int accumulate, cudaStream_t s) {
   k_sum<<<1, 256, 0, s>>>(in, count, out, accumulate);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -121,8 +121,9 @@ __global__ void __launch_bounds__(256) k_gram(const cx<T>* __restrict__ A, int l
 
 // out[i][j] = sum_s partials[s][i][j] in split order; Hermitian: fill the lower
 // triangle from the upper one and make the diagonal exactly real.
-__global__ void k_gram_reduce(const double2* __restrict__ partials, int splits, int ma, int mb,
-                              int hermitian, double2* __restrict__ out) {
+template <typename P>
+__global__ void k_gram_reduce(const P* __restrict__ partials, int splits, int ma, int mb, int hermitian,
+                              double2* __restrict__ out) {
   const int64_t total = (int64_t)ma * mb;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -130,8 +131,8 @@ __global__ void k_gram_reduce(const double2* __restrict__ partials, int splits, 
     if (hermitian && (i / TILE) > (j / TILE)) continue;  // tile not computed
     double sr = 0.0, si = 0.0;
     for (int s = 0; s < splits; ++s) {
-      const double2 v = partials[(int64_t)s * total + e];
-      sr += v.x; si += v.y;
+      const P v = partials[(int64_t)s * total + e];
+      sr += (double)v.x; si += (double)v.y;
     }
     if (hermitian) {
       if (i == j) {
@@ -154,7 +155,17 @@ cudaError_t launch_gram_reduce_herm(const double2* partials, int splits, int m, 
   const int64_t total = (int64_t)m * m;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4096) blocks = 4096;
-  k_gram_reduce<<<blocks, 256, 0, s>>>(partials, splits, m, m, 1, out);
+  k_gram_reduce<double2><<<blocks, 256, 0, s>>>(partials, splits, m, m, 1, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_reduce_herm_f32(const float2* partials, int splits, int m, double2* out, cudaStream_t s) {
+  const int64_t total = (int64_t)m * m;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_gram_reduce<float2><<<blocks, 256, 0, s>>>(partials, splits, m, m, 1, out);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -180,12 +191,14 @@ cudaError_t launch_gram(const void* A, int lda, int ma, const void* B, int ldb, 
   dim3 grid(tiles, splits);
   k_gram<T><<<grid, 256, 0, s>>>((const cx<T>*)A, lda, ma, (const cx<T>*)B, ldb, mb, N, chunk, tj,
                                  hermitian ? 1 : 0, partials, pairbit, chalf);
+  note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t total = (int64_t)ma * mb;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4096) blocks = 4096;
-  k_gram_reduce<<<blocks, 256, 0, s>>>(partials, splits, ma, mb, hermitian ? 1 : 0, out);
+  k_gram_reduce<double2><<<blocks, 256, 0, s>>>(partials, splits, ma, mb, hermitian ? 1 : 0, out);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -280,6 +293,7 @@ cudaError_t launch_rowmat(const void* A1, int lda1, int k1, const double2* M1, i
   dim3 grid((unsigned)((N + TILE - 1) / TILE), (unsigned)((p + TILE - 1) / TILE));
   k_rowmat<T><<<grid, 256, 0, s>>>((const cx<T>*)A1, lda1, k1, M1, ldm1, (const cx<T>*)A2, lda2, k2, M2,
                                    ldm2, (cx<T>*)Y, ldy, p, N, pairbit, chalf, phalf);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -318,12 +332,14 @@ __global__ void k_build_proj(const double2* __restrict__ U, int c, int K, int k,
 cudaError_t launch_assemble_gram(const double2* S, int c, int K, const PairQ& q, double2* Gp, cudaStream_t s) {
   const int m = K * c;
   k_assemble_gram<<<(m * m + 255) / 256, 256, 0, s>>>(S, c, K, q, Gp);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_build_proj(const double2* U, int c, int K, int k, const PairQ& q, double2* D, cudaStream_t s) {
   const int n = 4 * c * k;
   k_build_proj<<<(n + 255) / 256, 256, 0, s>>>(U, c, K, k, q, D);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -425,11 +441,16 @@ cudaError_t launch_trunc_batch_gemms(const TruncTask* tasks, const int* gram_bst
   if (ntasks <= 0) return cudaSuccess;
   if (phase == 0) {
     k_pair_gram_batch<T><<<gram_blocks, 256, 0, s>>>(tasks, gram_bstart, ntasks);
+    note_launches(1);
     k_reduce_assemble_batch<<<dim3((max_m2 + 255) / 256, ntasks), 256, 0, s>>>(tasks);
+    note_launches(1);
   } else {
     k_build_proj_batch<<<dim3((max_d + 255) / 256, ntasks), 256, 0, s>>>(tasks);
+    note_launches(1);
     k_pair_rowmat_batch<T><<<proj_blocks, 256, 0, s>>>(tasks, proj_bstart, ntasks);
+    note_launches(1);
     k_accum_batch<<<(ntasks + 127) / 128, 128, 0, s>>>(tasks, ntasks);
+    note_launches(1);
   }
   return cudaGetLastError();
 }
@@ -503,11 +524,14 @@ cudaError_t launch_trunc_adj_small(const double2* C, const double2* U, const dou
   const int d = m - k;
   if (d > 0) {
     k_tadj_fa<<<(d * k + 127) / 128, 128, 0, s>>>(C, U, lam, m, k, FA);
+    note_launches(1);
     k_tadj_t1<<<(m * k + 127) / 128, 128, 0, s>>>(U, FA, m, k, T1);
+    note_launches(1);
   } else {
     cudaMemsetAsync(T1, 0, sizeof(double2) * (size_t)m * k, s);
   }
   k_tadj_mcat<<<(m * m + 127) / 128, 128, 0, s>>>(T1, U, m, k, Mcat);
+  note_launches(1);
   return cudaGetLastError();
 }
 

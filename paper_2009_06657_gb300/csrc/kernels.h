@@ -22,6 +22,11 @@ struct GroupOp {
 };
 
 // Result block written by the eigensolver (device memory).
+// Process-wide count of kernels this library has launched (graph replays add
+// the kernels of the graph); read through lr_launch_count.
+void note_launches(long long n);
+long long launches_total();
+
 struct EigOut {
   int k;            // kept columns
   int sweeps;       // Jacobi sweeps used
@@ -63,6 +68,8 @@ cudaError_t launch_gram(const void* A, int lda, int ma, const void* B, int ldb, 
 int gram_splits(int64_t N, int ma, int mb);
 // sum split partials of a Hermitian m x m Gram (upper 64-tiles computed) into out
 cudaError_t launch_gram_reduce_herm(const double2* partials, int splits, int m, double2* out, cudaStream_t s);
+// the same from FP32 partials (summed in FP64)
+cudaError_t launch_gram_reduce_herm_f32(const float2* partials, int splits, int m, double2* out, cudaStream_t s);
 // tensor-core (tcgen05, 3xTF32) pair Gram for the FP32 state; status: device int set on a wait timeout
 bool gram_pair_tc_supported(int c, int64_t N2);
 cudaError_t launch_gram_pair_tc(const void* V, int ld, int c, int pairbit, int64_t N2, double2* partials,

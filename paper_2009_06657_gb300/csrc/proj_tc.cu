@@ -5,13 +5,24 @@
 //
 // Real form: with Z the pair rows as interleaved (re, im) floats (4c values)
 // and D_r the 4c x 4k real matrix of D ([[Re, Im], [-Im, Re]] per entry), the
-// output row is Z D_r. One CTA computes 128 pair rows: the 4c-long rows are
-// staged 32 real columns at a time (K-major core-matrix layout, TF32 high part
-// + FP32 remainder), D_r^T is pre-split and pre-laid-out in global memory by a
-// small kernel and copied per chunk, and one thread issues the 3xTF32 MMAs
-// (M = 128, N = 4k, K = 8) into a tensor-memory accumulator; two buffers and
-// two mbarriers overlap staging with the MMAs. The epilogue reads the FP32
-// accumulator with tcgen05.ld and writes complex64 rows x0 and x0 | 2^q.
+// output row is Z D_r. One CTA computes 256 pair rows as two M = 128 MMA tiles
+// that share each staged chunk of D_r (two accumulators, 512 tensor-memory
+// columns). The K dimension (4c real input columns) is staged 16 at a time in
+// a three-deep ring:
+//   * warp 8 streams D_r^T chunks (pre-split into TF32 high part + FP32
+//     remainder and pre-laid-out in the K-major core-matrix layout by
+//     k_proj_prep) with one bulk async copy per chunk (cp.async.bulk, completion
+//     on an mbarrier), as soon as the MMAs that used the slot have finished;
+//   * warps 0-7 keep the pair rows of the next two chunks in flight in
+//     registers while the current one is split and stored, so global latency
+//     overlaps the MMAs;
+//   * warps 0-7 arrive on the slot's "full" mbarrier once the chunk is stored;
+//   * warp 9 waits for both, issues the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi,
+//     M = 128, N = 4k, K = 8) for both tiles and commits them to the slot's
+//     "free" mbarrier, which the row and D_r producers wait on before reuse.
+// The epilogue reads each accumulator with tcgen05.ld, transposes 32 x 32
+// blocks through shared memory and writes whole 128-byte row segments of
+// rows x0 and x0 | 2^q. Every wait is bounded and sets the status word.
 #include <stdint.h>
 
 #include "common.cuh"
@@ -24,22 +35,29 @@ namespace {
 
 using namespace tc;
 
-constexpr int PT_THREADS = 256;
-constexpr int PT_M = 128;   // pair rows per CTA
-constexpr int PT_KC = 32;   // real input columns per chunk
+constexpr int PT_AW = 256;            // row-staging / epilogue threads (warps 0-7)
+constexpr int PT_THREADS = PT_AW + 64;  // + warp 8: D_r streaming, warp 9: MMA issue
+constexpr int PT_TILE = 128;
+constexpr int PT_ROWS = 2 * PT_TILE;  // pair rows per CTA
+constexpr int PT_KC = 16;             // real input columns per chunk
 constexpr int PT_MAXN = 256;
+constexpr int PT_NS = 3;              // ring depth
 constexpr uint32_t PT_LBO = 128;
 constexpr uint32_t PT_SBO = (PT_KC / 4) * 128;
-constexpr int PT_A_FLOATS = PT_M * PT_KC;        // one of hi / lo
-constexpr int PT_B_FLOATS = PT_MAXN * PT_KC;     // one of hi / lo
+constexpr int PT_A_FLOATS = PT_ROWS * PT_KC;   // one of hi / lo
+constexpr int PT_B_FLOATS = PT_MAXN * PT_KC;   // one of hi / lo
 constexpr int PT_STAGE_FLOATS = 2 * PT_A_FLOATS + 2 * PT_B_FLOATS;
-constexpr int PT_SMEM = 2 * PT_STAGE_FLOATS * 4 + 1024;
+constexpr int PT_SMEM = PT_NS * PT_STAGE_FLOATS * 4 + 1024;
+constexpr int PT_EP_LD = 36;          // floats per row of the epilogue transpose tile
 
 __device__ __forceinline__ int core_off(int row, int kl) {  // floats, K-major core-matrix layout
   return ((row >> 3) * (PT_KC / 4) + (kl >> 2)) * 32 + (row & 7) * 4 + (kl & 3);
 }
 
-// D (2c x 2k complex, row-major) -> per chunk kc: [hi | lo] of D_r^T (N = 4k rows x 32)
+// barrier of the row-staging warps only (warp 8 keeps streaming)
+__device__ __forceinline__ void bar_rows() { asm volatile("barrier.sync 1, %0;" ::"n"(PT_AW) : "memory"); }
+
+// D (2c x 2k complex, row-major) -> per chunk kc: [hi | lo] of D_r^T (N = 4k rows x 16)
 __global__ void k_proj_prep(const double2* __restrict__ D, int c, int k, float* __restrict__ B) {
   const int N = 4 * k, K = 4 * c;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -58,123 +76,183 @@ __global__ void k_proj_prep(const double2* __restrict__ D, int c, int k, float* 
   chunk[N * PT_KC + core_off(n, kl)] = f - h;
 }
 
+// the four float4 of pair-row data this thread stages for chunk ch
+__device__ __forceinline__ void load_rows(const float2* __restrict__ V, int ld, int c, int pairbit, int64_t N2,
+                                          int64_t m0, int ch, int warp, int lane, float4 (&ra)[4]) {
+  const int kg = lane >> 3;
+  const int n0 = ch * PT_KC;
+  const int b = n0 >= 2 * c;  // the whole chunk lies in one half (2c is a multiple of 16)
+  const int cc = ((n0 - b * 2 * c) >> 1) + kg * 2;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = (warp * 4 + i) * 8 + (lane & 7);
+    const int64_t x = m0 + row;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (x < N2) {
+      const uint64_t xp = insert_zero((uint64_t)x, pairbit) | ((uint64_t)b << pairbit);
+      v = __ldg((const float4*)(V + xp * (uint64_t)ld + cc));
+    }
+    ra[i] = v;
+  }
+}
+
 __global__ void __launch_bounds__(PT_THREADS, 1)
     k_proj_pair_tc(const float2* __restrict__ V, int ld, int c, int k, int pairbit, int64_t N2,
                    const float* __restrict__ B, float2* __restrict__ W, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* stage = (float*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar_mma[PT_NS], mbar_b[PT_NS], mfull[PT_NS];
+  __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = 4 * c, N = 4 * k;
   const int nchunks = K / PT_KC;
-  const int64_t m0 = (int64_t)blockIdx.x * PT_M;
+  const int64_t m0 = (int64_t)blockIdx.x * PT_ROWS;
+  const uint32_t b_bytes = (uint32_t)(2 * N * PT_KC * 4);
 
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    for (int s = 0; s < PT_NS; ++s) {
+      mbar_init(smem_u32(&mbar_mma[s]), 1);
+      mbar_init(smem_u32(&mbar_b[s]), 1);
+      mbar_init(smem_u32(&mfull[s]), PT_AW);
+    }
+    s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  bool ok = true;
 
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const int s = ch & 1;
-    float* a_hi = stage + s * PT_STAGE_FLOATS;
-    float* a_lo = a_hi + PT_A_FLOATS;
-    float* b_hi = a_lo + PT_A_FLOATS;
-    float* b_lo = b_hi + PT_B_FLOATS;
-    if (ch >= 2) {
-      if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((ch - 2) >> 1) & 1))) ok = false;
+  if (warp == PT_AW / 32) {
+    // ---- D_r streaming: chunk ch into slot ch % 3 once MMAs of ch - 3 are done
+    if (lane == 0) {
+      bool ok = true;
+      int issued = 0;
+      for (int ch = 0; ch < nchunks && ok; ++ch) {
+        const int s = ch % PT_NS;
+        if (ch >= PT_NS) ok = mbar_wait(smem_u32(&mbar_mma[s]), (uint32_t)(((ch - PT_NS) / PT_NS) & 1));
+        if (!ok) break;
+        float* bdst = stage + s * PT_STAGE_FLOATS + 2 * PT_A_FLOATS;
+        bulk_load(smem_u32(bdst), B + (int64_t)ch * 2 * N * PT_KC, b_bytes, smem_u32(&mbar_b[s]));
+        issued = ch + 1;
+      }
+      // no copy may still be landing when the CTA leaves
+      for (int ch = issued - PT_NS > 0 ? issued - PT_NS : 0; ch < issued; ++ch)
+        if (!mbar_wait(smem_u32(&mbar_b[ch % PT_NS]), (uint32_t)((ch / PT_NS) & 1))) ok = false;
+      if (!ok) s_fail = 1;
     }
-    // A: 128 rows x 32 real columns; a float4 covers 4 consecutive real columns
-    // (two complex values of one physical row). Each group of 8 lanes stores
-    // one 128-byte core matrix (8 rows, same 4-column group): no bank conflicts.
-    {
-      const int rr = lane & 7, grp = lane >> 3;
-      for (int u = warp; u < (PT_M / 8) * 2; u += PT_THREADS / 32) {
-        const int g = u >> 1, kgb = (u & 1) * 4;  // row group, first of 4 column groups
-        const int row = g * 8 + rr, kg = kgb + grp;
-        const int64_t x = m0 + row;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (x < N2) {
-          const int n = ch * PT_KC + kg * 4;  // first real column
-          const int b = n >= 2 * c;
-          const int cc = (n - b * 2 * c) >> 1;
-          const uint64_t xp = insert_zero((uint64_t)x, pairbit) | ((uint64_t)b << pairbit);
-          v = __ldg((const float4*)(V + xp * (uint64_t)ld + cc));
+  } else if (warp == PT_AW / 32 + 1) {
+    // ---- MMA issue: chunk ch once its rows are staged and its D_r chunk landed
+    if (lane == 0) {
+      bool ok = true;
+      for (int ch = 0; ch < nchunks && ok; ++ch) {
+        const int s = ch % PT_NS;
+        ok = mbar_wait(smem_u32(&mfull[s]), (uint32_t)((ch / PT_NS) & 1)) &&
+             mbar_wait(smem_u32(&mbar_b[s]), (uint32_t)((ch / PT_NS) & 1));
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        float* a_hi = stage + s * PT_STAGE_FLOATS;
+        float* a_lo = a_hi + PT_A_FLOATS;
+        float* b_hi = a_lo + PT_A_FLOATS;
+        float* b_lo = b_hi + N * PT_KC;
+        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+        const uint32_t id = idesc_tf32(N);
+#pragma unroll
+        for (int ks = 0; ks < PT_KC / 8; ++ks) {
+          const uint32_t o = (uint32_t)ks * 2 * PT_LBO;
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const uint32_t ot = o + (uint32_t)t * (PT_TILE / 8) * PT_SBO;
+            const uint32_t d = tmem + (uint32_t)t * 256u;
+            const uint32_t first = (ch == 0 && ks == 0) ? 0u : 1u;
+            mma_tf32(d, sdesc(ah + ot, PT_LBO, PT_SBO), sdesc(bh + o, PT_LBO, PT_SBO), id, first);
+            mma_tf32(d, sdesc(ah + ot, PT_LBO, PT_SBO), sdesc(bl + o, PT_LBO, PT_SBO), id, 1u);
+            mma_tf32(d, sdesc(al + ot, PT_LBO, PT_SBO), sdesc(bh + o, PT_LBO, PT_SBO), id, 1u);
+          }
         }
+        commit(smem_u32(&mbar_mma[s]));
+      }
+      if (!ok) s_fail = 1;
+    }
+  } else {
+    // ---- pair rows: split into TF32 high part + remainder; two register sets
+    // keep the rows of chunks ch + 1 and ch + 2 in flight while chunk ch is
+    // split and stored
+    bool ok = true;
+    float4 ra[4], rb[4];
+    auto step = [&](int ch, float4 (&rv)[4]) {
+      const int s = ch % PT_NS;
+      float* a_hi = stage + s * PT_STAGE_FLOATS;
+      float* a_lo = a_hi + PT_A_FLOATS;
+      if (ch >= PT_NS && ok) ok = mbar_wait(smem_u32(&mbar_mma[s]), (uint32_t)(((ch - PT_NS) / PT_NS) & 1));
+      if (!ok) return;
+      const int kg = lane >> 3;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = (warp * 4 + i) * 8 + (lane & 7);
+        const float4 v = rv[i];
         const float h0 = tf32_hi(v.x), h1 = tf32_hi(v.y), h2 = tf32_hi(v.z), h3 = tf32_hi(v.w);
         const int off = core_off(row, kg * 4);
         *(float4*)(a_hi + off) = make_float4(h0, h1, h2, h3);
         *(float4*)(a_lo + off) = make_float4(v.x - h0, v.y - h1, v.z - h2, v.w - h3);
       }
+      if (ch + 2 < nchunks) load_rows(V, ld, c, pairbit, N2, m0, ch + 2, warp, lane, rv);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&mfull[s])) : "memory");
+    };
+    if (nchunks > 0) load_rows(V, ld, c, pairbit, N2, m0, 0, warp, lane, ra);
+    if (nchunks > 1) load_rows(V, ld, c, pairbit, N2, m0, 1, warp, lane, rb);
+    for (int ch = 0; ch < nchunks && ok; ch += 2) {
+      step(ch, ra);
+      if (ch + 1 < nchunks) step(ch + 1, rb);
     }
-    // B: prepared chunk (hi then lo), contiguous N x 32 floats each
-    {
-      const float4* src = (const float4*)(B + (int64_t)ch * 2 * (N * PT_KC));
-      float4* dst_hi = (float4*)b_hi;
-      float4* dst_lo = (float4*)b_lo;
-      const int n4 = N * PT_KC / 4;
-      for (int i = tid; i < n4; i += PT_THREADS) {
-        dst_hi[i] = __ldg(src + i);
-        dst_lo[i] = __ldg(src + n4 + i);
-      }
+    if (nchunks > 0 && ok) {
+      const int ch = nchunks - 1;
+      ok = mbar_wait(smem_u32(&mbar_mma[ch % PT_NS]), (uint32_t)((ch / PT_NS) & 1));
     }
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-      const uint32_t id = idesc_tf32(N);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) s_fail = 1;
+    bar_rows();
+    if (__shfl_sync(0xffffffffu, s_fail, 0) == 0) {  // warp-uniform: tcgen05.ld is warp-collective
+      // ---- epilogue: warp w reads tile w / 4, tensor-memory lanes 32 (w % 4) .. + 31
+      const int t = warp >> 2, wq = warp & 3;
+      float* ep = stage + warp * (32 * PT_EP_LD);  // the ring is idle now
+      const int64_t rbase = m0 + t * PT_TILE + wq * 32;
+      for (int cb = 0; cb < N; cb += 32) {
+        float v[32];
+        tmem_ld32(tmem + (uint32_t)t * 256u + ((uint32_t)(wq * 32) << 16) + (uint32_t)cb, v);
 #pragma unroll
-      for (int ks = 0; ks < PT_KC / 8; ++ks) {
-        const uint32_t o = (uint32_t)ks * 2 * PT_LBO;
-        const uint32_t first = (ch == 0 && ks == 0) ? 0u : 1u;
-        mma_tf32(tmem, sdesc(ah + o, PT_LBO, PT_SBO), sdesc(bh + o, PT_LBO, PT_SBO), id, first);
-        mma_tf32(tmem, sdesc(ah + o, PT_LBO, PT_SBO), sdesc(bl + o, PT_LBO, PT_SBO), id, 1u);
-        mma_tf32(tmem, sdesc(al + o, PT_LBO, PT_SBO), sdesc(bh + o, PT_LBO, PT_SBO), id, 1u);
-      }
-      commit(smem_u32(&mbar[s]));
-    }
-  }
-  for (int ch = nchunks - 2; ch < nchunks; ++ch) {
-    if (ch < 0) continue;
-    if (!mbar_wait(smem_u32(&mbar[ch & 1]), (uint32_t)((ch >> 1) & 1))) ok = false;
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  ok = __syncthreads_and(ok) != 0;
-  if (!ok && tid == 0) atomicExch(status, 1);
-
-  // epilogue: warps 0-3, row = 32 warp + lane; real output columns in chunks of 32
-  if (warp < 4 && ok) {
-    const int row = warp * 32 + lane;
-    const int64_t x = m0 + row;
-    for (int cb = 0; cb < N; cb += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-      if (x < N2) {
+        for (int j = 0; j < 8; ++j)
+          *(float4*)(ep + lane * PT_EP_LD + 4 * j) = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        __syncwarp();
+        const int piece = lane & 7;
+        const int Jp = cb / 2 + 2 * piece;  // first of the piece's two complex output columns
+        if (Jp < 2 * k) {
+          const int b = Jp >= k;
+          const int col = Jp - b * k;
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int J = cb / 2 + jj;  // complex output column of the pair row
-          if (J >= 2 * k) break;
-          const int b = J >= k;
-          const uint64_t xp = insert_zero((uint64_t)x, pairbit) | ((uint64_t)b << pairbit);
-          W[xp * (uint64_t)ld + (J - b * k)] = make_float2(v[2 * jj], v[2 * jj + 1]);
+          for (int i = 0; i < 8; ++i) {
+            const int rl = i * 4 + (lane >> 3);
+            const int64_t x = rbase + rl;
+            if (x < N2) {
+              const uint64_t xp = insert_zero((uint64_t)x, pairbit) | ((uint64_t)b << pairbit);
+              *(float4*)(W + xp * (uint64_t)ld + col) = *(const float4*)(ep + rl * PT_EP_LD + 4 * piece);
+            }
+          }
         }
+        __syncwarp();
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  if (tid == 0 && s_fail) atomicExch(status, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
 }  // namespace
@@ -195,9 +273,11 @@ cudaError_t launch_proj_pair_tc(const void* V, int ld, int c, int k, int pairbit
   }
   const int nel = (4 * k) * (4 * c);
   k_proj_prep<<<(nel + 255) / 256, 256, 0, s>>>(D, c, k, Bscratch);
-  const int blocks = (int)((N2 + PT_M - 1) / PT_M);
+  note_launches(1);
+  const int blocks = (int)((N2 + PT_ROWS - 1) / PT_ROWS);
   k_proj_pair_tc<<<blocks, PT_THREADS, PT_SMEM, s>>>((const float2*)V, ld, c, k, pairbit, N2, Bscratch,
                                                       (float2*)W, status);
+  note_launches(1);
   return cudaGetLastError();
 }
 

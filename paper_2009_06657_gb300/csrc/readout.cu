@@ -124,6 +124,7 @@ static int ro_blocks(int64_t N) {
 template <typename T>
 cudaError_t launch_probs(const void* V, int64_t N, int c, int ld, void* out, cudaStream_t s) {
   k_probs<T><<<ro_blocks(N), RO_THREADS, 0, s>>>((const cx<T>*)V, N, c, ld, (T*)out);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -132,7 +133,9 @@ cudaError_t launch_zexp(const void* V, int64_t N, int c, int ld, int n, double* 
                         cudaStream_t s) {
   const int nb = ro_blocks(N);
   k_zexp<T><<<nb, RO_THREADS, 0, s>>>((const cx<T>*)V, N, c, ld, n, partials);
+  note_launches(1);
   k_colsum<<<1, 32, 0, s>>>(partials, nb, 1, 32, n + 1, out);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -143,8 +146,10 @@ cudaError_t launch_pauli_expect(const void* V, int64_t N, int c, int ld, int T_t
   const int nb = ro_blocks(N);
   dim3 grid(nb, T_terms);
   k_pauli_expect<T><<<grid, RO_THREADS, 0, s>>>((const cx<T>*)V, N, c, ld, xm, zm, partials);
+  note_launches(1);
   // out[t] = sum_b partials[t * nb + b]
   k_colsum<<<(T_terms + 127) / 128, 128, 0, s>>>(partials, nb, nb, 1, T_terms, out);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 // kernel (Eqs. 3-4); a truncation (Sec. II.B) runs Gram -> eigensolve ->
 // projection on the handle's stream without a host round trip unless the
 // caller asks for a value.
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -21,7 +22,12 @@ using zc = std::complex<double>;
 namespace lret {
 thread_local char g_errmsg[256];
 void set_error(const char* fmt, const char* a, const char* b) { snprintf(g_errmsg, sizeof(g_errmsg), fmt, a, b); }
+static std::atomic<long long> g_launches{0};
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace lret
+
+extern "C" int64_t lr_launch_count(void) { return (int64_t)lret::launches_total(); }
 
 namespace {
 
@@ -374,6 +380,7 @@ int run_eigh(lr_ctx* h, int m, int r_eff, double eps, int* k_out) {
   }
   tend(h, LR_K_EIGH, te);
   k_accum<<<1, 1, 0, h->stream>>>(h->eo, h->acc);
+  note_launches(1);
   CK(cudaGetLastError());
   if (r_eff > 0) {
     *k_out = r_eff < m ? r_eff : m;
@@ -1020,7 +1027,7 @@ int lr_get_info(lr_handle h, lr_info* info) {
   info->stages = (int64_t)h->tape.size();
   info->discarded = h->h_small[0];
   info->last_gap = h->h_small[1];
-  if (tcs) return LR_ETIMEOUT;
+  if (tcs || h->h_small[2] >= 3) return LR_ETIMEOUT;  // eigensolver status 3: a bounded wait gave up
   return h->h_small[2] > 0 ? LR_ENOCONV : LR_OK;
 }
 

@@ -49,6 +49,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
   return done != 0;
 }
 
+// one-shot bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completion counted on an mbarrier that this thread arms with the byte count
+__device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst_smem),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count));
+}
+
 // round to the nearest TF32 value (10 explicit mantissa bits)
 __device__ __forceinline__ float tf32_hi(float x) {
   uint32_t u = __float_as_uint(x);

@@ -48,6 +48,11 @@ def pauli_masks(terms, n):
     return xm, zm, cf
 
 
+def launch_count():
+    """Kernels launched by the library so far in this process (lr_launch_count)."""
+    return int(lib.lr_launch_count())
+
+
 def kraus_preset(kind, p):
     out = np.zeros(32, dtype=np.float64)
     K = C.c_int(0)

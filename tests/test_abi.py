@@ -68,3 +68,8 @@ def test_pauli_masks_encoding():
     from paper_2009_06657_gb300.sim import pauli_masks
     xm, zm, cf = pauli_masks([(0.5, [(0, "X"), (2, "Y"), (3, "Z")])], 4)
     assert int(xm[0]) == 0b0101 and int(zm[0]) == 0b1100 and cf[0] == 0.5
+
+
+def test_launch_counter_reads_without_device(lib):
+    n = lib.lib.lr_launch_count()
+    assert isinstance(n, int) and n >= 0
