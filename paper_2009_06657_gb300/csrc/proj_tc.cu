@@ -13,7 +13,7 @@
 //     remainder and pre-laid-out in the K-major core-matrix layout by
 //     k_proj_prep) with one bulk async copy per chunk (cp.async.bulk, completion
 //     on an mbarrier), as soon as the MMAs that used the slot have finished;
-//   * warps 0-7 keep the pair rows of the next two chunks in flight in
+//   * warps 0-7 keep the pair rows of the next three chunks in flight in
 //     registers while the current one is split and stored, so global latency
 //     overlaps the MMAs;
 //   * warps 0-7 arrive on the slot's "full" mbarrier once the chunk is stored;
@@ -49,6 +49,7 @@ constexpr int PT_B_FLOATS = PT_MAXN * PT_KC;   // one of hi / lo
 constexpr int PT_STAGE_FLOATS = 2 * PT_A_FLOATS + 2 * PT_B_FLOATS;
 constexpr int PT_SMEM = PT_NS * PT_STAGE_FLOATS * 4 + 1024;
 constexpr int PT_EP_LD = 36;          // floats per row of the epilogue transpose tile
+constexpr int PF = 3;                 // chunks of pair rows in flight in registers
 
 __device__ __forceinline__ int core_off(int row, int kl) {  // floats, K-major core-matrix layout
   return ((row >> 3) * (PT_KC / 4) + (kl >> 2)) * 32 + (row & 7) * 4 + (kl & 3);
@@ -180,11 +181,11 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       if (!ok) s_fail = 1;
     }
   } else {
-    // ---- pair rows: split into TF32 high part + remainder; two register sets
-    // keep the rows of chunks ch + 1 and ch + 2 in flight while chunk ch is
-    // split and stored
+    // ---- pair rows: split into TF32 high part + remainder; three register sets
+    // keep the rows of chunks ch + 1 .. ch + 3 in flight while chunk ch is split
+    // and stored
     bool ok = true;
-    float4 ra[4], rb[4];
+    float4 ra[4], rb[4], rc[4];
     auto step = [&](int ch, float4 (&rv)[4]) {
       const int s = ch % PT_NS;
       float* a_hi = stage + s * PT_STAGE_FLOATS;
@@ -201,15 +202,17 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
         *(float4*)(a_hi + off) = make_float4(h0, h1, h2, h3);
         *(float4*)(a_lo + off) = make_float4(v.x - h0, v.y - h1, v.z - h2, v.w - h3);
       }
-      if (ch + 2 < nchunks) load_rows(V, ld, c, pairbit, N2, m0, ch + 2, warp, lane, rv);
+      if (ch + PF < nchunks) load_rows(V, ld, c, pairbit, N2, m0, ch + PF, warp, lane, rv);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&mfull[s])) : "memory");
     };
     if (nchunks > 0) load_rows(V, ld, c, pairbit, N2, m0, 0, warp, lane, ra);
     if (nchunks > 1) load_rows(V, ld, c, pairbit, N2, m0, 1, warp, lane, rb);
-    for (int ch = 0; ch < nchunks && ok; ch += 2) {
+    if (nchunks > 2) load_rows(V, ld, c, pairbit, N2, m0, 2, warp, lane, rc);
+    for (int ch = 0; ch < nchunks && ok; ch += PF) {
       step(ch, ra);
       if (ch + 1 < nchunks) step(ch + 1, rb);
+      if (ch + 2 < nchunks) step(ch + 2, rc);
     }
     if (nchunks > 0 && ok) {
       const int ch = nchunks - 1;
