@@ -381,6 +381,12 @@ def algorithmic():
     }
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the same kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum, m = 256); the eigensolver's
+# traffic does not depend on the qubit count (it reads the m x m Gram matrix).
+NCU_TRAFFIC = {"eigh": 1188864}
+
+
 def kernel_rooflines(kt, peaks):
     alg = algorithmic()
     out = {}
@@ -473,7 +479,7 @@ def main():
         "kernel_ms_per_step": {k: v[0] for k, v in kt.items()},
         "kernel_launches_per_step": {k: v[1] for k, v in kt.items()},
         "roofline": {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                     "frac": (ach / peak) if ach else None, "traffic": None,
+                     "frac": (ach / peak) if ach else None, "traffic": NCU_TRAFFIC.get(dom),
                      "peak_source": peaks["source"]},
         "kernels": kr,
         "clocks": res["clk"],
