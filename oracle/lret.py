@@ -13,7 +13,10 @@ definitions directly, without blocking or fusion:
 * ``LRETState`` -- Algorithm 1 (Sec. II.D) with one-qubit Kraus groups
   (Sec. II.C, M = 1): L <- G L (Eq. 3); L <- [sqrt(p_1) K_1 L, ...] (Eq. 4);
   eigenvalue truncation through the small Gram matrix L^dag L (Sec. II.B,
-  Theorem 1 of App. B); readouts Prob(x) (Eq. 9) and Tr(L^dag O L) (Sec. II.D).
+  Theorem 1 of App. B); readouts Prob(x) (Eq. 9) and Tr(L^dag O L) (Sec. II.D),
+  the von Neumann entropy of App. A from the spectrum of L^dag L.
+* ``sample_inverse_cdf`` -- measurement counts drawn from Prob(x) (Sec. II.D)
+  with caller-supplied uniforms.
 
 Conventions (the paper fixes none of them):
 
@@ -287,6 +290,37 @@ class LRETState:
 
     def trace(self):
         return float(np.real(np.sum(np.abs(self.L) ** 2)))
+
+    # App. A: S = -Tr(rho log2 rho) of the normalised state. The nonzero
+    # eigenvalues of rho = L L^dag are those of L^dag L (Theorem 1).
+    def entropy(self):
+        G = self.L.conj().T @ self.L
+        return entropy_from_eigenvalues(np.linalg.eigvalsh(0.5 * (G + G.conj().T)))
+
+
+def entropy_from_eigenvalues(lam):
+    """S = -sum_i mu_i log2 mu_i with mu = max(lam, 0) / sum(max(lam, 0)) (App. A:
+    von Neumann entropy in bits of the normalised state; zero terms omitted).
+    The effective rank of App. A is then 2**S."""
+    lp = np.clip(np.asarray(lam, dtype=np.float64), 0.0, None)
+    mu = lp / lp.sum()
+    mu = mu[mu > 0]
+    return float(-np.sum(mu * np.log2(mu)))
+
+
+def entropy_dense(rho):
+    """The same entropy from the full density matrix (2^n x 2^n), for pins."""
+    return entropy_from_eigenvalues(np.linalg.eigvalsh(0.5 * (rho + rho.conj().T)))
+
+
+def sample_inverse_cdf(probs, uniforms):
+    """Measurement sampling from Prob(x) (Sec. II.D): shot s is the smallest x
+    with CDF(x) > u_s * CDF(last), CDF the running sum of Prob(x) in index order,
+    clamped to the last index. ``uniforms`` are the caller's draws in [0, 1)."""
+    cdf = np.cumsum(np.asarray(probs, dtype=np.float64))
+    t = np.asarray(uniforms, dtype=np.float64) * cdf[-1]
+    idx = np.searchsorted(cdf, t, side="right")
+    return np.minimum(idx, len(cdf) - 1).astype(np.int64)
 
 
 # --------------------------------------------------------------------------

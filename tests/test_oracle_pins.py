@@ -254,3 +254,83 @@ def test_distortion_definition():
     pn = np.array([0.6, 0.3, 0.1])
     pl = np.array([0.52, 0.29, 0.19])
     assert abs(O.distortion(pl, pe, pn) - (0.04 / 0.2)) < 1e-15
+
+
+# ---- von Neumann entropy (App. A) and measurement sampling (Sec. II.D) -----
+
+def _h2(x):
+    return -x * np.log2(x) - (1 - x) * np.log2(1 - x)
+
+
+def test_entropy_pure_state_is_zero():
+    st = O.LRETState(3)
+    for q in range(3):
+        st.gate([q], O.rotation("Y", 0.3 + q))
+    st.gate([0, 1], O.cnot())
+    assert abs(st.entropy()) < 1e-12
+
+
+@pytest.mark.parametrize("p", [1e-3, 0.05, 0.75])
+def test_entropy_of_depolarized_product_state_closed_form(p):
+    # each qubit of |0..0> after its own depolarizing channel has spectrum
+    # (1 - 2p/3, 2p/3), so S = n * H2(2p/3) bits; p = 3/4 gives I/2 per qubit, S = n
+    n = 3
+    st, fdm = O.LRETState(n), O.FDMState(n)
+    for q in range(n):
+        st.channel(q, O.depolarizing(p))
+        fdm.channel(q, O.depolarizing(p))
+    want = n * _h2(2 * p / 3)
+    assert abs(st.entropy() - want) < 1e-12
+    assert abs(O.entropy_dense(fdm.rho) - want) < 1e-12
+    if p == 0.75:
+        assert abs(st.entropy() - n) < 1e-12
+
+
+def test_entropy_lowrank_matches_dense_after_truncation():
+    # the Gram-spectrum route (Theorem 1) against the eigenvalues of the dense
+    # L L^dag, on a truncated state (trace below 1: both normalise)
+    n = 5
+    ops = random_layered(n, 4, seed=77, noise=("dep", 0.02))
+    st = O.run_lret(n, ops, r=6)
+    assert st.trace() < 1.0
+    assert abs(st.entropy() - O.entropy_dense(st.rho())) < 1e-10
+    # normalisation: a scaled spectrum has the same entropy, two equal weights give 1 bit
+    assert abs(O.entropy_from_eigenvalues([0.2, 0.2]) - 1.0) < 1e-15
+    lam = np.array([0.5, 0.3, 0.2, 0.0, -1e-17])
+    assert abs(O.entropy_from_eigenvalues(3.7 * lam) - O.entropy_from_eigenvalues(lam)) < 1e-15
+
+
+def test_entropy_full_rank_lret_matches_fdm():
+    n = 4
+    ops = random_layered(n, 3, seed=78, noise=("mixed", 0.02, 0.05))
+    lret, fdm = O.run_lret(n, ops, r=2 ** n), O.run_fdm(n, ops)
+    assert abs(lret.entropy() - O.entropy_dense(fdm.rho)) < 1e-10
+
+
+def test_sampling_uniform_distribution_closed_form():
+    # Ry(pi/2) on every qubit gives Prob(x) = 2^-n: shot u lands on floor(u 2^n)
+    n = 4
+    sv = O.SVState(n)
+    for q in range(n):
+        sv.gate([q], O.rotation("Y", np.pi / 2))
+    k = np.arange(2 ** n)
+    u = (k + 0.5) / 2 ** n
+    assert np.array_equal(O.sample_inverse_cdf(sv.probs(), u), k)
+
+
+def test_sampling_matches_brute_force_definition():
+    rng = np.random.default_rng(5)
+    p = rng.random(7)
+    p[[1, 4]] = 0.0  # zero-probability outcomes are never drawn
+    u = rng.random(500)
+    got = O.sample_inverse_cdf(p, u)
+    tot = sum(p)
+    for s, us in zip(got, u):
+        acc, want = 0.0, len(p) - 1
+        for x in range(len(p)):
+            acc += p[x]
+            if acc > us * tot:
+                want = x
+                break
+        assert s == want
+        assert p[s] > 0
