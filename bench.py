@@ -201,6 +201,30 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / n_e2e
 
+        # readouts beyond the step (Sec. II.D sampling, App. A entropy) on the same state:
+        # 1000 shots from Prob(x) and the entropy of the 64-column state, CUDA events
+        rd = {}
+        u = np.random.default_rng(SEED + 2).random(1000)
+        sim.sample(u)  # warm-up (allocates the CDF buffer)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(5):
+            sim.sample(u)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_s = ev0.elapsed_time(ev1) / 5
+        sbytes = (1 << N_QUBITS) * RANK * 8 + (1 << N_QUBITS) * 8 * 3  # V once; CDF write, offset pass
+        rd["sample_1000_shots_ms"] = t_s
+        rd["sample_hbm_gbs"] = sbytes / (t_s * 1e-3) / 1e9
+        S = sim.entropy()
+        ev0.record(stream)
+        for _ in range(3):
+            S = sim.entropy()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        rd["entropy_ms"] = ev0.elapsed_time(ev1) / 3
+        rd["entropy_bits"], rd["effective_rank"] = S
+
     info = sim.info()
     sim.close()
     # FP64 comparators at the same size (few truncations; rate per noisy gate-step)
@@ -208,7 +232,7 @@ def run_ours(args, rank, world):
     adj = bench_adjoint(dev, stream) if (rank == 0 and not args.no_adjoint) else None
     bat = bench_batch(dev, stream, scale=args.batch_scale) if (rank == 0 and not args.no_batch) else None
     return dict(ms=ms, g_per=g_per, c_per=c_per, ktimes=ktimes, clk=clk, e2e_s=e2e_s, fp64=fp64, info=info,
-                adjoint=adj, batch=bat, launches=n_launch)
+                adjoint=adj, batch=bat, launches=n_launch, readouts=rd)
 
 
 def bench_fp64(args, layers, dev, stream):
@@ -486,6 +510,7 @@ def main():
         "e2e": {"value": res["g_per"] / res["e2e_s"], "unit": "noisy gate-steps/s",
                 "h2d_bytes_per_step": h2d_bytes(get_layers()[0]), "d2h_bytes_per_step": (1 << N_QUBITS) * 4 + 8},
         "fp64": None, "cpu_baseline": None, "adjoint": res.get("adjoint"), "batch": res.get("batch"),
+        "readouts": res.get("readouts"),
     }
     out["gpu_launches"] = res["launches"]  # the library's own launch counter over the timed region
     if res["fp64"]:

@@ -284,6 +284,27 @@ int lr_set_timing(lr_handle h, int on);
  * ms_out and counts_out have LR_NKCLASS entries. Synchronises and resets. */
 int lr_kernel_times(lr_handle h, double* ms_out, int64_t* counts_out);
 
+/* Measurement sampling (Sec. II.D: the counts of a computational-basis
+ * measurement are drawn from Prob(x), Eq. 9, without forming rho). Shot s is the
+ * smallest basis index x with CDF(x) > uniforms[s] * CDF(2^n - 1), CDF(x) the
+ * running sum of Prob(x) over indices 0..x (inverse-transform sampling), clamped
+ * to 2^n - 1. Prob(x) is formed as lr_probs forms it; the CDF is summed in FP64
+ * in a fixed order, so equal states and draws give equal shots.
+ *   shots    number of shots (>= 0)
+ *   uniforms host array of `shots` draws in [0, 1), owned by the caller (the
+ *            library draws no random numbers); any value outside -> LR_EINVAL
+ *   out_host host array of `shots` int64 basis indices, written by the call
+ * Flushes queued gates and channels, allocates its CDF buffer (2^n doubles) on
+ * the first call or when more shots are asked, and synchronises. */
+int lr_sample(lr_handle h, int shots, const double* uniforms, int64_t* out_host);
+
+/* Von Neumann entropy of the normalised state (App. A): S = -sum_i mu_i log2 mu_i,
+ * mu the eigenvalues of rho / Tr rho, obtained from the Gram matrix V^dag V
+ * (whose nonzero eigenvalues are those of rho = V V^dag, Theorem 1) with the FP64
+ * eigensolvers whatever the dtype; out_host[0] = S in bits, out_host[1] = 2^S (the
+ * effective rank). More than 256 columns -> LR_ECAPACITY. Synchronises. */
+int lr_entropy(lr_handle h, double* out_host);
+
 const char* lr_status_string(int status);
 
 /* Number of GPU kernels this library has launched in this process, over all

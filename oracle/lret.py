@@ -100,20 +100,43 @@ def channel_kraus(op):
     raise ValueError(op)
 
 
+def swap():
+    """Exchanges the two qubits: |b0 b1> -> |b1 b0> in the basis 2 b(q0) + b(q1)."""
+    M = np.zeros((4, 4), dtype=np.complex128)
+    for b0 in range(2):
+        for b1 in range(2):
+            M[2 * b1 + b0, 2 * b0 + b1] = 1.0
+    return M
+
+
+# fixed one-qubit gates of the randomized-benchmarking set (Sec. III, random circuits)
+FIXED_1Q = {
+    "x": SX,
+    "y": SY,
+    "z": SZ,
+    "s": np.diag([1.0, 1.0j]).astype(np.complex128),
+    "t": np.diag([1.0, np.exp(0.25j * np.pi)]).astype(np.complex128),
+}
+
+
 def gate_matrix(op):
     """(qubits, matrix) for a gate op of the shared op-list format."""
     name = op["op"]
     if name in ("rx", "ry", "rz"):
         return [op["q"]], rotation(name[1], op["theta"])
+    if name in FIXED_1Q:
+        return [op["q"]], FIXED_1Q[name]
     if name == "cnot":
         return list(op["q"]), cnot()
     if name == "cz":
         return list(op["q"]), cz()
+    if name == "swap":
+        return list(op["q"]), swap()
     raise ValueError(op)
 
 
 def is_gate(op):
-    return op["op"] in ("rx", "ry", "rz", "cnot", "cz")
+    return op["op"] in ("rx", "ry", "rz", "cnot", "cz", "swap") or op["op"] in FIXED_1Q
 
 
 def is_channel(op):

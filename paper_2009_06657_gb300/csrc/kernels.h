@@ -173,6 +173,16 @@ size_t eigh_cluster_work_bytes(bool fp64);
 cudaError_t launch_trunc_adj_small(const double2* C, const double2* U, const double* lam, int m,
                                    int k, double2* FA, double2* T1, double2* Mcat, cudaStream_t s);
 
+// ---- measurement sampling (Sec. II.D): FP64 CDF of Prob(x) (N doubles in cdf,
+// block sums in bsum[ceil(N / SC_ROWS)], offsets and the total in
+// boff[ceil(N / SC_ROWS) + 1]) and one inverse-CDF search per shot
+constexpr int SC_ROWS = 1024;
+template <typename T>
+cudaError_t launch_sample(const void* V, int64_t N, int c, int ld, double* cdf, double* bsum, double* boff,
+                          const double* u, int shots, int64_t* out, cudaStream_t s);
+// ---- von Neumann entropy (App. A) of m eigenvalues: out[0] = S (bits), out[1] = 2^S
+cudaError_t launch_entropy(const double* lam, int m, double* out, cudaStream_t s);
+
 // ---- readouts (grids never exceed kReadoutMaxBlocks blocks)
 constexpr int kReadoutMaxBlocks = 1024;
 template <typename T>

@@ -80,6 +80,10 @@ struct lr_ctx {
   double* acc = nullptr;       // [0] cumulative discarded, [1] last gap, [2] eig status, [3] compressions
   double* dscratch = nullptr;  // readout partials / small outputs
   size_t dscratch_elems = 0;
+  double* samp = nullptr;      // measurement sampling: CDF, block sums and offsets, uniforms
+  size_t samp_elems = 0;
+  int64_t* samp_out = nullptr;
+  int samp_shots = 0;
   uint64_t* d_xm = nullptr;
   uint64_t* d_zm = nullptr;
   double* d_coeff = nullptr;
@@ -605,8 +609,9 @@ int lr_init_ex(int n, int r, int dtype, int capacity, void* stream, lr_handle* o
   if (!rc) rc = dmalloc(h, (void**)&h->evecs, sizeof(double2) * m * m);
   if (!rc) rc = dmalloc(h, (void**)&h->eo, sizeof(EigOut));
   if (!rc) {
-    size_t wb = eigh_work_bytes(m, dtype == LR_C128);
-    const size_t wc = eigh_cluster_work_bytes(dtype == LR_C128);
+    // FP64 sizes for every dtype: the entropy readout runs the FP64 solvers
+    size_t wb = eigh_work_bytes(m, true);
+    const size_t wc = eigh_cluster_work_bytes(true);
     rc = dmalloc(h, &h->eig_work, wb > wc ? wb : wc);
   }
   if (!rc) rc = dmalloc(h, (void**)&h->acc, sizeof(double) * 8);
@@ -644,6 +649,8 @@ int lr_free(lr_handle h) {
   dfree(h->eig_work);
   dfree((void*&)h->acc);
   dfree((void*&)h->dscratch);
+  dfree((void*&)h->samp);
+  dfree((void*&)h->samp_out);
   dfree((void*&)h->d_xm);
   dfree((void*&)h->d_zm);
   dfree((void*&)h->d_coeff);
@@ -841,6 +848,79 @@ int lr_probs(lr_handle h, void* out_dev) {
     return launch_probs<decltype(t)>(h->V, h->N, h->c, h->cap, out_dev, h->stream);
   }));
   tend(h, LR_K_READOUT, te);
+  return LR_OK;
+}
+
+int lr_sample(lr_handle h, int shots, const double* uniforms, int64_t* out_host) {
+  if (!h || shots < 0 || (shots > 0 && (!uniforms || !out_host))) return LR_EINVAL;
+  for (int s = 0; s < shots; ++s)
+    if (!(uniforms[s] >= 0.0 && uniforms[s] < 1.0)) return LR_EINVAL;
+  if (shots == 0) return LR_OK;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  const int64_t nb = (h->N + SC_ROWS - 1) / SC_ROWS;
+  const size_t need = (size_t)h->N + 2 * (size_t)nb + 1 + (size_t)shots;
+  if (need > h->samp_elems) {
+    dfree((void*&)h->samp);
+    h->samp_elems = 0;
+    rc = dmalloc(h, (void**)&h->samp, sizeof(double) * need);
+    if (rc) return rc;
+    h->samp_elems = need;
+  }
+  if (shots > h->samp_shots) {
+    dfree((void*&)h->samp_out);
+    h->samp_shots = 0;
+    rc = dmalloc(h, (void**)&h->samp_out, sizeof(int64_t) * shots);
+    if (rc) return rc;
+    h->samp_shots = shots;
+  }
+  double* cdf = h->samp;
+  double* bsum = cdf + h->N;
+  double* boff = bsum + nb;  // nb + 1 values
+  double* u = boff + nb + 1;
+  CK(cudaMemcpyAsync(u, uniforms, sizeof(double) * shots, cudaMemcpyHostToDevice, h->stream));
+  const int te = tbeg(h);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_sample<decltype(t)>(h->V, h->N, h->c, h->cap, cdf, bsum, boff, u, shots, h->samp_out, h->stream);
+  }));
+  tend(h, LR_K_READOUT, te);
+  CK(cudaMemcpyAsync(out_host, h->samp_out, sizeof(int64_t) * shots, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LR_OK;
+}
+
+int lr_entropy(lr_handle h, double* out_host) {
+  if (!h || !out_host) return LR_EINVAL;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  const int c = h->c;
+  if (c > 256) {
+    snprintf(g_errmsg, sizeof(g_errmsg), "entropy of %d columns exceeds the eigensolver limit 256", c);
+    return LR_ECAPACITY;
+  }
+  double* outd = h->dscratch;  // S, 2^S
+  if (c == 1) {
+    // one column: rho has rank one (pure up to normalisation)
+    out_host[0] = 0.0;
+    out_host[1] = 1.0;
+    return LR_OK;
+  }
+  // spectrum of V^dag V in FP64 (Theorem 1): the FP64 solvers whatever the dtype
+  const int splits = gram_splits(h->N, c, c);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_gram<decltype(t)>(h->V, h->cap, c, h->V, h->cap, c, h->N, true, h->partials, splits, h->G,
+                                    h->stream);
+  }));
+  if (c <= 64) {
+    CK(launch_eigh<double>(h->G, c, h->eig_work, h->evals, h->evecs, h->eo, c, 0.0, h->stream));
+  } else {
+    CK(launch_eigh_cluster<double>(h->G, c, h->eig_work, h->evals, h->evecs, h->eo, 1, 0.0, 0, h->stream));
+  }
+  CK(launch_entropy(h->evals, c, outd, h->stream));
+  CK(cudaMemcpyAsync(h->h_small, outd, sizeof(double) * 2, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  out_host[0] = h->h_small[0];
+  out_host[1] = h->h_small[1];
   return LR_OK;
 }
 

@@ -17,6 +17,15 @@ from ._ffi import check, lib
 _AXIS = {"x": 0, "y": 1, "z": 2}
 _CNOT = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=np.complex128)
 _CZ = np.diag([1, 1, 1, -1]).astype(np.complex128)
+# SWAP in the basis 2 b(q0) + b(q1)
+_SWAP = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+_FIXED = {
+    "x": np.array([[0, 1], [1, 0]], dtype=np.complex128),
+    "y": np.array([[0, -1j], [1j, 0]], dtype=np.complex128),
+    "z": np.array([[1, 0], [0, -1]], dtype=np.complex128),
+    "s": np.array([[1, 0], [0, 1j]], dtype=np.complex128),
+    "t": np.array([[1, 0], [0, np.exp(0.25j * np.pi)]], dtype=np.complex128),
+}
 _CHAN = {"dep": _ffi.LR_DEPOLARIZING, "ad": _ffi.LR_AMPLITUDE_DAMPING, "bf": _ffi.LR_BIT_FLIP}
 
 
@@ -158,6 +167,20 @@ class LRSim:
         check(lib.lr_z_expect(self.h, _dptr(out)), "lr_z_expect")
         return out[: self.n], out[self.n]
 
+    def sample(self, uniforms):
+        """Basis indices of len(uniforms) measurement shots drawn from Prob(x) by
+        inverse transform with the caller's draws in [0, 1) (lr_sample)."""
+        u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64).reshape(-1))
+        out = np.zeros(len(u), dtype=np.int64)
+        check(lib.lr_sample(self.h, len(u), _dptr(u), out.ctypes.data_as(C.POINTER(C.c_int64))), "lr_sample")
+        return out
+
+    def entropy(self):
+        """(S in bits, effective rank 2^S) of the normalised state (lr_entropy)."""
+        out = np.zeros(2, dtype=np.float64)
+        check(lib.lr_entropy(self.h, _dptr(out)), "lr_entropy")
+        return float(out[0]), float(out[1])
+
     def set_record(self, on=True):
         check(lib.lr_set_record(self.h, 1 if on else 0), "lr_set_record")
 
@@ -224,6 +247,10 @@ def run_ops(sim, ops, r=0, thetas=None, compress=True):
             sim.apply_gate(o["q"], _CNOT)
         elif name == "cz":
             sim.apply_gate(o["q"], _CZ)
+        elif name == "swap":
+            sim.apply_gate(o["q"], _SWAP)
+        elif name in _FIXED:
+            sim.apply_gate([o["q"]], _FIXED[name])
         elif name in _CHAN:
             sim.apply_channel(name, o["q"], o["p"] if "p" in o else o["gamma"])
             if compress:

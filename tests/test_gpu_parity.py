@@ -369,3 +369,24 @@ def test_tensor_core_truncation_matches_oracle(lr, r, nchan, seed):
     assert np.sum(np.abs(out[True][0] - ref.probs())) < bound
     assert np.sum(np.abs(out[True][0] - out[False][0])) < bound
     assert abs(out[True][1]["discarded"] - ref.discarded) < bound
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,r", [(6, 64), (9, 24)], ids=["n6-full", "n9r24"])
+def test_rb_gate_set_with_bit_flip_matches_oracle(lr, dtype, n, r):
+    """The randomized-benchmarking gate set (X, Y, Z, S, T, RX, RY, RZ, SWAP, CZ,
+    CNOT) on adjacent pairs, with depolarizing, amplitude-damping and bit-flip
+    channels drawn per gate: full rank (exact) and truncated."""
+    from workloads import random_rb
+    for s in range(500, 524):
+        ops = random_rb(n, 3, seed=s, noise=("mixed3", 0.01, 0.02, 0.015), qubit_jitter=(0.5, 1.5))
+        ref = O.run_lret(n, ops, r=r)
+        if UNIT[dtype] * _cut_sensitivity(ref) < SENS_BUDGET[dtype] * TOL[dtype]:
+            break
+    else:
+        pytest.skip("no seed with well-separated cuts")
+    sim = lr.LRSim(n, r, dtype=dtype)
+    lr.run_ops(sim, ops, r=r)
+    terms = random_pauli_sum(n, 16, seed=s + 7)
+    _compare(lr, sim, ref, n, terms, TOL[dtype])
+    assert abs(sim.info()["discarded"] - ref.discarded) < TOL[dtype]

@@ -1,0 +1,177 @@
+"""Parity of the measurement-sampling and entropy readouts (lr_sample,
+lr_entropy) with the CPU oracle, through the C ABI.
+
+Entropy (App. A) is a function of the spectrum only, so it is compared directly.
+Its tolerance follows from the state tolerance: with mu the eigenvalues of the
+normalised state, |dS| <= sum_i |d mu_i| (|log2 mu_i| + 1/ln 2) <= (max_i
+|log2 mu_i| + 1/ln 2) ||d mu||_1, and ||d mu||_1 is held to twice the state
+tolerance (FP64 1e-11, FP32 1e-5) plus twice the predicted rounding shift of the
+truncated state at its cuts (unit roundoff times the cut sensitivity).
+
+Shots are integers decided by floating point: a shot is compared exactly with
+the oracle's where the oracle's draw u * total lies farther than a margin from
+every CDF boundary; every shot must be valid (its interval of the CDF contains
+the draw within the tolerance).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import lret as O  # noqa: E402
+from workloads import random_layered  # noqa: E402
+
+TOL = {"c128": 1e-11, "c64": 1e-5}
+UNIT = {"c128": 1.1e-16, "c64": 6e-8}
+
+
+@pytest.fixture(scope="module")
+def lr():
+    import paper_2009_06657_gb300 as m
+    return m
+
+
+def _cut_sensitivity(st):
+    """sum over cuts of lambda_1 lambda_k / (lambda_k - lambda_{k+1}): unit roundoff
+    times this estimates how far rounding can move the truncated state (a cut
+    among zero eigenvalues moves nothing)."""
+    tot = 0.0
+    for e in st.log:
+        k, lam = e["k"], e["lam"]
+        if k >= e["m"] or lam[k - 1] <= 1e-12 * lam[0]:
+            continue
+        gap = lam[k - 1] - lam[k]
+        if gap <= 0:
+            return np.inf
+        tot += lam[0] * lam[k - 1] / gap
+    return tot
+
+
+def _healthy(n, r, depth, noise, seed, dtype, tries=24):
+    """First seed whose predicted truncation error fits the state tolerance."""
+    for s in range(seed, seed + tries):
+        ops = random_layered(n, depth, seed=s, noise=noise, qubit_jitter=(0.5, 1.5))
+        ref = O.run_lret(n, ops, r=r)
+        if UNIT[dtype] * _cut_sensitivity(ref) < 10 * TOL[dtype]:
+            return ops, ref
+    pytest.skip("no seed with well-separated cuts")
+
+
+def _entropy_tol(ref, dtype):
+    # state budget: twice the tolerance plus the predicted rounding shift of the
+    # truncated state at its cuts (unit roundoff x cut sensitivity)
+    G = ref.L.conj().T @ ref.L
+    lam = np.clip(np.linalg.eigvalsh(0.5 * (G + G.conj().T)), 0.0, None)
+    mu = lam / lam.sum()
+    mu = mu[mu > 1e-300]
+    budget = 2.0 * TOL[dtype] + 2.0 * UNIT[dtype] * _cut_sensitivity(ref)
+    return (np.max(np.abs(np.log2(mu))) + 1.0 / np.log(2.0)) * budget
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("case", [(6, 64, 2, ("mixed", 0.02, 0.05), 10),   # full rank, no truncation
+                                  (9, 24, 2, ("dep", 0.01), 20),          # truncated, Jacobi (c <= 64)
+                                  (8, 100, 2, ("ad", 0.03), 30)],         # truncated, cluster (c > 64, K = 2)
+                         ids=["n6-full", "n9r24", "n8r100ad"])
+def test_entropy_matches_oracle(lr, dtype, case):
+    n, r, depth, noise, seed = case
+    ops, ref = _healthy(n, r, depth, noise, seed, dtype)
+    sim = lr.LRSim(n, r, dtype=dtype)
+    lr.run_ops(sim, ops, r=r)
+    assert sim.info()["columns"] == ref.L.shape[1]
+    S, R = sim.entropy()
+    want = ref.entropy()
+    tol = _entropy_tol(ref, dtype)
+    assert abs(S - want) < tol, (S, want, tol)
+    assert abs(R - 2.0 ** want) < 2.0 ** want * np.log(2.0) * tol * 1.01
+    assert sim.entropy() == (S, R)  # deterministic
+    if n == 6 and r == 64:  # full rank: the exact density matrix gives the same entropy
+        assert abs(S - O.entropy_dense(O.run_fdm(n, ops).rho)) < tol
+
+
+def test_entropy_of_pure_state_is_zero(lr):
+    n = 5
+    ops = [o for o in random_layered(n, 2, seed=7, noise=("dep", 0.0)) if O.is_gate(o)]
+    for dtype in ("c128", "c64"):
+        sim = lr.LRSim(n, 8, dtype=dtype)
+        lr.run_ops(sim, ops, r=8)
+        S, R = sim.entropy()
+        assert abs(S) < 1e-12 and abs(R - 1.0) < 1e-12
+
+
+def _valid(shots, probs, u, tol):
+    """Each shot x satisfies CDF(x-1) - tol <= u * total <= CDF(x) + tol and has Prob(x) > 0."""
+    cdf = np.cumsum(probs)
+    tot = cdf[-1]
+    t = u * tot
+    lo = np.where(shots > 0, cdf[np.maximum(shots - 1, 0)], 0.0)
+    hi = cdf[shots]
+    return bool(np.all(lo - tol <= t) and np.all(t <= hi + tol) and np.all(probs[shots] > 0))
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_sampling_matches_oracle(lr, dtype):
+    n, r = 9, 24
+    ops, ref = _healthy(n, r, 2, ("dep", 0.01), 40, dtype)
+    sim = lr.LRSim(n, r, dtype=dtype)
+    lr.run_ops(sim, ops, r=r)
+    rng = np.random.default_rng(11)
+    u = rng.random(4000)
+    got = sim.sample(u)
+    pr = ref.probs()
+    want = O.sample_inverse_cdf(pr, u)
+    budget = 2 * TOL[dtype] + 2 * UNIT[dtype] * _cut_sensitivity(ref)
+    assert _valid(got, pr, u, budget)
+    # exact agreement wherever the draw is clear of every CDF boundary
+    cdf = np.cumsum(pr)
+    t = u * cdf[-1]
+    dist = np.min(np.abs(cdf[None, :] - t[:, None]), axis=1)
+    clear = dist > 2 * budget
+    assert clear.mean() > 0.9
+    assert np.array_equal(got[clear], want[clear])
+    assert np.array_equal(sim.sample(u), got)  # deterministic
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_sampling_uniform_state_closed_form(lr, dtype):
+    # Ry(pi/2) on every qubit: Prob(x) = 2^-n, a draw at the middle of cell k gives k
+    n = 7
+    sim = lr.LRSim(n, 4, dtype=dtype)
+    for q in range(n):
+        sim.apply_rotation("y", q, np.pi / 2)
+    k = np.arange(2 ** n)
+    assert np.array_equal(sim.sample((k + 0.5) / 2 ** n), k)
+
+
+def test_sampling_full_size_against_own_probabilities(lr):
+    # 20 qubits, r = 64, after a few truncations: the shots obey the inverse-CDF rule
+    # on the library's own Prob(x) (lr_probs), summed on the host in FP64
+    import torch
+    n, r = 20, 64
+    ops = random_layered(n, 1, seed=3000, noise=("dep", 5e-4))[:24]
+    sim = lr.LRSim(n, r, dtype="c64")
+    lr.run_ops(sim, ops, r=r)
+    p = sim.probs().double().cpu().numpy()
+    u = np.random.default_rng(3).random(1000)
+    got = sim.sample(u)
+    assert _valid(got, p, u, 1e-9)
+    want = O.sample_inverse_cdf(p, u)
+    cdf = np.cumsum(p)
+    t = u * cdf[-1]
+    idx = np.searchsorted(cdf, t)
+    near = np.minimum(np.abs(cdf[np.minimum(idx, len(cdf) - 1)] - t), np.abs(cdf[np.maximum(idx - 1, 0)] - t))
+    clear = near > 1e-9
+    assert np.array_equal(got[clear], want[clear])
+    torch.cuda.synchronize()
+
+
+def test_sampling_rejects_bad_draws(lr):
+    import ctypes as C
+    sim = lr.LRSim(3, 4, dtype="c64")
+    out = np.zeros(2, dtype=np.int64)
+    for bad in ([0.5, 1.0], [-0.1, 0.2], [np.nan, 0.1]):
+        u = np.array(bad, dtype=np.float64)
+        st = lr._ffi.lib.lr_sample(sim.h, 2, u.ctypes.data_as(C.POINTER(C.c_double)),
+                                   out.ctypes.data_as(C.POINTER(C.c_int64)))
+        assert st == lr._ffi.LR_EINVAL
+    assert len(sim.sample([])) == 0

@@ -334,3 +334,49 @@ def test_sampling_matches_brute_force_definition():
                 break
         assert s == want
         assert p[s] > 0
+
+
+# ---- randomized-benchmarking gate set and bit flip (Sec. III) ----------------
+
+def test_fixed_one_qubit_gate_identities():
+    S, T, X, Y, Z = (O.FIXED_1Q[k] for k in ("s", "t", "x", "y", "z"))
+    assert np.allclose(S @ S, Z, atol=1e-15)
+    assert np.allclose(T @ T, S, atol=1e-15)
+    assert np.allclose(np.linalg.matrix_power(T, 8), np.eye(2), atol=1e-15)
+    assert np.allclose(X @ Y, 1j * Z, atol=1e-15)  # Pauli algebra fixes the signs of Y
+    # S maps <X> to <Y> on |+>: Ry(pi/2)|0> = |+>, then S
+    sv = O.SVState(1)
+    sv.gate([0], O.rotation("Y", np.pi / 2))
+    sv.gate([0], S)
+    assert abs(sv.expect([(1.0, [(0, "Y")])]) - 1.0) < 1e-14
+
+
+def test_swap_is_three_cnots_and_moves_a_flip():
+    C01 = O.cnot()  # control q0, target q1 in the basis 2 b(q0) + b(q1)
+    # CNOT with control q1, target q0 in the same basis
+    C10 = np.zeros((4, 4), dtype=np.complex128)
+    for b0 in range(2):
+        for b1 in range(2):
+            C10[2 * (b0 ^ b1) + b1, 2 * b0 + b1] = 1.0
+    assert np.allclose(C01 @ C10 @ C01, O.swap(), atol=1e-15)
+    st = O.SVState(3)
+    st.gate([0], O.FIXED_1Q["x"])          # |001>: qubit 0 set
+    st.gate([0, 2], O.swap())              # qubit 2 set -> index 4
+    assert abs(st.probs()[4] - 1.0) < 1e-15
+
+
+def test_bit_flip_on_zero_closed_form():
+    p = 0.07
+    st = O.LRETState(2)
+    st.channel(1, O.bit_flip(p))
+    assert np.allclose(st.probs(), [1 - p, 0, p, 0], atol=1e-15)
+
+
+def test_rb_circuit_lret_full_rank_equals_fdm():
+    from workloads import random_rb
+    n = 4
+    ops = random_rb(n, 4, seed=91, noise=("mixed3", 0.02, 0.05, 0.03))
+    names = {o["op"] for o in ops}
+    assert {"swap", "cz", "cnot"} & names and {"x", "s", "t", "rx"} & names and "bf" in names
+    lret, fdm = O.run_lret(n, ops, r=2 ** n), O.run_fdm(n, ops)
+    assert np.max(np.abs(lret.rho() - fdm.rho)) < 1e-12

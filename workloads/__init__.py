@@ -38,6 +38,7 @@ import numpy as np
 __all__ = [
     "random_layered",
     "hea",
+    "random_rb",
     "random_pauli_sum",
     "count_ops",
     "CONFIGS",
@@ -106,6 +107,59 @@ def random_layered(n, depth, seed, noise=("dep", 1e-3), two_qubit="cnot",
             if nz is not None:
                 ops.append(_channel(rng, a, nz, scale))
                 ops.append(_channel(rng, b, nz, scale))
+    return ops
+
+
+RB_ONE_QUBIT = ("x", "y", "z", "s", "t", "rx", "ry", "rz")
+RB_TWO_QUBIT = ("swap", "cz", "cnot")
+
+
+def random_rb(n, depth, seed, noise=("dep", 1e-3), qubit_jitter=None):
+    """Seeded dense random circuit over the randomized-benchmarking gate set
+    (X, Y, Z, S, T, RX, RY, RZ, SWAP, CZ, CNOT): in every layer, walking up the
+    qubits, a two-qubit gate on the adjacent pair (q, q+1) or a one-qubit gate
+    on q, each with probability 1/2 (rotation angles U[0, 2 pi)); a channel
+    follows every gate on each qubit it touches. noise as for random_layered,
+    plus ("mixed3", p_dep, gamma_ad, p_bf) drawing one of the three kinds per gate.
+    """
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    rng = np.random.default_rng(seed)
+    scale = None
+    if qubit_jitter is not None:
+        scale = np.random.default_rng(seed + 7919).uniform(qubit_jitter[0], qubit_jitter[1], size=n)
+
+    def nz_for_gate():
+        if noise is None:
+            return None
+        if noise[0] == "mixed3":
+            k = int(rng.integers(3))
+            return (("dep", noise[1]), ("ad", noise[2]), ("bf", noise[3]))[k]
+        return _noise_for_gate(rng, noise)
+
+    ops = []
+    for _ in range(depth):
+        q = 0
+        while q < n:
+            if q + 1 < n and rng.random() < 0.5:
+                name = RB_TWO_QUBIT[int(rng.integers(len(RB_TWO_QUBIT)))]
+                ops.append({"op": name, "q": [q, q + 1]})
+                nz = nz_for_gate()
+                if nz is not None:
+                    ops.append(_channel(rng, q, nz, scale))
+                    ops.append(_channel(rng, q + 1, nz, scale))
+                q += 2
+            else:
+                name = RB_ONE_QUBIT[int(rng.integers(len(RB_ONE_QUBIT)))]
+                op = {"op": name, "q": q}
+                if name.startswith("r"):
+                    op["theta"] = float(rng.uniform(0.0, 2.0 * np.pi))
+                    op["pid"] = -1
+                ops.append(op)
+                nz = nz_for_gate()
+                if nz is not None:
+                    ops.append(_channel(rng, q, nz, scale))
+                q += 1
     return ops
 
 
