@@ -10,8 +10,10 @@ definitions directly, without blocking or fusion:
 * ``FDMState``  -- full density-matrix evolution, Eq. (1) (Sec. II.A):
   rho <- sum_a p_a K_a rho K_a^dag, gates rho <- G rho G^dag.
 * ``SVState``   -- noiseless statevector, used for the zero-noise pin.
-* ``LRETState`` -- Algorithm 1 (Sec. II.D) with one-qubit Kraus groups
-  (Sec. II.C, M = 1): L <- G L (Eq. 3); L <- [sqrt(p_1) K_1 L, ...] (Eq. 4);
+* ``LRETState`` -- Algorithm 1 (Sec. II.D) with Kraus groups of M one-qubit
+  channels (Sec. II.C, Eq. 7; M = 1 truncates after every channel):
+  L <- G L (Eq. 3), G a dense k-qubit or diagonal unitary as well;
+  L <- [sqrt(p_1) K_1 L, ...] (Eq. 4);
   eigenvalue truncation through the small Gram matrix L^dag L (Sec. II.B,
   Theorem 1 of App. B); readouts Prob(x) (Eq. 9) and Tr(L^dag O L) (Sec. II.D),
   the von Neumann entropy of App. A from the spectrum of L^dag L.
@@ -28,6 +30,11 @@ Conventions (the paper fixes none of them):
   Depolarizing (Sec. III.A.1): {sqrt(1-p) I, sqrt(p/3) X, sqrt(p/3) Y, sqrt(p/3) Z}.
   Amplitude damping (Sec. III.A.3): E0 = [[1,0],[0,sqrt(1-g)]], E1 = [[0,sqrt(g)],[0,0]].
   Bit flip (Sec. III.A.3): {sqrt(1-p) I, sqrt(p) X}.
+* A k-qubit matrix on qubits (q_0, ..., q_{k-1}) is indexed by
+  sum_i b(q_i) 2^(k-1-i): the first listed qubit is the most significant bit.
+  A diagonal gate lists its 2^k diagonal entries in the same order.
+* Kraus groups (Sec. II.C): a truncation follows every M-th channel of the
+  circuit, and the last channels of a circuit get one of their own.
 * Truncation keeps k = min(r, m) columns for a fixed rank r, or, for a
   threshold eps, the smallest k whose eigenvalue sum reaches (1 - eps) of the
   current trace (the crossing eigenvalue is kept). No renormalisation, so
@@ -116,6 +123,7 @@ FIXED_1Q = {
     "z": SZ,
     "s": np.diag([1.0, 1.0j]).astype(np.complex128),
     "t": np.diag([1.0, np.exp(0.25j * np.pi)]).astype(np.complex128),
+    "h": np.array([[1.0, 1.0], [1.0, -1.0]], dtype=np.complex128) / np.sqrt(2.0),
 }
 
 
@@ -132,11 +140,15 @@ def gate_matrix(op):
         return list(op["q"]), cz()
     if name == "swap":
         return list(op["q"]), swap()
+    if name == "unitary":
+        return list(op["q"]), np.asarray(op["U"], dtype=np.complex128)
+    if name == "diag":
+        return list(op["q"]), np.diag(np.asarray(op["d"], dtype=np.complex128))
     raise ValueError(op)
 
 
 def is_gate(op):
-    return op["op"] in ("rx", "ry", "rz", "cnot", "cz", "swap") or op["op"] in FIXED_1Q
+    return op["op"] in ("rx", "ry", "rz", "cnot", "cz", "swap", "unitary", "diag") or op["op"] in FIXED_1Q
 
 
 def is_channel(op):
@@ -164,6 +176,22 @@ def apply_rows(n, A, qubits, M):
     # tensordot puts M's output indices first; move them back into place
     out = np.moveaxis(out, list(range(k)), axes)
     return out.reshape(2 ** n, c)
+
+
+def diag_index(n, qubits):
+    """For every basis index x, sum_i b(q_i) 2^(k-1-i) (first qubit most significant)."""
+    x = np.arange(2 ** n, dtype=np.int64)
+    k = len(qubits)
+    idx = np.zeros(2 ** n, dtype=np.int64)
+    for i, q in enumerate(qubits):
+        idx |= ((x >> q) & 1) << (k - 1 - i)
+    return idx
+
+
+def apply_diag_rows(n, A, qubits, d):
+    """Return (diag(d) on `qubits`) @ A: row x scaled by d[diag_index(x)]."""
+    d = np.asarray(d, dtype=np.complex128)
+    return d[diag_index(n, qubits)][:, None] * A
 
 
 def pauli_string_matrix_apply(n, A, term):
@@ -202,6 +230,11 @@ class FDMState:
     def gate(self, qubits, U):
         self.rho = self._conj_apply(qubits, U)
 
+    def diag(self, qubits, d):
+        # rho <- D rho D^dag: rho[x, y] d[x] conj(d[y])
+        dx = np.asarray(d, dtype=np.complex128)[diag_index(self.n, qubits)]
+        self.rho = dx[:, None] * self.rho * dx.conj()[None, :]
+
     def channel(self, q, kraus):
         acc = np.zeros_like(self.rho)
         for K in kraus:
@@ -227,6 +260,9 @@ class SVState:
 
     def gate(self, qubits, U):
         self.psi = apply_rows(self.n, self.psi, qubits, U)
+
+    def diag(self, qubits, d):
+        self.psi = apply_diag_rows(self.n, self.psi, qubits, d)
 
     def probs(self):
         return np.abs(self.psi[:, 0]) ** 2
@@ -271,6 +307,10 @@ class LRETState:
     # Eq. (3): L <- G L
     def gate(self, qubits, U):
         self.L = apply_rows(self.n, self.L, qubits, U)
+
+    # Eq. (3) with a diagonal G
+    def diag(self, qubits, d):
+        self.L = apply_diag_rows(self.n, self.L, qubits, d)
 
     # Eq. (4): L <- [sqrt(p_1) K_1 L, ..., sqrt(p_A) K_A L]  (alpha-major blocks)
     def channel(self, q, kraus):
@@ -361,19 +401,33 @@ def with_thetas(ops, thetas):
     return out
 
 
-def run_lret(n, ops, r=None, eps=None, compress=True):
-    """Algorithm 1: gate, then per one-qubit channel concatenate and truncate."""
+def _apply_gate_op(st, o):
+    if o["op"] == "diag":
+        st.diag(list(o["q"]), o["d"])
+    else:
+        qs, U = gate_matrix(o)
+        st.gate(qs, U)
+
+
+def run_lret(n, ops, r=None, eps=None, compress=True, group=1):
+    """Algorithm 1: gates (Eq. 3), channels concatenated (Eq. 4), and a
+    truncation after every `group`-th channel (Kraus groups, Sec. II.C) plus one
+    after the circuit's last channels if they have not been truncated yet."""
     st = LRETState(n)
+    pending = 0
     for o in ops:
         if is_gate(o):
-            qs, U = gate_matrix(o)
-            st.gate(qs, U)
+            _apply_gate_op(st, o)
         elif is_channel(o):
             st.channel(o["q"], channel_kraus(o))
-            if compress:
+            pending += 1
+            if compress and pending == group:
                 st.compress(r=r, eps=eps)
+                pending = 0
         else:
             raise ValueError(o)
+    if compress and pending:
+        st.compress(r=r, eps=eps)
     return st
 
 
@@ -381,8 +435,7 @@ def run_fdm(n, ops):
     st = FDMState(n)
     for o in ops:
         if is_gate(o):
-            qs, U = gate_matrix(o)
-            st.gate(qs, U)
+            _apply_gate_op(st, o)
         elif is_channel(o):
             st.channel(o["q"], channel_kraus(o))
     return st
@@ -392,8 +445,7 @@ def run_sv(n, ops):
     st = SVState(n)
     for o in ops:
         if is_gate(o):
-            qs, U = gate_matrix(o)
-            st.gate(qs, U)
+            _apply_gate_op(st, o)
     return st
 
 

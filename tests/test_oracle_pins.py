@@ -380,3 +380,110 @@ def test_rb_circuit_lret_full_rank_equals_fdm():
     assert {"swap", "cz", "cnot"} & names and {"x", "s", "t", "rx"} & names and "bf" in names
     lret, fdm = O.run_lret(n, ops, r=2 ** n), O.run_fdm(n, ops)
     assert np.max(np.abs(lret.rho() - fdm.rho)) < 1e-12
+
+
+# ---- dense k-qubit and diagonal gates, Kraus groups, Grover (Sec. II.C, III.D) --
+
+def _rand_unitary(rng, d):
+    Z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    Q, R = np.linalg.qr(Z)
+    return Q * (np.diag(R) / np.abs(np.diag(R)))[None, :]
+
+
+def test_dense_gate_is_kron_of_its_factors_first_qubit_most_significant():
+    rng = np.random.default_rng(11)
+    n = 5
+    A = rng.normal(size=(2 ** n, 3)) + 1j * rng.normal(size=(2 ** n, 3))
+    qs = [3, 0, 4]
+    F = [_rand_unitary(rng, 2) for _ in qs]
+    seq = A
+    for q, M in zip(qs, F):
+        seq = O.apply_rows(n, seq, [q], M)
+    dense = O.apply_rows(n, A, qs, np.kron(np.kron(F[0], F[1]), F[2]))
+    assert np.max(np.abs(dense - seq)) < 1e-13
+
+
+def test_dense_permutation_moves_basis_state_by_hand():
+    # 3-qubit cyclic shift i -> i + 1 (mod 8) on qubits (q0, q1, q2) = (1, 4, 2):
+    # index i = 4 b(1) + 2 b(4) + b(2)
+    n = 5
+    P = np.zeros((8, 8), dtype=np.complex128)
+    for i in range(8):
+        P[(i + 1) % 8, i] = 1.0
+    # |x> with b(1) = 0, b(4) = 1, b(2) = 1 -> i = 3 -> 4 = (b(1)=1, b(4)=0, b(2)=0)
+    x = (1 << 4) | (1 << 2) | (1 << 0)  # qubit 0 set as a spectator
+    st = O.SVState(n)
+    st.psi[:] = 0
+    st.psi[x, 0] = 1.0
+    st.gate([1, 4, 2], P)
+    y = (1 << 1) | (1 << 0)
+    assert abs(st.probs()[y] - 1.0) < 1e-15
+
+
+def test_diagonal_gate_matches_dense_and_bitwise_definition():
+    rng = np.random.default_rng(12)
+    n = 6
+    qs = [2, 5, 0, 3]
+    d = np.exp(1j * rng.uniform(0, 2 * np.pi, size=16))
+    A = rng.normal(size=(2 ** n, 4)) + 1j * rng.normal(size=(2 ** n, 4))
+    got = O.apply_diag_rows(n, A, qs, d)
+    assert np.max(np.abs(got - O.apply_rows(n, A, qs, np.diag(d)))) < 1e-13
+    for x in range(2 ** n):  # index from the binary string, most significant qubit first
+        bits = format(x, f"0{n}b")[::-1]
+        i = int("".join(bits[q] for q in qs), 2)
+        assert np.max(np.abs(got[x] - d[i] * A[x])) < 1e-14
+
+
+@pytest.mark.parametrize("n", [5, 6, 7])
+@pytest.mark.parametrize("dense", [True, False])
+def test_grover_noiseless_success_closed_form(n, dense):
+    from workloads import grover, grover_good
+    ops, t = grover(n, p=0.0, dense=dense)
+    good = grover_good(n)
+    theta = np.arcsin(np.sqrt(good.sum() / 2 ** n))
+    pg = O.run_sv(n, ops).probs()[good].sum()
+    assert abs(pg - np.sin((2 * t + 1) * theta) ** 2) < 1e-12
+    assert t == int(np.floor(np.pi / 4 * np.sqrt(2 ** n / good.sum())))
+
+
+def test_grover_dense_and_decomposed_iterates_agree_under_noise():
+    from workloads import grover
+    n = 4
+    a, _ = grover(n, p=0.02, dense=True)
+    b, _ = grover(n, p=0.02, dense=False)
+    ra, rb = O.run_fdm(n, a).rho, O.run_fdm(n, b).rho
+    assert np.max(np.abs(ra - rb)) < 1e-13
+
+
+def test_grover_lret_full_rank_equals_fdm():
+    from workloads import grover
+    n = 4
+    ops, _ = grover(n, p=0.03, dense=False)
+    lret, fdm = O.run_lret(n, ops, r=2 ** n), O.run_fdm(n, ops)
+    assert np.max(np.abs(lret.rho() - fdm.rho)) < 1e-12
+
+
+def test_kraus_groups_truncate_after_every_mth_channel():
+    from workloads import random_rb
+    ops = random_rb(4, 3, seed=93, noise=("dep", 0.01))
+    nch = sum(1 for o in ops if O.is_channel(o))
+    for M in (1, 2, 3):
+        st = O.run_lret(4, ops, r=16, group=M)
+        assert len(st.log) == -(-nch // M)
+        assert np.max(np.abs(st.rho() - O.run_fdm(4, ops).rho)) < 1e-12
+
+
+def test_kraus_group_truncation_is_the_best_rank_r_approximation():
+    # from an exact state, one group of M = 2 channels then one truncation keeps
+    # the top-r spectral part of the exact density matrix (Eckart-Young, Sec. II.B)
+    from workloads import random_layered
+    n, r = 4, 5
+    pre = random_layered(n, 2, seed=94, noise=None)
+    ops = pre + [{"op": "dep", "q": 1, "p": 0.2}, {"op": "ad", "q": 3, "gamma": 0.3}]
+    st = O.run_lret(n, ops, r=r, group=2)
+    assert len(st.log) == 1 and st.log[0]["m"] == 4 * 2  # one column, then K = 4 and K = 2
+    rho = O.run_fdm(n, ops).rho
+    w, U = np.linalg.eigh(rho)
+    top = (U[:, -r:] * w[-r:]) @ U[:, -r:].conj().T
+    assert np.max(np.abs(st.rho() - top)) < 1e-12
+    assert abs(st.discarded - w[:-r].sum()) < 1e-12

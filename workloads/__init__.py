@@ -14,6 +14,11 @@ Op list format (a list of dicts, applied in order):
 * ``{"op": "dep", "q": int, "p": float}`` -- one-qubit depolarizing channel.
 * ``{"op": "ad", "q": int, "gamma": float}`` -- one-qubit amplitude damping.
 * ``{"op": "bf", "q": int, "p": float}`` -- one-qubit bit flip.
+* ``{"op": "h", "q": int}`` and the other fixed one-qubit gates x, y, z, s, t.
+* ``{"op": "unitary", "q": [q_0, ..., q_{k-1}], "U": (2^k, 2^k) complex array}``
+  -- a dense k-qubit gate, row/column index sum_i b(q_i) 2^(k-1-i).
+* ``{"op": "diag", "q": [q_0, ..., q_{k-1}], "d": (2^k,) complex array}`` -- a
+  diagonal k-qubit gate, entries in the same index order.
 
 Qubit ``q`` is bit ``q`` of the computational-basis index (little-endian).
 Channels follow the gate they decorate; the low-rank runners truncate after
@@ -30,6 +35,14 @@ are those of the five benchmark configurations):
   (angles N(0, 0.5^2), all differentiable) then a CZ ladder CZ(0,1)...CZ(n-2,n-1).
 * ``random_pauli_sum``: T terms, weight U{1..min(4, n)}, distinct qubits,
   uniform X/Y/Z, coefficients N(0, 1).
+* ``grover``: amplitude amplification of the basis states of Hamming weight
+  <= 2 (Sec. III.D), each Grover iterate one dense n-qubit unitary or a
+  diagonal oracle plus a diffuser; depolarizing noise on every qubit after the
+  initial Hadamards and after every iterate. The iterate's entries are the
+  circuit's definition (a sign per basis state, and the reflection about the
+  uniform superposition), written out here as plain arrays.
+* ``random_dense``: layers of seeded Haar-random dense k-qubit gates on random
+  qubit subsets, each followed by channels on the qubits it touches.
 """
 from __future__ import annotations
 
@@ -40,6 +53,9 @@ __all__ = [
     "hea",
     "random_rb",
     "random_pauli_sum",
+    "grover",
+    "grover_good",
+    "random_dense",
     "count_ops",
     "CONFIGS",
 ]
@@ -193,6 +209,87 @@ def hea(n, layers, seed, noise=("dep", 1e-3), theta_std=0.5, qubit_jitter=None):
     return ops, np.asarray(thetas, dtype=np.float64)
 
 
+def grover_good(n, max_weight=2):
+    """Boolean mask over the 2^n basis states: Hamming weight <= max_weight."""
+    x = np.arange(2 ** n, dtype=np.int64)
+    hw = np.zeros(2 ** n, dtype=np.int64)
+    for q in range(n):
+        hw += (x >> q) & 1
+    return hw <= max_weight
+
+
+def grover(n, iterates=None, p=1e-3, dense=True, max_weight=2):
+    """Amplitude amplification of {x : HW(x) <= max_weight} on n qubits.
+
+    Ops: H on every qubit, then `iterates` Grover iterates (default
+    floor(pi/4 sqrt(1/p_good))). dense=True writes each iterate as one
+    n-qubit "unitary" op on qubits [n-1, ..., 0] (so its index is the basis
+    index x); dense=False writes it as a "diag" sign oracle, H on every qubit, a
+    "diag" reflection about |0...0> (+1 at x = 0, -1 elsewhere) and H on every
+    qubit again. p > 0 puts a depolarizing channel of strength p on every
+    qubit after the Hadamards and after each iterate.
+    Returns (ops, iterates).
+    """
+    good = grover_good(n, max_weight)
+    N = 2 ** n
+    if iterates is None:
+        iterates = int(np.floor(np.pi / 4.0 * np.sqrt(N / good.sum())))
+    sign = np.where(good, -1.0, 1.0).astype(np.complex128)
+    allq = list(range(n - 1, -1, -1))
+    ops = []
+
+    def noise():
+        if p > 0:
+            for q in range(n):
+                ops.append({"op": "dep", "q": q, "p": float(p)})
+
+    for q in range(n):
+        ops.append({"op": "h", "q": q})
+    noise()
+    if dense:
+        # (2|s><s| - I) O with |s> the uniform superposition, O = diag(sign)
+        U = (np.full((N, N), 2.0 / N, dtype=np.complex128) - np.eye(N, dtype=np.complex128)) * sign[None, :]
+    refl0 = -np.ones(N, dtype=np.complex128)
+    refl0[0] = 1.0
+    for _ in range(iterates):
+        if dense:
+            ops.append({"op": "unitary", "q": allq, "U": U})
+        else:
+            ops.append({"op": "diag", "q": allq, "d": sign})
+            for q in range(n):
+                ops.append({"op": "h", "q": q})
+            ops.append({"op": "diag", "q": allq, "d": refl0})
+            for q in range(n):
+                ops.append({"op": "h", "q": q})
+        noise()
+    return ops, iterates
+
+
+def _haar_unitary(rng, d):
+    """Haar-random d x d unitary: QR of a complex Gaussian, phases fixed."""
+    Z = (rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))) / np.sqrt(2.0)
+    Q, R = np.linalg.qr(Z)
+    ph = np.diag(R) / np.abs(np.diag(R))
+    return Q * ph[None, :]
+
+
+def random_dense(n, layers, seed, k_range=(3, 5), noise=("dep", 1e-3)):
+    """Per layer one dense k-qubit gate (k uniform in k_range, distinct random
+    qubits in random order, Haar-random matrix), then a channel on each of its
+    qubits."""
+    rng = np.random.default_rng(seed)
+    ops = []
+    for _ in range(layers):
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        k = min(k, n)
+        qs = [int(q) for q in rng.choice(n, size=k, replace=False)]
+        ops.append({"op": "unitary", "q": qs, "U": _haar_unitary(rng, 2 ** k)})
+        if noise is not None:
+            for q in qs:
+                ops.append(_channel(rng, q, _noise_for_gate(rng, noise)))
+    return ops
+
+
 def random_pauli_sum(n, T, seed, max_weight=4):
     """T random Pauli strings: list of (coeff, [(qubit, 'X'|'Y'|'Z'), ...])."""
     rng = np.random.default_rng(seed)
@@ -208,7 +305,7 @@ def random_pauli_sum(n, T, seed, max_weight=4):
 
 def count_ops(ops):
     """(gates, channels) in an op list."""
-    g = sum(1 for o in ops if o["op"] in ("rx", "ry", "rz", "cnot", "cz"))
+    g = sum(1 for o in ops if o["op"] not in ("dep", "ad", "bf"))
     c = sum(1 for o in ops if o["op"] in ("dep", "ad", "bf"))
     return g, c
 
