@@ -231,8 +231,9 @@ def run_ours(args, rank, world):
     fp64 = bench_fp64(args, layers, dev, stream) if (rank == 0 and not args.no_fp64) else None
     adj = bench_adjoint(dev, stream) if (rank == 0 and not args.no_adjoint) else None
     bat = bench_batch(dev, stream, scale=args.batch_scale) if (rank == 0 and not args.no_batch) else None
+    grv = bench_grover(dev, stream) if (rank == 0 and not args.no_grover) else None
     return dict(ms=ms, g_per=g_per, c_per=c_per, ktimes=ktimes, clk=clk, e2e_s=e2e_s, fp64=fp64, info=info,
-                adjoint=adj, batch=bat, launches=n_launch, readouts=rd)
+                adjoint=adj, batch=bat, launches=n_launch, readouts=rd, grover=grv)
 
 
 def bench_fp64(args, layers, dev, stream):
@@ -336,6 +337,65 @@ def bench_adjoint(dev, stream, reps=2):
     return {"workload": "14-qubit HEA, 6 layers, 168 parameters, r=32, dep p=1e-3, 50 Pauli terms, "
                         "checkpoint every 8 stages", "forward_s": f, "backward_s": b,
             "adjoint_over_forward": b / f, "grad_norm": float(sum(x * x for x in g) ** 0.5)}
+
+
+def bench_grover(dev, stream, reps=3):
+    """Amplitude amplification of the basis states of Hamming weight <= 2 at 13
+    qubits (Sec. III.D's largest size): Hadamards, 7 Grover iterates, a
+    depolarizing channel (p = 1e-3) on every qubit after the Hadamards and after
+    each iterate, each followed by a truncation to rank 41 (0.5 % of full rank),
+    complex64. Dense form: each iterate is one 8192 x 8192 unitary held on the
+    device (lr_apply_gate_device); factorised form: sign oracle and reflection as
+    diagonal gates between two Hadamard layers. CUDA events on the handle's stream."""
+    import numpy as np
+    import torch
+
+    import paper_2009_06657_gb300 as lr
+    from workloads import grover, grover_good
+    n, r = 13, 41
+    ops, t = grover(n, p=1e-3, dense=True)
+    U = torch.tensor(next(o["U"] for o in ops if o["op"] == "unitary"), dtype=torch.complex64, device=dev)
+    ops_dev = [dict(o, U=U) if o["op"] == "unitary" else o for o in ops]
+    ops_fact, _ = grover(n, p=1e-3, dense=False)
+    good = torch.tensor(grover_good(n), device=dev)
+    sim = lr.LRSim(n, r, dtype="c64", stream=stream)
+    probs = torch.empty(1 << n, dtype=torch.float32, device=dev)
+    out = {"workload": "13-qubit Grover / amplitude amplification, HW(x) <= 2, 7 iterates, dep p=1e-3 "
+                       "on every qubit after each layer, r=41 (0.5% of full rank), complex64"}
+    with torch.cuda.stream(stream):
+        for name, seq in (("dense", ops_dev), ("factorised", ops_fact)):
+            ts = []
+            for i in range(reps + 1):
+                sim.reset()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lr.run_ops(sim, seq, r=r)
+                sim.probs(probs)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i > 0:
+                    ts.append(e0.elapsed_time(e1))
+            out[name + "_circuit_ms"] = statistics.median(ts)
+            out[name + "_good_probability"] = float(probs[good].double().sum())
+        # one dense iterate on the final 41-column state: 8 D^2 c real flops
+        c = sim.info()["columns"]
+        D = 1 << n
+        allq = list(range(n - 1, -1, -1))
+        sim.apply_gate(allq, U)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            sim.apply_gate(allq, U)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        out["dense_iterate_columns"] = c
+        out["dense_iterate_ms"] = ms
+        out["dense_iterate_tflops"] = 8.0 * D * D * c / (ms * 1e-3) / 1e12
+        out["dense_iterate_gate_read_gbs"] = D * D * 8 * ((c + 31) // 32) / (ms * 1e-3) / 1e9
+    out["iterates"] = t
+    sim.close()
+    return out
 
 
 def bench_batch(dev, stream, scale=0.05, sample_single=12):
@@ -458,6 +518,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-grover", action="store_true")
     ap.add_argument("--batch-scale", type=float, default=0.05)
     args = ap.parse_args()
     if args.profile_case:
@@ -510,7 +571,7 @@ def main():
         "e2e": {"value": res["g_per"] / res["e2e_s"], "unit": "noisy gate-steps/s",
                 "h2d_bytes_per_step": h2d_bytes(get_layers()[0]), "d2h_bytes_per_step": (1 << N_QUBITS) * 4 + 8},
         "fp64": None, "cpu_baseline": None, "adjoint": res.get("adjoint"), "batch": res.get("batch"),
-        "readouts": res.get("readouts"),
+        "readouts": res.get("readouts"), "grover": res.get("grover"),
     }
     out["gpu_launches"] = res["launches"]  # the library's own launch counter over the timed region
     if res["fp64"]:

@@ -43,7 +43,7 @@ extern "C" {
 #endif
 
 #define LR_OK 0
-#define LR_EINVAL -1     /* bad argument: qubit out of range, nq > 2, n > 30, ... */
+#define LR_EINVAL -1     /* bad argument: qubit out of range, n > 30, ... */
 #define LR_EKRAUS -2     /* || sum_a Kt_a^dag Kt_a - I ||_max > 1e-10 */
 #define LR_ECAPACITY -3  /* columns would exceed the allocated capacity */
 #define LR_ENOMEM -4     /* device allocation failed */
@@ -72,18 +72,48 @@ int lr_free(lr_handle h);
 /* Return to |0...0>, clear the discarded mass, the tape and the queue. */
 int lr_reset(lr_handle h);
 
-/* Queue gate G on nq (1 or 2) qubits, Eq. (3). U is 2^nq x 2^nq complex.
- * dU (nullable) is dG/dtheta for parameter param_id (>= 0 makes the gate
- * differentiable; -1 = fixed). */
+/* Gate G on nq qubits, Eq. (3): V <- G V. U is 2^nq x 2^nq complex, row-major,
+ * indexed by sum_i b(qubits[i]) 2^(nq-1-i) (the first listed qubit is the most
+ * significant bit; for nq = 2 this is 2*b(q0) + b(q1)).
+ * nq = 1 or 2: the gate is queued and fused with a following channel on one of
+ *   its qubits. dU (nullable) is dG/dtheta for parameter param_id (>= 0 makes
+ *   the gate differentiable; -1 = fixed).
+ * 3 <= nq <= LR_MAX_GATE_QUBITS (and nq <= n): a dense multi-qubit unitary
+ *   (Sec. II.C's k-qubit operators; the Grover iterates of Sec. III.D as one
+ *   unitary). Queued work runs first, then the gate runs at once on the
+ *   device in the state's precision; it must be fixed (dU = NULL,
+ *   param_id = -1). Recording keeps a device copy of U for lr_backward.
+ * Errors: LR_EINVAL for repeated or out-of-range qubits or non-finite entries.
+ * U is not checked for unitarity. */
+#define LR_MAX_GATE_QUBITS 13
 int lr_apply_gate(lr_handle h, int nq, const int* qubits, const double* U,
                   const double* dU, int param_id);
+
+/* Dense gate as lr_apply_gate with 3 <= nq <= LR_MAX_GATE_QUBITS, the matrix
+ * given as a caller-owned DEVICE buffer U_dev of 2^nq x 2^nq complex numbers in
+ * the state's precision (float2 pairs for LR_C64, double2 for LR_C128),
+ * row-major, on the handle's device. It is read on the handle's stream and
+ * must stay valid until that work has run; no copy is made (except the tape's
+ * copy while recording). For gates applied many times (Grover iterates) this
+ * skips the host conversion and upload. LR_EINVAL if U_dev is not device memory. */
+int lr_apply_gate_device(lr_handle h, int nq, const int* qubits, const void* U_dev);
+
+/* Diagonal gate on nq (1..n) qubits: row x of V is multiplied by
+ * diag[sum_i b(qubits[i]) 2^(nq-1-i)] (Eq. 3 with a diagonal G, e.g. a phase
+ * oracle). diag holds 2^nq complex entries (interleaved doubles). Queued work
+ * runs first; the gate runs at once, in place. Errors as for lr_apply_gate. */
+int lr_apply_diagonal(lr_handle h, int nq, const int* qubits, const double* diag);
 
 /* Queue R_axis(theta) = exp(-i theta sigma_axis / 2) on qubit q; axis 0/1/2 =
  * X/Y/Z. The derivative is built natively. */
 int lr_apply_rotation(lr_handle h, int axis, int q, double theta, int param_id);
 
 /* Queue a one-qubit channel: K (1..4) Kraus matrices Kt_a (2x2 complex each,
- * probability folded in), Eq. (4). Completeness is checked (LR_EKRAUS). */
+ * probability folded in), Eq. (4). Completeness is checked (LR_EKRAUS).
+ * Channels applied one after another with no lr_compress between them form
+ * one Kraus group of M channels (Sec. II.C, Eq. 7): the columns multiply
+ * (c -> c K_1 K_2 ... K_M) and the next lr_compress truncates the group at
+ * once. LR_ECAPACITY if the columns would exceed the capacity (lr_init_ex). */
 int lr_apply_kraus(lr_handle h, int q, int K, const double* kraus);
 
 /* Kraus sets of the paper's channels with the probability folded in, written

@@ -75,6 +75,8 @@ _SIGS = {
     "lr_free": (C.c_int, [_H]),
     "lr_reset": (C.c_int, [_H]),
     "lr_apply_gate": (C.c_int, [_H, C.c_int, _I, _D, _D, C.c_int]),
+    "lr_apply_diagonal": (C.c_int, [_H, C.c_int, _I, _D]),
+    "lr_apply_gate_device": (C.c_int, [_H, C.c_int, _I, C.c_void_p]),
     "lr_apply_rotation": (C.c_int, [_H, C.c_int, C.c_int, C.c_double, C.c_int]),
     "lr_apply_kraus": (C.c_int, [_H, C.c_int, C.c_int, _D]),
     "lr_kraus_preset": (C.c_int, [C.c_int, C.c_double, _D, _I]),

@@ -44,6 +44,28 @@ template <typename T>
 cudaError_t launch_expand(const void* V, void* W, int64_t N, int c, int ld, const GroupOp& op,
                           cudaStream_t s);
 
+// ---- dense k-qubit gate (3 <= k <= 13): W[base(g) + off[a]][j] = sum_b G[a][b] V[base(g) + off[b]][j]
+// pos = the k target qubits in ascending order; G is D x D row-major (D = 2^k) in the
+// state's precision; off[a] = the target bits of matrix index a placed at their qubits.
+// adjoint = 1 applies G^dag.
+struct DenseOp {
+  int k;
+  int pos[32];
+};
+template <typename T>
+cudaError_t launch_dense(const void* V, void* W, int64_t N, int c, int ld, const DenseOp& op, const void* G,
+                         const uint32_t* off, int adjoint, cudaStream_t s);
+
+// ---- diagonal k-qubit gate: W[x][j] = d[i(x)] V[x][j], i(x) = sum_t b(q[t]) 2^(k-1-t);
+// conj = 1 applies conj(d). V == W allowed.
+struct DiagOp {
+  int k;
+  int q[32];
+};
+template <typename T>
+cudaError_t launch_diag(const void* V, void* W, int64_t N, int c, int ld, const DiagOp& op, const void* d,
+                        int conj, cudaStream_t s);
+
 // ---- adjoint of the expansion: Vbar[x_g][j] = sum_{alpha,a} conj(M[alpha][a][g]) Wbar[x_a][alpha c + j]
 // and grad_partials[block] = 2 Re sum conj(Wbar) (dM V). Returns the grid size used.
 template <typename T>

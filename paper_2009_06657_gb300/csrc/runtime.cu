@@ -6,6 +6,7 @@
 // kernel (Eqs. 3-4); a truncation (Sec. II.B) runs Gram -> eigensolve ->
 // projection on the handle's stream without a host round trip unless the
 // caller asks for a value.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <complex>
@@ -32,9 +33,13 @@ extern "C" int64_t lr_launch_count(void) { return (int64_t)lret::launches_total(
 namespace {
 
 struct Stage {
-  int type = 0;  // 0 = expansion, 1 = truncation
+  int type = 0;  // 0 = expansion, 1 = truncation, 2 = dense k-qubit gate, 3 = diagonal gate
   int c_in = 0, c_out = 0;
   GroupOp op{};
+  DenseOp dop{};
+  DiagOp gop{};
+  void* gmat = nullptr;      // types 2/3: gate matrix / diagonal in the state's precision
+  uint32_t* goff = nullptr;  // type 2: row offsets of the matrix indices
   int param_id = -1;
   int m = 0, k = 0;
   double2* U = nullptr;  // m x m eigenvectors (columns, descending)
@@ -84,6 +89,11 @@ struct lr_ctx {
   size_t samp_elems = 0;
   int64_t* samp_out = nullptr;
   int samp_shots = 0;
+  void* gmat = nullptr;        // dense / diagonal gate operand (state precision)
+  size_t gmat_bytes = 0;
+  uint32_t* goff = nullptr;    // dense gate row offsets
+  size_t goff_elems = 0;
+  int goff_k = 0, goff_q[32] = {0};  // qubit list the offsets were built for
   uint64_t* d_xm = nullptr;
   uint64_t* d_zm = nullptr;
   double* d_coeff = nullptr;
@@ -527,8 +537,45 @@ void clear_tape(lr_ctx* h) {
     dfree(st.ckpt);
     dfree((void*&)st.U);
     dfree((void*&)st.lam);
+    dfree(st.gmat);
+    dfree((void*&)st.goff);
   }
   h->tape.clear();
+}
+
+// Copy `count` interleaved complex doubles to h->gmat in the state's precision
+// (FP32 pairs for LR_C64), growing the buffer as needed.
+int upload_gate_operand(lr_ctx* h, const double* src, size_t count) {
+  const size_t bytes = count * h->esz;
+  if (bytes > h->gmat_bytes) {
+    dfree(h->gmat);
+    h->gmat_bytes = 0;
+    int rc = dmalloc(h, &h->gmat, bytes);
+    if (rc) return rc;
+    h->gmat_bytes = bytes;
+  }
+  CK(cudaStreamSynchronize(h->stream));  // the previous operand may still be in use
+  if (h->dtype == LR_C64) {
+    std::vector<float> tmp(2 * count);
+    for (size_t i = 0; i < 2 * count; ++i) tmp[i] = (float)src[i];
+    CK(cudaMemcpy(h->gmat, tmp.data(), bytes, cudaMemcpyHostToDevice));
+  } else {
+    CK(cudaMemcpy(h->gmat, src, bytes, cudaMemcpyHostToDevice));
+  }
+  return LR_OK;
+}
+
+// Keep a private copy of a gate operand (and the current offsets) for the tape.
+int tape_copy_operand(lr_ctx* h, Stage& st, const void* src, size_t count, int with_off, int D) {
+  int rc = dmalloc(h, &st.gmat, count * h->esz);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(st.gmat, src, count * h->esz, cudaMemcpyDeviceToDevice, h->stream));
+  if (with_off) {
+    rc = dmalloc(h, (void**)&st.goff, sizeof(uint32_t) * D);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(st.goff, h->goff, sizeof(uint32_t) * D, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return LR_OK;
 }
 
 int set_initial_state(lr_ctx* h) {
@@ -550,6 +597,66 @@ int set_initial_state(lr_ctx* h) {
   return LR_OK;
 }
 
+// Dense k-qubit gate, 3 <= k <= LR_MAX_GATE_QUBITS: runs at once (not fused).
+// The operand is either a host matrix of complex doubles (U_host, converted and
+// uploaded here) or a caller-owned device matrix in the state's precision (U_dev).
+int apply_dense(lr_ctx* h, int k, const int* qubits, const double* U_host, const void* U_dev) {
+  const int D = 1 << k;
+  const size_t cnt = (size_t)D * D;
+  if (U_host)
+    for (size_t i = 0; i < 2 * cnt; ++i)
+      if (!std::isfinite(U_host[i])) return LR_EINVAL;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  DenseOp op{};
+  op.k = k;
+  for (int i = 0; i < k; ++i) op.pos[i] = qubits[i];
+  std::sort(op.pos, op.pos + k);
+  if (U_host) {
+    rc = upload_gate_operand(h, U_host, cnt);  // synchronises
+    if (rc) return rc;
+  }
+  // row offsets of the matrix indices; kept while the qubit list repeats
+  bool same = h->goff && h->goff_k == k;
+  for (int i = 0; same && i < k; ++i) same = h->goff_q[i] == qubits[i];
+  if (!same) {
+    std::vector<uint32_t> off(D);
+    for (int a = 0; a < D; ++a) {
+      uint32_t o = 0;
+      for (int i = 0; i < k; ++i) o |= (uint32_t)((a >> (k - 1 - i)) & 1) << qubits[i];
+      off[a] = o;
+    }
+    CK(cudaStreamSynchronize(h->stream));  // a previous gate may still read the table
+    if ((size_t)D > h->goff_elems) {
+      dfree((void*&)h->goff);
+      h->goff_elems = 0;
+      rc = dmalloc(h, (void**)&h->goff, sizeof(uint32_t) * D);
+      if (rc) return rc;
+      h->goff_elems = D;
+    }
+    CK(cudaMemcpy(h->goff, off.data(), sizeof(uint32_t) * D, cudaMemcpyHostToDevice));
+    h->goff_k = k;
+    for (int i = 0; i < k; ++i) h->goff_q[i] = qubits[i];
+  }
+  const void* G = U_host ? h->gmat : U_dev;
+  Stage st;
+  if (h->record) {
+    st.type = 2;
+    st.c_in = st.c_out = h->c;
+    st.dop = op;
+    rc = snapshot(h, st);
+    if (!rc) rc = tape_copy_operand(h, st, G, cnt, 1, D);
+    if (rc) return rc;
+  }
+  const int te = tbeg(h);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_dense<decltype(t)>(h->V, h->W, h->N, h->c, h->cap, op, G, h->goff, 0, h->stream);
+  }));
+  tend(h, LR_K_EXPAND, te);
+  std::swap(h->V, h->W);
+  if (h->record) h->tape.push_back(st);
+  return LR_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -651,6 +758,8 @@ int lr_free(lr_handle h) {
   dfree((void*&)h->dscratch);
   dfree((void*&)h->samp);
   dfree((void*&)h->samp_out);
+  dfree(h->gmat);
+  dfree((void*&)h->goff);
   dfree((void*&)h->d_xm);
   dfree((void*&)h->d_zm);
   dfree((void*&)h->d_coeff);
@@ -675,8 +784,68 @@ int lr_reset(lr_handle h) {
   return set_initial_state(h);
 }
 
+
+int lr_apply_diagonal(lr_handle h, int nq, const int* qubits, const double* diag) {
+  if (!h || !qubits || !diag || nq < 1 || nq > h->n || nq > 30) return LR_EINVAL;
+  for (int i = 0; i < nq; ++i) {
+    if (qubits[i] < 0 || qubits[i] >= h->n) return LR_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (qubits[j] == qubits[i]) return LR_EINVAL;
+  }
+  const size_t cnt = (size_t)1 << nq;
+  for (size_t i = 0; i < 2 * cnt; ++i)
+    if (!std::isfinite(diag[i])) return LR_EINVAL;
+  int rc = flush_all(h);
+  if (rc) return rc;
+  DiagOp op{};
+  op.k = nq;
+  for (int i = 0; i < nq; ++i) op.q[i] = qubits[i];
+  rc = upload_gate_operand(h, diag, cnt);
+  if (rc) return rc;
+  Stage st;
+  if (h->record) {
+    st.type = 3;
+    st.c_in = st.c_out = h->c;
+    st.gop = op;
+    rc = snapshot(h, st);
+    if (!rc) rc = tape_copy_operand(h, st, h->gmat, cnt, 0, 0);
+    if (rc) return rc;
+  }
+  const int te = tbeg(h);
+  CK(by_dtype(h->dtype, [&](auto t) {
+    return launch_diag<decltype(t)>(h->V, h->V, h->N, h->c, h->cap, op, h->gmat, 0, h->stream);
+  }));
+  tend(h, LR_K_EXPAND, te);
+  if (h->record) h->tape.push_back(st);
+  return LR_OK;
+}
+
+int lr_apply_gate_device(lr_handle h, int nq, const int* qubits, const void* U_dev) {
+  if (!h || !qubits || !U_dev || nq < 3 || nq > LR_MAX_GATE_QUBITS || nq > h->n) return LR_EINVAL;
+  for (int i = 0; i < nq; ++i) {
+    if (qubits[i] < 0 || qubits[i] >= h->n) return LR_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (qubits[j] == qubits[i]) return LR_EINVAL;
+  }
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, U_dev) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return LR_EINVAL;
+  }
+  return apply_dense(h, nq, qubits, nullptr, U_dev);
+}
+
 int lr_apply_gate(lr_handle h, int nq, const int* qubits, const double* U, const double* dU, int param_id) {
-  if (!h || !qubits || !U || (nq != 1 && nq != 2)) return LR_EINVAL;
+  if (!h || !qubits || !U || nq < 1 || nq > LR_MAX_GATE_QUBITS || nq > h->n) return LR_EINVAL;
+  if (nq >= 3) {
+    for (int i = 0; i < nq; ++i) {
+      if (qubits[i] < 0 || qubits[i] >= h->n) return LR_EINVAL;
+      for (int j = 0; j < i; ++j)
+        if (qubits[j] == qubits[i]) return LR_EINVAL;
+    }
+    if (param_id >= 0 || dU) return LR_EINVAL;  // dense gates are fixed
+    return apply_dense(h, nq, qubits, U, nullptr);
+  }
   for (int i = 0; i < nq; ++i)
     if (qubits[i] < 0 || qubits[i] >= h->n) return LR_EINVAL;
   if (nq == 2 && qubits[0] == qubits[1]) return LR_EINVAL;
@@ -1046,6 +1215,14 @@ int lr_backward(lr_handle h, int T, const uint64_t* xmask, const uint64_t* zmask
         CK(by_dtype(h->dtype, [&](auto t) {
           return launch_expand<decltype(t)>(in, outp, N, st.c_in, ld, st.op, h->stream);
         }));
+      } else if (st.type == 2) {
+        CK(by_dtype(h->dtype, [&](auto t) {
+          return launch_dense<decltype(t)>(in, outp, N, st.c_in, ld, st.dop, st.gmat, st.goff, 0, h->stream);
+        }));
+      } else if (st.type == 3) {
+        CK(by_dtype(h->dtype, [&](auto t) {
+          return launch_diag<decltype(t)>(in, outp, N, st.c_in, ld, st.gop, st.gmat, 0, h->stream);
+        }));
       } else {
         CK(by_dtype(h->dtype, [&](auto t) {
           return launch_rowmat<decltype(t)>(in, ld, st.m, st.U, st.m, nullptr, 0, 0, nullptr, 0, outp, ld, st.k,
@@ -1067,6 +1244,15 @@ int lr_backward(lr_handle h, int T, const uint64_t* xmask, const uint64_t* zmask
         }));
         if (st.op.has_grad && st.param_id >= 0)
           CK(launch_sum(h->bpart, nb, h->bgrad + st.param_id, 1, h->stream));
+      } else if (st.type == 2) {
+        // Vbar_in = G^dag Vbar_out
+        CK(by_dtype(h->dtype, [&](auto t) {
+          return launch_dense<decltype(t)>(vbar, vbin, N, st.c_in, ld, st.dop, st.gmat, st.goff, 1, h->stream);
+        }));
+      } else if (st.type == 3) {
+        CK(by_dtype(h->dtype, [&](auto t) {
+          return launch_diag<decltype(t)>(vbar, vbin, N, st.c_in, ld, st.gop, st.gmat, 1, h->stream);
+        }));
       } else {
         const int m = st.m, k = st.k;
         const int splits = gram_splits(N, m, k);

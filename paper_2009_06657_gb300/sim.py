@@ -25,6 +25,7 @@ _FIXED = {
     "z": np.array([[1, 0], [0, -1]], dtype=np.complex128),
     "s": np.array([[1, 0], [0, 1j]], dtype=np.complex128),
     "t": np.array([[1, 0], [0, np.exp(0.25j * np.pi)]], dtype=np.complex128),
+    "h": np.array([[1, 1], [1, -1]], dtype=np.complex128) / np.sqrt(2.0),
 }
 _CHAN = {"dep": _ffi.LR_DEPOLARIZING, "ad": _ffi.LR_AMPLITUDE_DAMPING, "bf": _ffi.LR_BIT_FLIP}
 
@@ -100,10 +101,26 @@ class LRSim:
 
     def apply_gate(self, qubits, U, dU=None, param_id=-1):
         qs = (C.c_int * len(qubits))(*[int(q) for q in qubits])
+        if isinstance(U, torch.Tensor) and U.is_cuda:
+            # dense gate from a device matrix in the state's precision (lr_apply_gate_device)
+            want = torch.complex64 if self.dtype == _ffi.LR_C64 else torch.complex128
+            if U.dtype != want or not U.is_contiguous() or U.shape != (1 << len(qubits), 1 << len(qubits)):
+                raise ValueError(f"device gate must be a contiguous {want} matrix of side 2^k")
+            check(lib.lr_apply_gate_device(self.h, len(qubits), qs, C.c_void_p(U.data_ptr())),
+                  "lr_apply_gate_device")
+            return
         Uf = _cplx_flat(U)
         dUf = _cplx_flat(dU) if dU is not None else None
         check(lib.lr_apply_gate(self.h, len(qubits), qs, _dptr(Uf),
                                 _dptr(dUf) if dUf is not None else None, int(param_id)), "lr_apply_gate")
+
+    def apply_diagonal(self, qubits, d):
+        """Diagonal gate: row x scaled by d[sum_i b(q_i) 2^(k-1-i)] (lr_apply_diagonal)."""
+        qs = (C.c_int * len(qubits))(*[int(q) for q in qubits])
+        df = _cplx_flat(np.asarray(d).reshape(-1))
+        if df.size != 2 << len(qubits):
+            raise ValueError("diagonal needs 2^k entries")
+        check(lib.lr_apply_diagonal(self.h, len(qubits), qs, _dptr(df)), "lr_apply_diagonal")
 
     def apply_rotation(self, axis, q, theta, param_id=-1):
         check(lib.lr_apply_rotation(self.h, _AXIS[axis.lower()], int(q), float(theta), int(param_id)),
@@ -235,8 +252,10 @@ def is_gate(op):
     return op["op"] in ("rx", "ry", "rz", "cnot", "cz")
 
 
-def run_ops(sim, ops, r=0, thetas=None, compress=True):
-    """Apply an op list; truncate after every channel (one-qubit Kraus groups)."""
+def run_ops(sim, ops, r=0, thetas=None, compress=True, group=1):
+    """Apply an op list. A truncation follows every `group`-th channel (Kraus
+    groups of M = group channels) and the circuit's last untruncated channels."""
+    pending = 0
     for o in ops:
         name = o["op"]
         if name in ("rx", "ry", "rz"):
@@ -251,12 +270,20 @@ def run_ops(sim, ops, r=0, thetas=None, compress=True):
             sim.apply_gate(o["q"], _SWAP)
         elif name in _FIXED:
             sim.apply_gate([o["q"]], _FIXED[name])
+        elif name == "unitary":
+            sim.apply_gate(list(o["q"]), o["U"])
+        elif name == "diag":
+            sim.apply_diagonal(list(o["q"]), o["d"])
         elif name in _CHAN:
             sim.apply_channel(name, o["q"], o["p"] if "p" in o else o["gamma"])
-            if compress:
+            pending += 1
+            if compress and pending == group:
                 sim.compress(r)
+                pending = 0
         else:
             raise ValueError(f"unknown op {name!r}")
+    if compress and pending:
+        sim.compress(r)
     return sim
 
 

@@ -218,7 +218,7 @@ def grover_good(n, max_weight=2):
     return hw <= max_weight
 
 
-def grover(n, iterates=None, p=1e-3, dense=True, max_weight=2):
+def grover(n, iterates=None, p=1e-3, dense=True, max_weight=2, qubit_jitter=None, seed=0):
     """Amplitude amplification of {x : HW(x) <= max_weight} on n qubits.
 
     Ops: H on every qubit, then `iterates` Grover iterates (default
@@ -227,7 +227,8 @@ def grover(n, iterates=None, p=1e-3, dense=True, max_weight=2):
     index x); dense=False writes it as a "diag" sign oracle, H on every qubit, a
     "diag" reflection about |0...0> (+1 at x = 0, -1 elsewhere) and H on every
     qubit again. p > 0 puts a depolarizing channel of strength p on every
-    qubit after the Hadamards and after each iterate.
+    qubit after the Hadamards and after each iterate; qubit_jitter = (lo, hi)
+    scales qubit q's strength by a seeded U[lo, hi) factor.
     Returns (ops, iterates).
     """
     good = grover_good(n, max_weight)
@@ -238,10 +239,14 @@ def grover(n, iterates=None, p=1e-3, dense=True, max_weight=2):
     allq = list(range(n - 1, -1, -1))
     ops = []
 
+    scale = np.ones(n)
+    if qubit_jitter is not None:
+        scale = np.random.default_rng(seed + 7919).uniform(qubit_jitter[0], qubit_jitter[1], size=n)
+
     def noise():
         if p > 0:
             for q in range(n):
-                ops.append({"op": "dep", "q": q, "p": float(p)})
+                ops.append({"op": "dep", "q": q, "p": float(p * scale[q])})
 
     for q in range(n):
         ops.append({"op": "h", "q": q})
