@@ -958,10 +958,12 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     for (int q = 0; q < 6; ++q) out->cycles[q] = t_ph[q];
 #ifdef LRET_EIG_PROFILE
     for (int q = 0; q < 6; ++q) out->cycles[q] = sp[q];
+#if LRET_EIG_PROFILE != 2
     out->cycles[2] = sh.gdbg[0];  // x and its updates
     out->cycles[3] = sh.gdbg[1];  // first group barrier
     out->cycles[4] = sh.gdbg[2];  // norms and scalars
     out->cycles[5] = sh.gdbg[3];  // v, store
+#endif
 #endif
   }
 }

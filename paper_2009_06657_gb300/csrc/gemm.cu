@@ -380,6 +380,30 @@ __global__ void k_build_proj(const double2* __restrict__ U, int c, int K, int k,
   D[e] = acc;
 }
 
+// C (M x N) = op(A) B with op(A) = A (M x K, row stride lda) or A^dag (A stored K x M).
+// Small FP64 products of the deferred pair projection; one thread per output.
+__global__ void k_zgemm_small(const double2* __restrict__ A, int lda, int adj, const double2* __restrict__ B, int ldb,
+                              double2* __restrict__ C, int ldc, int M, int N, int K) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * N) return;
+  const int i = e / N, j = e % N;
+  double2 acc = make_double2(0, 0);
+  if (adj) {
+    for (int l = 0; l < K; ++l) cfmac(acc, A[(int64_t)l * lda + i], B[(int64_t)l * ldb + j]);
+  } else {
+    for (int l = 0; l < K; ++l) cfma(acc, A[(int64_t)i * lda + l], B[(int64_t)l * ldb + j]);
+  }
+  C[(int64_t)i * ldc + j] = acc;
+}
+
+cudaError_t launch_zgemm_small(const double2* A, int lda, int adj, const double2* B, int ldb, double2* C, int ldc,
+                               int M, int N, int K, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  k_zgemm_small<<<(M * N + 127) / 128, 128, 0, s>>>(A, lda, adj, B, ldb, C, ldc, M, N, K);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_assemble_gram(const double2* S, int c, int K, const PairQ& q, double2* Gp, cudaStream_t s) {
   const int m = K * c;
   k_assemble_gram<<<(m * m + 255) / 256, 256, 0, s>>>(S, c, K, q, Gp);

@@ -105,6 +105,9 @@ struct PairQ {
 };
 // G' (K c x K c) from the pair Gram S (2c x 2c)
 cudaError_t launch_assemble_gram(const double2* S, int c, int K, const PairQ& q, double2* Gp, cudaStream_t s);
+// C (M x N) = op(A) B, op(A) = A (adj = 0, A is M x K) or A^dag (adj = 1, A is K x M); FP64
+cudaError_t launch_zgemm_small(const double2* A, int lda, int adj, const double2* B, int ldb, double2* C, int ldc,
+                               int M, int N, int K, cudaStream_t s);
 // D (2c x 2k) = pair-projection matrix from the leading k eigenvectors U (m x m)
 cudaError_t launch_build_proj(const double2* U, int c, int K, int k, const PairQ& q, double2* D, cudaStream_t s);
 

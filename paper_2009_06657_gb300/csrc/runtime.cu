@@ -74,6 +74,15 @@ struct lr_ctx {
   float* projB = nullptr;    // pre-split projection operand for the tensor-core projection
   int use_tc = 1;
   double2* D = nullptr;   // pair projection (2c x 2k)
+  // deferred pair projection: the state is [V_0 V_1] C on qubit pend_q, V holding
+  // pend_cm materialised columns and h->c the state's columns; S holds the pair
+  // Gram of the materialised V on pend_q
+  bool pend = false;
+  int pend_q = 0, pend_cm = 0;
+  double2* pend_C = nullptr;   // 2 pend_cm x 2 c (row stride 2 c)
+  double2* pend_C2 = nullptr;  // product scratch
+  double2* S2 = nullptr;       // pair Gram of the deferred state (2c x 2c)
+  double2* Ztmp = nullptr;     // C^dag S
   // workspaces
   double2* partials = nullptr;
   size_t partials_elems = 0;
@@ -275,8 +284,37 @@ int snapshot(lr_ctx* h, Stage& st) {
   return LR_OK;
 }
 
+// V <- [V_0 V_1] D on qubit q (D: 2c x 2k, row stride 2k), into W, then swap.
+int run_pair_proj(lr_ctx* h, const double2* D, int c, int k, int q) {
+  const int64_t N2 = h->N / 2;
+  const int ld = h->cap;
+  const int te = tbeg(h);
+  if (h->dtype == LR_C64 && h->use_tc && proj_pair_tc_supported(c, k, N2)) {
+    CK(launch_proj_pair_tc(h->V, ld, c, k, q, N2, D, h->projB, h->W, h->tc_status, h->stream));
+  } else {
+    CK(by_dtype(h->dtype, [&](auto t) {
+      return launch_rowmat<decltype(t)>(h->V, ld, 2 * c, D, 2 * k, nullptr, 0, 0, nullptr, 0, h->W, ld, 2 * k,
+                                        N2, h->stream, q, c, k);
+    }));
+  }
+  tend(h, LR_K_PROJECT, te);
+  std::swap(h->V, h->W);
+  return LR_OK;
+}
+
+// Apply a deferred pair projection, if any, so that V holds the state.
+int materialize(lr_ctx* h) {
+  if (!h->pend) return LR_OK;
+  h->pend = false;
+  return run_pair_proj(h, h->pend_C, h->pend_cm, h->c, h->pend_q);
+}
+
 // Run one expansion stage V -> W, swap. Queue flags are cleared by the caller.
 int run_expand(lr_ctx* h, bool use_gate, bool use_chan) {
+  {
+    int rc = materialize(h);
+    if (rc) return rc;
+  }
   GroupOp op;
   int pid;
   build_op(h, use_gate, use_chan, &op, &pid);
@@ -317,6 +355,10 @@ int flush_gate(lr_ctx* h) {
 }
 
 int flush_all(lr_ctx* h) {
+  {
+    int rc = materialize(h);
+    if (rc) return rc;
+  }
   if (h->has_chan) {
     int rc = run_expand(h, h->has_gate, true);
     if (rc) return rc;
@@ -436,34 +478,57 @@ int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
           for (int a = 0; a < 2; ++a) acc += std::conj(M[al][a * 2 + b]) * M[be][a * 2 + bp];
           put(pq.Q[al][be][b][bp], acc);
         }
-  const int splits = gram_splits(N2, 2 * c, 2 * c);
-  int te = tbeg(h);
-  if (h->dtype == LR_C64 && h->use_tc && gram_pair_tc_supported(c, N2)) {
-    const int max_splits = (int)(h->partials_elems / ((size_t)4 * c * c));
-    CK(launch_gram_pair_tc(h->V, ld, c, q, N2, h->partials, max_splits, h->S, h->tc_status, h->stream));
-  } else {
-    CK(by_dtype(h->dtype, [&](auto t) {
-      return launch_gram<decltype(t)>(h->V, ld, 2 * c, h->V, ld, 2 * c, N2, true, h->partials, splits, h->S,
-                                      h->stream, q, c);
-    }));
+  // A truncation on the qubit of a deferred projection continues it: with the
+  // state [V_0 V_1] C, its pair Gram is C^dag S C (S the pair Gram of V), and the
+  // new projection composes, C <- C D. Otherwise the deferred one is applied first.
+  const bool fuse = h->pend && h->pend_q == q;
+  if (h->pend && !fuse) {
+    int rc = materialize(h);
+    if (rc) return rc;
   }
-  CK(launch_assemble_gram(h->S, c, K, pq, h->G, h->stream));
+  if (!h->pend_C) {
+    const size_t big = sizeof(double2) * 512 * 512;
+    int rc = dmalloc(h, (void**)&h->pend_C, big);
+    if (!rc) rc = dmalloc(h, (void**)&h->pend_C2, big);
+    if (!rc) rc = dmalloc(h, (void**)&h->S2, big);
+    if (!rc) rc = dmalloc(h, (void**)&h->Ztmp, big);
+    if (rc) return rc;
+  }
+  const int cm = fuse ? h->pend_cm : c;
+  int te = tbeg(h);
+  if (fuse) {
+    CK(launch_zgemm_small(h->pend_C, 2 * c, 1, h->S, 2 * cm, h->Ztmp, 2 * cm, 2 * c, 2 * cm, 2 * cm, h->stream));
+    CK(launch_zgemm_small(h->Ztmp, 2 * cm, 0, h->pend_C, 2 * c, h->S2, 2 * c, 2 * c, 2 * c, 2 * cm, h->stream));
+    CK(launch_assemble_gram(h->S2, c, K, pq, h->G, h->stream));
+  } else {
+    const int splits = gram_splits(N2, 2 * c, 2 * c);
+    if (h->dtype == LR_C64 && h->use_tc && gram_pair_tc_supported(c, N2)) {
+      const int max_splits = (int)(h->partials_elems / ((size_t)4 * c * c));
+      CK(launch_gram_pair_tc(h->V, ld, c, q, N2, h->partials, max_splits, h->S, h->tc_status, h->stream));
+    } else {
+      CK(by_dtype(h->dtype, [&](auto t) {
+        return launch_gram<decltype(t)>(h->V, ld, 2 * c, h->V, ld, 2 * c, N2, true, h->partials, splits, h->S,
+                                        h->stream, q, c);
+      }));
+    }
+    CK(launch_assemble_gram(h->S, c, K, pq, h->G, h->stream));
+  }
   tend(h, LR_K_GRAM, te);
   int k;
   int rc = run_eigh(h, m, r_eff, eps, &k);
   if (rc) return rc;
   te = tbeg(h);
   CK(launch_build_proj(h->evecs, c, K, k, pq, h->D, h->stream));
-  if (h->dtype == LR_C64 && h->use_tc && proj_pair_tc_supported(c, k, N2)) {
-    CK(launch_proj_pair_tc(h->V, ld, c, k, q, N2, h->D, h->projB, h->W, h->tc_status, h->stream));
+  if (fuse) {
+    CK(launch_zgemm_small(h->pend_C, 2 * c, 0, h->D, 2 * k, h->pend_C2, 2 * k, 2 * cm, 2 * k, 2 * c, h->stream));
+    std::swap(h->pend_C, h->pend_C2);
   } else {
-    CK(by_dtype(h->dtype, [&](auto t) {
-      return launch_rowmat<decltype(t)>(h->V, ld, 2 * c, h->D, 2 * k, nullptr, 0, 0, nullptr, 0, h->W, ld, 2 * k,
-                                        N2, h->stream, q, c, k);
-    }));
+    CK(cudaMemcpyAsync(h->pend_C, h->D, sizeof(double2) * 4 * c * k, cudaMemcpyDeviceToDevice, h->stream));
+    h->pend_cm = c;
+    h->pend_q = q;
   }
   tend(h, LR_K_PROJECT, te);
-  std::swap(h->V, h->W);
+  h->pend = true;  // the projection itself runs when the state is next needed
   h->c = k;
   h->ncomp++;
   h->has_gate = false;
@@ -592,6 +657,7 @@ int set_initial_state(lr_ctx* h) {
   CK(cudaStreamSynchronize(h->stream));
   h->c = 1;
   h->has_gate = h->has_chan = false;
+  h->pend = false;
   h->ncomp = 0;
   clear_tape(h);
   return LR_OK;
@@ -750,6 +816,10 @@ int lr_free(lr_handle h) {
   dfree((void*&)h->tc_status);
   dfree((void*&)h->projB);
   dfree((void*&)h->D);
+  dfree((void*&)h->pend_C);
+  dfree((void*&)h->pend_C2);
+  dfree((void*&)h->S2);
+  dfree((void*&)h->Ztmp);
   dfree((void*&)h->evals);
   dfree((void*&)h->evecs);
   dfree((void*&)h->eo);
@@ -857,7 +927,10 @@ int lr_apply_gate(lr_handle h, int nq, const int* qubits, const double* U, const
     dUc[i] = dU ? zc(dU[2 * i], dU[2 * i + 1]) : zc(0);
   }
   if (check_unitary_like(Uc, d)) return LR_EINVAL;
-  int rc = flush_all(h);  // a queued channel or gate runs first
+  // a queued channel or gate runs first; a deferred projection stays deferred for a
+  // one-qubit gate on its qubit (the next truncation there can continue it)
+  const bool keep = h->pend && !h->has_gate && !h->has_chan && nq == 1 && qubits[0] == h->pend_q;
+  int rc = keep ? LR_OK : flush_all(h);
   if (rc) return rc;
   h->has_gate = true;
   h->gate_nq = nq;

@@ -390,3 +390,55 @@ def test_rb_gate_set_with_bit_flip_matches_oracle(lr, dtype, n, r):
     terms = random_pauli_sum(n, 16, seed=s + 7)
     _compare(lr, sim, ref, n, terms, TOL[dtype])
     assert abs(sim.info()["discarded"] - ref.discarded) < TOL[dtype]
+
+
+# ---- deferred pair projection (consecutive truncations on one qubit) ---------
+
+def _same_qubit_runs(n, seed, per_qubit=3):
+    """Per qubit `per_qubit` (rotation, channel) pairs in a row, then a CNOT
+    matching; per-qubit noise strengths jittered to avoid exact ties."""
+    rng = np.random.default_rng(seed)
+    scale = rng.uniform(0.5, 1.5, size=n)
+    ops = []
+    for q in range(n):
+        for t in range(per_qubit):
+            ops.append({"op": ("ry", "rz", "rx")[t % 3], "q": q, "theta": float(rng.uniform(0, 2 * np.pi)),
+                        "pid": -1})
+            if t % 2 == 0:
+                ops.append({"op": "dep", "q": q, "p": 0.02 * scale[q]})
+            else:
+                ops.append({"op": "ad", "q": q, "gamma": 0.03 * scale[q]})
+    perm = rng.permutation(n)
+    for i in range(0, n - 1, 2):
+        ops.append({"op": "cnot", "q": [int(perm[i]), int(perm[i + 1])]})
+        ops.append({"op": "dep", "q": int(perm[i]), "p": 0.01 * scale[perm[i]]})
+    return ops
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_deferred_projection_matches_oracle_and_eager_projection(lr, dtype):
+    """Truncations in a row on one qubit continue one deferred projection (pair Gram
+    C^dag S C, composed coefficients); the result equals the oracle and the same
+    run with the state materialised after every truncation."""
+    n, r = 9, 12
+    for s in range(7000, 7024):
+        ops = _same_qubit_runs(n, s)
+        ref = O.run_lret(n, ops, r=r)
+        if UNIT[dtype] * _cut_sensitivity(ref) < SENS_BUDGET[dtype] * TOL[dtype]:
+            break
+    else:
+        pytest.skip("no seed with well-separated cuts")
+    sim = lr.LRSim(n, r, dtype=dtype)
+    lr.run_ops(sim, ops, r=r)
+    tol = TOL[dtype] + 2 * UNIT[dtype] * _cut_sensitivity(ref)
+    _compare(lr, sim, ref, n, random_pauli_sum(n, 12, seed=s + 1), tol)
+    assert abs(sim.info()["discarded"] - ref.discarded) < tol
+    # eager: read the state's trace after every truncation (materialises it)
+    sim2 = lr.LRSim(n, r, dtype=dtype)
+    for o in ops:
+        lr.run_ops(sim2, [o], r=r)
+        if O.is_channel(o):
+            sim2.z_expect()
+    p1 = sim.probs().double().cpu().numpy()
+    p2 = sim2.probs().double().cpu().numpy()
+    assert np.sum(np.abs(p1 - p2)) < tol
