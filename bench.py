@@ -461,7 +461,8 @@ def algorithmic():
         # expansion for two-qubit gates (gate only, K = 1): read and write V
         "expand": {"flop": None, "bytes": 2 * N * r * esz},
         "readout": {"flop": None, "bytes": N * r * esz + N * 4},
-        "pauli": {"flop": None, "bytes": 2 * N * r * esz * N_TERMS},
+        # <H>: one pass over V per group of 4 terms, reading each row and its 4 partner rows
+        "pauli": {"flop": None, "bytes": -(-N_TERMS // 4) * 5 * N * r * esz},
     }
 
 
@@ -506,8 +507,38 @@ def profile_case(n):
     sim.close()
 
 
+def profile_readouts(n):
+    """A short run for profilers of the kernels beyond the truncation: one dense
+    13-qubit Grover iterate (8192 x 8192 unitary on 41 columns), then on an n-qubit
+    state of the benchmark family (r = 64): the grouped <H> readout of 64 Pauli
+    terms, 1000 measurement shots and the entropy."""
+    import numpy as np
+    import torch
+
+    import paper_2009_06657_gb300 as lr
+    from workloads import grover, random_layered, random_pauli_sum
+    ops, _ = grover(13, p=1e-3, dense=True)
+    U = torch.tensor(next(o["U"] for o in ops if o["op"] == "unitary"), dtype=torch.complex64, device="cuda")
+    g = lr.LRSim(13, 41, dtype="c64")
+    lr.run_ops(g, [dict(o, U=U) if o["op"] == "unitary" else o for o in ops[:40]], r=41)
+    g.apply_gate(list(range(12, -1, -1)), U)
+    torch.cuda.synchronize()
+    sim = lr.LRSim(n, RANK, dtype="c64")
+    lr.run_ops(sim, random_layered(n, 1, seed=SEED, noise=("dep", P_DEP))[:12], r=RANK)
+    terms = random_pauli_sum(n, N_TERMS, seed=SEED + 1)
+    val = sim.expect(terms)
+    shots = sim.sample(np.random.default_rng(SEED + 2).random(1000))
+    S = sim.entropy()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_readouts": n, "expect": val, "shots": int(len(shots)), "entropy": S[0]}))
+    g.close()
+    sim.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-readouts", type=int, default=0,
+                    help="run only the dense-gate and readout kernels on an n-qubit state for profilers and exit")
     ap.add_argument("--profile-case", type=int, default=0,
                     help="run only a short n-qubit case for profilers (no timing) and exit")
     ap.add_argument("--gpus", type=int, default=1)
@@ -521,6 +552,9 @@ def main():
     ap.add_argument("--no-grover", action="store_true")
     ap.add_argument("--batch-scale", type=float, default=0.05)
     args = ap.parse_args()
+    if args.profile_readouts:
+        profile_readouts(args.profile_readouts)
+        return
     if args.profile_case:
         profile_case(args.profile_case)
         return

@@ -304,6 +304,9 @@ int lr_batch_free(lr_batch_handle b);
 #define LR_K_PROJECT 3  /* V <- V' U_r */
 #define LR_K_READOUT 4  /* Prob(x) */
 #define LR_K_PAULI 5    /* Pauli expectations */
+#define LR_K_SMALL 6    /* small dense products of a truncation: Gram assembly from the
+                           pair Gram, pair projection coefficients, deferred-projection
+                           products */
 #define LR_NKCLASS 8
 
 /* Bracket every forward kernel launch with CUDA events on the handle's stream

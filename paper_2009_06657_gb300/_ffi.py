@@ -26,7 +26,7 @@ LR_DEPOLARIZING = 0
 LR_AMPLITUDE_DAMPING = 1
 LR_BIT_FLIP = 2
 LR_STATIC_MAX_TERMS = 256
-KCLASSES = ["expand", "gram", "eigh", "project", "readout", "pauli"]
+KCLASSES = ["expand", "gram", "eigh", "project", "readout", "pauli", "small"]
 LR_NKCLASS = 8
 
 

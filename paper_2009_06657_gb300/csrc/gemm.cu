@@ -381,25 +381,46 @@ __global__ void k_build_proj(const double2* __restrict__ U, int c, int K, int k,
 }
 
 // C (M x N) = op(A) B with op(A) = A (M x K, row stride lda) or A^dag (A stored K x M).
-// Small FP64 products of the deferred pair projection; one thread per output.
-__global__ void k_zgemm_small(const double2* __restrict__ A, int lda, int adj, const double2* __restrict__ B, int ldb,
-                              double2* __restrict__ C, int ldc, int M, int N, int K) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= M * N) return;
-  const int i = e / N, j = e % N;
-  double2 acc = make_double2(0, 0);
-  if (adj) {
-    for (int l = 0; l < K; ++l) cfmac(acc, A[(int64_t)l * lda + i], B[(int64_t)l * ldb + j]);
-  } else {
-    for (int l = 0; l < K; ++l) cfma(acc, A[(int64_t)i * lda + l], B[(int64_t)l * ldb + j]);
+// Small products of the deferred pair projection (M, N, K <= 512) in FP64 (the
+// composed coefficients feed every later truncation on the qubit, so their rounding
+// accumulates; FP32 products measurably loosened a 480-truncation run). 16 x 16
+// output tiles, K staged 16 at a time in shared memory.
+constexpr int ZT = 16;
+template <typename TC>
+__global__ void __launch_bounds__(ZT * ZT) k_zgemm_small(const double2* __restrict__ A, int lda, int adj,
+                                                         const double2* __restrict__ B, int ldb,
+                                                         double2* __restrict__ C, int ldc, int M, int N, int K) {
+  __shared__ cx<TC> sA[ZT][ZT + 1];  // sA[i][l] = op(A)[i0 + i][l0 + l]
+  __shared__ cx<TC> sB[ZT][ZT + 1];  // sB[l][j] = B[l0 + l][j0 + j]
+  const int tx = threadIdx.x % ZT, ty = threadIdx.x / ZT;
+  const int i0 = blockIdx.y * ZT, j0 = blockIdx.x * ZT;
+  cx<TC> acc = mk<TC>(0, 0);
+  for (int l0 = 0; l0 < K; l0 += ZT) {
+    {
+      // op(A) tile: row i0 + ty, column l0 + tx
+      const int i = i0 + ty, l = l0 + tx;
+      double2 a = make_double2(0, 0);
+      if (i < M && l < K) a = adj ? conjg(A[(int64_t)l * lda + i]) : A[(int64_t)i * lda + l];
+      sA[ty][tx] = mk<TC>((TC)a.x, (TC)a.y);
+      const int lb = l0 + ty, j = j0 + tx;
+      double2 b = make_double2(0, 0);
+      if (lb < K && j < N) b = B[(int64_t)lb * ldb + j];
+      sB[ty][tx] = mk<TC>((TC)b.x, (TC)b.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < ZT; ++l) cfma(acc, sA[ty][l], sB[l][tx]);
+    __syncthreads();
   }
-  C[(int64_t)i * ldc + j] = acc;
+  const int i = i0 + ty, j = j0 + tx;
+  if (i < M && j < N) C[(int64_t)i * ldc + j] = make_double2((double)acc.x, (double)acc.y);
 }
 
 cudaError_t launch_zgemm_small(const double2* A, int lda, int adj, const double2* B, int ldb, double2* C, int ldc,
                                int M, int N, int K, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  k_zgemm_small<<<(M * N + 127) / 128, 128, 0, s>>>(A, lda, adj, B, ldb, C, ldc, M, N, K);
+  const dim3 grid((N + ZT - 1) / ZT, (M + ZT - 1) / ZT);
+  k_zgemm_small<double><<<grid, ZT * ZT, 0, s>>>(A, lda, adj, B, ldb, C, ldc, M, N, K);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -495,12 +495,15 @@ int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
     if (rc) return rc;
   }
   const int cm = fuse ? h->pend_cm : c;
-  int te = tbeg(h);
+  int te;
   if (fuse) {
+    te = tbeg(h);
     CK(launch_zgemm_small(h->pend_C, 2 * c, 1, h->S, 2 * cm, h->Ztmp, 2 * cm, 2 * c, 2 * cm, 2 * cm, h->stream));
     CK(launch_zgemm_small(h->Ztmp, 2 * cm, 0, h->pend_C, 2 * c, h->S2, 2 * c, 2 * c, 2 * c, 2 * cm, h->stream));
     CK(launch_assemble_gram(h->S2, c, K, pq, h->G, h->stream));
+    tend(h, LR_K_SMALL, te);
   } else {
+    te = tbeg(h);
     const int splits = gram_splits(N2, 2 * c, 2 * c);
     if (h->dtype == LR_C64 && h->use_tc && gram_pair_tc_supported(c, N2)) {
       const int max_splits = (int)(h->partials_elems / ((size_t)4 * c * c));
@@ -511,9 +514,11 @@ int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
                                         h->stream, q, c);
       }));
     }
+    tend(h, LR_K_GRAM, te);
+    te = tbeg(h);
     CK(launch_assemble_gram(h->S, c, K, pq, h->G, h->stream));
+    tend(h, LR_K_SMALL, te);
   }
-  tend(h, LR_K_GRAM, te);
   int k;
   int rc = run_eigh(h, m, r_eff, eps, &k);
   if (rc) return rc;
@@ -527,7 +532,7 @@ int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
     h->pend_cm = c;
     h->pend_q = q;
   }
-  tend(h, LR_K_PROJECT, te);
+  tend(h, LR_K_SMALL, te);
   h->pend = true;  // the projection itself runs when the state is next needed
   h->c = k;
   h->ncomp++;
