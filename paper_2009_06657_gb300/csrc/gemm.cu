@@ -211,11 +211,63 @@ cudaError_t launch_gram_reduce_herm(const double2* partials, int splits, int m, 
   return cudaGetLastError();
 }
 
+// The Hermitian reduction of FP32 partials with four threads per element: thread
+// sub of a group of four sums splits sub, sub + 4, ... (compensated), and the four
+// (sum, compensation) pairs are added in a fixed order, so the result does not
+// depend on scheduling. Four times the threads of one-thread-per-element, each with a
+// quarter of the dependent loads.
+__global__ void k_gram_reduce_herm_f32x4(const float2* __restrict__ partials, int splits, int m,
+                                         double2* __restrict__ out) {
+  const int64_t total = (int64_t)m * m;
+  const int lane = threadIdx.x & 31, sub = lane & 3;
+  // a warp takes 8 consecutive elements per iteration (warp-uniform loop: the
+  // shuffles below need every lane)
+  const int64_t wstep = (((int64_t)gridDim.x * blockDim.x) >> 5) * 8;
+  for (int64_t gb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 8; gb < total; gb += wstep) {
+    const int64_t g = gb + (lane >> 2);
+    const int i = (int)(g / m), j = (int)(g % m);
+    const bool keep = g < total && (i / TILE) <= (j / TILE) && i <= j;  // computed tile, upper triangle
+    float s_r = 0.f, c_r = 0.f, s_i = 0.f, c_i = 0.f;
+    if (keep) {
+      int s = sub;
+      for (; s + 12 < splits; s += 16) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = partials[(int64_t)(s + 4 * u) * total + g];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          neumaier(s_r, c_r, v[u].x);
+          neumaier(s_i, c_i, v[u].y);
+        }
+      }
+      for (; s < splits; s += 4) {
+        const float2 v = partials[(int64_t)s * total + g];
+        neumaier(s_r, c_r, v.x);
+        neumaier(s_i, c_i, v.y);
+      }
+    }
+    // (sum + compensation) of the four threads, in the order 0 + 1, 2 + 3, then both
+    double r = (double)s_r + (double)c_r, im = (double)s_i + (double)c_i;
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    im += __shfl_xor_sync(0xffffffffu, im, 1);
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    im += __shfl_xor_sync(0xffffffffu, im, 2);
+    if (keep && sub == 0) {
+      if (i == j) {
+        out[g] = make_double2(r, 0.0);
+      } else {
+        out[g] = make_double2(r, im);
+        out[(int64_t)j * m + i] = make_double2(r, -im);
+      }
+    }
+  }
+}
+
 cudaError_t launch_gram_reduce_herm_f32(const float2* partials, int splits, int m, double2* out, cudaStream_t s) {
   const int64_t total = (int64_t)m * m;
-  int blocks = (int)((total + 255) / 256);
+  int blocks = (int)((4 * total + 255) / 256);
   if (blocks > 4096) blocks = 4096;
-  k_gram_reduce<float2><<<blocks, 256, 0, s>>>(partials, splits, m, m, 1, out);
+  k_gram_reduce_herm_f32x4<<<blocks, 256, 0, s>>>(partials, splits, m, out);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -383,9 +435,9 @@ __global__ void k_build_proj(const double2* __restrict__ U, int c, int K, int k,
 // C (M x N) = op(A) B with op(A) = A (M x K, row stride lda) or A^dag (A stored K x M).
 // Small products of the deferred pair projection (M, N, K <= 512) in FP64 (the
 // composed coefficients feed every later truncation on the qubit, so their rounding
-// accumulates; FP32 products measurably loosened a 480-truncation run). 16 x 16
-// output tiles, K staged 16 at a time in shared memory.
-constexpr int ZT = 16;
+// accumulates; FP32 products measurably loosened a 480-truncation run). ZT x ZT
+// output tiles, K staged ZT at a time in shared memory.
+constexpr int ZT = 8;  // 8 x 8 tiles: a 128 x 128 product spreads over 256 blocks (all SMs)
 template <typename TC>
 __global__ void __launch_bounds__(ZT * ZT) k_zgemm_small(const double2* __restrict__ A, int lda, int adj,
                                                          const double2* __restrict__ B, int ldb,
