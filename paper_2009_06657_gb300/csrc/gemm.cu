@@ -119,10 +119,11 @@ __global__ void __launch_bounds__(256) k_gram(const cx<T>* __restrict__ A, int l
                blockIdx.y);
 }
 
-// sum over the splits of one entry, in a fixed order. FP64 partials: eight
-// independent FP64 running sums. FP32 partials: compensated FP32 sums (Neumaier;
-// error about 2 eps of the sum of magnitudes, like an FP64 sum of FP32 terms),
-// because FP64 arithmetic and conversions run at 1/62 of the FP32 rate here.
+// sum over the splits of one entry, in a fixed order: eight independent FP64
+// running sums. (FP32 partials are summed by k_gram_reduce_herm_f32x4 with
+// compensated FP32 sums -- error about 2 eps of the sum of magnitudes, like an FP64
+// sum of FP32 terms -- because FP64 arithmetic and conversions run at 1/62 of the
+// FP32 rate here.)
 __device__ __forceinline__ void split_sum(const double2* __restrict__ partials, int splits, int64_t total,
                                           int64_t e, double& sr, double& si) {
   double ar[8] = {0, 0, 0, 0, 0, 0, 0, 0}, ai[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -148,29 +149,6 @@ __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
   const float t = s + x;
   c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
   s = t;
-}
-
-__device__ __forceinline__ void split_sum(const float2* __restrict__ partials, int splits, int64_t total,
-                                          int64_t e, double& sr, double& si) {
-  float s_r = 0.f, c_r = 0.f, s_i = 0.f, c_i = 0.f;
-  int s = 0;
-  for (; s + 8 <= splits; s += 8) {
-    float2 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = partials[(int64_t)(s + u) * total + e];  // eight loads in flight
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      neumaier(s_r, c_r, v[u].x);
-      neumaier(s_i, c_i, v[u].y);
-    }
-  }
-  for (; s < splits; ++s) {
-    const float2 v = partials[(int64_t)s * total + e];
-    neumaier(s_r, c_r, v.x);
-    neumaier(s_i, c_i, v.y);
-  }
-  sr = (double)s_r + (double)c_r;
-  si = (double)s_i + (double)c_i;
 }
 
 // out[i][j] = sum_s partials[s][i][j]; Hermitian: fill the lower triangle from the
