@@ -487,3 +487,38 @@ def test_kraus_group_truncation_is_the_best_rank_r_approximation():
     top = (U[:, -r:] * w[-r:]) @ U[:, -r:].conj().T
     assert np.max(np.abs(st.rho() - top)) < 1e-12
     assert abs(st.discarded - w[:-r].sum()) < 1e-12
+
+
+# ---- printed values (tests/golden) -----------------------------------------
+
+def _golden(name):
+    import os
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_app_a_effective_rank_growth_printed_values():
+    """App. A prints gamma_bit ~ 0.008 and gamma_dep ~ 0.009 at p = 0.1 %: the oracle's
+    entropy of one bit flip on |0> and of a depolarizing channel on half of a Bell
+    pair (where the entropy bound is attained) gives 2^S - 1 that rounds to them."""
+    g = _golden("app_a_effective_rank.txt")
+    p = g["p"]
+    st = O.LRETState(1)
+    st.channel(0, O.bit_flip(p))
+    gamma_bit = 2.0 ** st.entropy() - 1.0
+    bell = O.LRETState(2)
+    bell.gate([0], O.FIXED_1Q["h"])
+    bell.gate([0, 1], O.cnot())
+    bell.channel(0, O.depolarizing(p))
+    gamma_dep = 2.0 ** bell.entropy() - 1.0
+    assert round(gamma_bit, 3) == g["gamma_bit"]
+    assert round(gamma_dep, 3) == g["gamma_dep"]
+    # and they equal the bound -sum p_a log2 p_a itself
+    assert abs(bell.entropy() - (-(1 - p) * np.log2(1 - p) - p * np.log2(p / 3))) < 1e-12
+    assert abs(st.entropy() - (-(1 - p) * np.log2(1 - p) - p * np.log2(p))) < 1e-12
