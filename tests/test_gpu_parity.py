@@ -70,8 +70,11 @@ def _cut_sensitivity(st):
     return tot
 
 
-# Fraction of the tolerance the predicted truncation error may take.
-SENS_BUDGET = {"c128": 0.1, "c64": 1.0}
+# Fraction of the tolerance the predicted truncation error may take. The prediction
+# (unit roundoff x cut sensitivity) is an upper estimate: on the 12-qubit complex64
+# case it is 1.2e-5 while the measured L1 error of Prob(x) is 5e-7, so complex64
+# seeds are accepted up to 2.5 x the tolerance and still held to the tolerance itself.
+SENS_BUDGET = {"c128": 0.1, "c64": 2.5}
 
 
 def _pick(n, r, depth, noise, seed, dtype, tries=24):
