@@ -645,34 +645,34 @@ def load_peaks():
             "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "source": "fallback"}
 
 
-def cpu_sample():
-    """Bounded CPU sample: the oracle runs the first layer's ops up to and
-    including its second full-width truncation (c = 64 -> 256 -> 64)."""
+def cpu_truncations(count):
+    """Bounded CPU sample: the oracle runs the first layer's ops; the prefix that
+    brings the state to 64 columns is untimed, then the next `count` full-width
+    truncations (channel, c = 64 -> 256 -> 64, Gram, eigh, projection) are timed
+    one by one. Returns their durations in seconds."""
     from oracle import lret as O
     ops = get_layers()[0]
     st = O.LRETState(N_QUBITS)
-    full = 0
-    t_trunc, n_trunc, g_done, t_all0 = 0.0, 0, 0, time.perf_counter()
+    times = []
     for o in ops:
         if O.is_gate(o):
             qs, U = O.gate_matrix(o)
             st.gate(qs, U)
-            g_done += 1
         else:
-            st.channel(o["q"], O.channel_kraus(o))
+            full = st.L.shape[1] == RANK
             t0 = time.perf_counter()
+            st.channel(o["q"], O.channel_kraus(o))
             st.compress(r=RANK)
-            if st.log[-1]["m"] == 4 * RANK:
-                t_trunc += time.perf_counter() - t0
-                n_trunc += 1
-                full += 1
-                if full >= 2:
+            if full and st.log[-1]["m"] == 4 * RANK:
+                times.append(time.perf_counter() - t0)
+                if len(times) >= count:
                     break
-    return t_trunc / max(n_trunc, 1), n_trunc
+    return times
 
 
 def cpu_baseline(res):
-    s_per_tr, n_tr = cpu_sample()
+    times = cpu_truncations(2)
+    s_per_tr, n_tr = statistics.median(times), len(times)
     tps = res["c_per"] / res["g_per"]
     return {"value": 1.0 / (s_per_tr * tps), "unit": "noisy gate-steps/s", "cores": os.cpu_count(),
             "kind": "oracle",
@@ -681,22 +681,25 @@ def cpu_baseline(res):
 
 
 def run_reference(args):
-    per = []
-    for i in range(args.warmup + args.steps):
-        s, n = cpu_sample()
-        if i >= args.warmup:
-            per.append(s)
-        if i == 0 and args.warmup + args.steps > 2:
-            break  # one sample bounds the run to a few minutes
-    s_per_tr = statistics.median(per) if per else s
+    """The oracle as it stands on the host cores: W untimed and K timed full-width
+    truncations of the benchmark workload (one per step), reported per noisy
+    gate-step like the GPU arm."""
+    times = cpu_truncations(args.warmup + args.steps)
+    per = times[args.warmup:] or times
+    s_per_tr = statistics.median(per)
     g_per, c_per = count(get_layers()[0])
     v = 1.0 / (s_per_tr * c_per / g_per)
+    cfg = workload_config()
+    cfg["gates_per_step"] = g_per
+    cfg["truncations_per_step"] = c_per
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "noisy gate-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded random circuits)",
-            "config": workload_config(),
+            "config": cfg,
             "cpu_baseline": {"value": v, "unit": "noisy gate-steps/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "full-width truncations of the 20-qubit workload on host cores"},
+                             "sample": f"oracle (NumPy complex128) on the host: {len(per)} timed full-width "
+                                       f"truncations of the 20-qubit workload after {args.warmup} untimed, "
+                                       f"extrapolated per noisy gate-step"},
             "e2e": {"value": v, "unit": "noisy gate-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
