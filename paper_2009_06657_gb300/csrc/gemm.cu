@@ -414,43 +414,57 @@ __global__ void k_build_proj(const double2* __restrict__ U, int c, int K, int k,
 // Small products of the deferred pair projection (M, N, K <= 512) in FP64 (the
 // composed coefficients feed every later truncation on the qubit, so their rounding
 // accumulates; FP32 products measurably loosened a 480-truncation run). ZT x ZT
-// output tiles, K staged ZT at a time in shared memory.
-constexpr int ZT = 8;  // 8 x 8 tiles: a 128 x 128 product spreads over 256 blocks (all SMs)
+// output tiles, K staged ZT * ZK at a time in shared memory and split over ZK thread
+// groups whose partial sums are added in a fixed order.
+constexpr int ZT = 8;  // 8 x 8 output tiles: a 128 x 128 product spreads over 256 blocks (all SMs)
+constexpr int ZK = 4;  // K split four ways inside a block (four times the warps, a quarter of the chain)
 template <typename TC>
-__global__ void __launch_bounds__(ZT * ZT) k_zgemm_small(const double2* __restrict__ A, int lda, int adj,
-                                                         const double2* __restrict__ B, int ldb,
-                                                         double2* __restrict__ C, int ldc, int M, int N, int K) {
-  __shared__ cx<TC> sA[ZT][ZT + 1];  // sA[i][l] = op(A)[i0 + i][l0 + l]
-  __shared__ cx<TC> sB[ZT][ZT + 1];  // sB[l][j] = B[l0 + l][j0 + j]
-  const int tx = threadIdx.x % ZT, ty = threadIdx.x / ZT;
+__global__ void __launch_bounds__(ZT * ZT * ZK) k_zgemm_small(const double2* __restrict__ A, int lda, int adj,
+                                                              const double2* __restrict__ B, int ldb,
+                                                              double2* __restrict__ C, int ldc, int M, int N,
+                                                              int K) {
+  constexpr int KS = ZT * ZK;        // K slice staged per step
+  __shared__ cx<TC> sA[ZT][KS + 1];  // sA[i][l] = op(A)[i0 + i][l0 + l]
+  __shared__ cx<TC> sB[KS][ZT + 1];  // sB[l][j] = B[l0 + l][j0 + j]
+  __shared__ cx<TC> red[ZK][ZT][ZT];
+  const int tid = threadIdx.x;
+  const int tx = tid % ZT, ty = (tid / ZT) % ZT, kg = tid / (ZT * ZT);
   const int i0 = blockIdx.y * ZT, j0 = blockIdx.x * ZT;
   cx<TC> acc = mk<TC>(0, 0);
-  for (int l0 = 0; l0 < K; l0 += ZT) {
+  for (int l0 = 0; l0 < K; l0 += KS) {
     {
-      // op(A) tile: row i0 + ty, column l0 + tx
-      const int i = i0 + ty, l = l0 + tx;
+      const int i = tid / KS, l = tid % KS;  // op(A) tile: ZT rows x KS columns, one per thread
+      const int gi = i0 + i, gl = l0 + l;
       double2 a = make_double2(0, 0);
-      if (i < M && l < K) a = adj ? conjg(A[(int64_t)l * lda + i]) : A[(int64_t)i * lda + l];
-      sA[ty][tx] = mk<TC>((TC)a.x, (TC)a.y);
-      const int lb = l0 + ty, j = j0 + tx;
+      if (gi < M && gl < K) a = adj ? conjg(A[(int64_t)gl * lda + gi]) : A[(int64_t)gi * lda + gl];
+      sA[i][l] = mk<TC>((TC)a.x, (TC)a.y);
+      const int lb = tid / ZT, j = tid % ZT;  // B tile: KS rows x ZT columns, one per thread
+      const int glb = l0 + lb, gj = j0 + j;
       double2 b = make_double2(0, 0);
-      if (lb < K && j < N) b = B[(int64_t)lb * ldb + j];
-      sB[ty][tx] = mk<TC>((TC)b.x, (TC)b.y);
+      if (glb < K && gj < N) b = B[(int64_t)glb * ldb + gj];
+      sB[lb][j] = mk<TC>((TC)b.x, (TC)b.y);
     }
     __syncthreads();
 #pragma unroll
-    for (int l = 0; l < ZT; ++l) cfma(acc, sA[ty][l], sB[l][tx]);
+    for (int l = kg * ZT; l < kg * ZT + ZT; ++l) cfma(acc, sA[ty][l], sB[l][tx]);
     __syncthreads();
   }
-  const int i = i0 + ty, j = j0 + tx;
-  if (i < M && j < N) C[(int64_t)i * ldc + j] = make_double2((double)acc.x, (double)acc.y);
+  red[kg][ty][tx] = acc;
+  __syncthreads();
+  if (kg == 0) {
+    cx<TC> r = red[0][ty][tx];
+#pragma unroll
+    for (int q = 1; q < ZK; ++q) r = cadd(r, red[q][ty][tx]);  // fixed order
+    const int i = i0 + ty, j = j0 + tx;
+    if (i < M && j < N) C[(int64_t)i * ldc + j] = make_double2((double)r.x, (double)r.y);
+  }
 }
 
 cudaError_t launch_zgemm_small(const double2* A, int lda, int adj, const double2* B, int ldb, double2* C, int ldc,
                                int M, int N, int K, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   const dim3 grid((N + ZT - 1) / ZT, (M + ZT - 1) / ZT);
-  k_zgemm_small<double><<<grid, ZT * ZT, 0, s>>>(A, lda, adj, B, ldb, C, ldc, M, N, K);
+  k_zgemm_small<double><<<grid, ZT * ZT * ZK, 0, s>>>(A, lda, adj, B, ldb, C, ldc, M, N, K);
   note_launches(1);
   return cudaGetLastError();
 }
