@@ -22,7 +22,11 @@
 //     reflector, so there is no second exchange: one cluster barrier per step.
 // The step state (v, p, partials, tau) rotates through three slots because a
 // CTA may run one step ahead of another. One CTA also writes each reflector to
-// global memory for the back-transform.
+// global memory for the back-transform. A step costs about the same whatever the
+// size of the trailing block (it is bound by the cluster barrier and the chain of
+// the reflector), so the last TAIL_N steps run on CTA 0 alone: the trailing
+// block is gathered into its shared memory and each step takes two block
+// barriers (matvec; rank-2 update beside the next reflector).
 //
 // Eigenvalues: multisection (each eigenvalue is bracketed by 16 threads that
 // evaluate the Sturm count at 16 interior points, a 17-fold shrink per round).
@@ -54,6 +58,8 @@ constexpr int CL_NW = CL_THREADS / 32;
 constexpr int CL_MAXM = 256;
 constexpr int CL_ROWS = CL_MAXM / CL;  // rows per CTA at most
 constexpr int MS = 16;                 // threads (and interior points) per eigenvalue in multisection
+constexpr int TAIL_N = 90;             // trailing block finished by CTA 0 alone
+static_assert(TAIL_N * TAIL_N <= CL_ROWS * CL_MAXM && TAIL_N <= 96, "trailing block: scratch A, 3 columns a lane");
 constexpr int BT_STAGE = 32;           // reflectors staged per shared-memory block in the back-transform
 template <typename T> struct BtGroup { static constexpr int v = 4; };  // reflectors applied together
 template <> struct BtGroup<double> { static constexpr int v = 2; };  // (register budget of 512 threads)
@@ -240,6 +246,94 @@ __device__ void group_reflector(ClusterShared<T>& sh, const cx<T>* __restrict__ 
 #undef LRET_GSTEP
 }
 
+// One warp forms v, tau from row jr of the trailing block (columns jr .. m - 1, at
+// most 96 of them: lane l holds columns jr + l + 32 h) after applying the update
+// of the current step, a -= v_r conj(w_c) + w_r conj(v_c) with r = jr; vv and ww
+// hold v and w at the lane's columns. Same scalars as group_reflector. For
+// jr = m - 1 only the last diagonal entry is formed.
+template <typename T>
+__device__ void warp_reflector(ClusterShared<T>& sh, const cx<T>* __restrict__ row, int jr, int m, int slv,
+                               const cx<T> (&vv)[3], const cx<T> (&ww)[3], bool upd, cx<T>* __restrict__ gref,
+                               int lane) {
+  const cx<T> vr = mk<T>(__shfl_sync(0xffffffffu, vv[0].x, 0), __shfl_sync(0xffffffffu, vv[0].y, 0));
+  const cx<T> wr = mk<T>(__shfl_sync(0xffffffffu, ww[0].x, 0), __shfl_sync(0xffffffffu, ww[0].y, 0));
+  cx<T> x[3];
+  T amax = 0, part = 0;
+#pragma unroll
+  for (int h = 0; h < 3; ++h) {
+    const int col = jr + lane + 32 * h;
+    cx<T> a = mk<T>(0, 0);
+    if (col < m) {
+      a = row[col];
+      if (upd) a = csub(a, cadd(cmul(vr, conjg(ww[h])), cmul(wr, conjg(vv[h]))));
+      if (col == jr) a.y = 0;
+      if (col > jr) {
+        amax = fmax(amax, fmax(fabs(a.x), fabs(a.y)));
+        if (col > jr + 1) part += a.x * a.x + a.y * a.y;
+      }
+    }
+    x[h] = a;
+  }
+  if (jr == m - 1) {  // last diagonal entry
+    if (lane == 0) {
+      sh.d[jr] = x[0].x;
+      sh.e[jr] = 0;
+    }
+    return;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    part += __shfl_xor_sync(0xffffffffu, part, o);
+  }
+  // alpha = conj(A[jr][jr+1]), entry h = 0 of lane 1
+  const cx<T> alpha = mk<T>(__shfl_sync(0xffffffffu, x[0].x, 1), -__shfl_sync(0xffffffffu, x[0].y, 1));
+  const T am = amax;
+  const T inv = am > (T)0 ? (T)1 / am : (T)0;
+  T xn2s = part * inv * inv;
+  if (am > (T)0 && part < (T)1e-30) {  // squares may have underflowed: sum scaled values
+    T sacc = 0;
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+      const int col = jr + lane + 32 * h;
+      if (col > jr + 1 && col < m) sacc += (x[h].x * inv) * (x[h].x * inv) + (x[h].y * inv) * (x[h].y * inv);
+    }
+    xn2s = warp_sum(sacc);
+  }
+  cx<T> tau, scale;
+  T beta;
+  if (am <= (T)1e-30 || (xn2s == (T)0 && alpha.y == (T)0)) {
+    tau = mk<T>(0, 0);
+    beta = alpha.x;
+    scale = mk<T>(0, 0);
+  } else {
+    const T ar = alpha.x * inv, ai = alpha.y * inv;
+    const T bs = -copysign(sqrt(ar * ar + ai * ai + xn2s), ar);
+    beta = am * bs;
+    tau = mk<T>((bs - ar) / bs, -ai / bs);
+    const T den = (ar - bs) * (ar - bs) + ai * ai;
+    scale = mk<T>((ar - bs) / den * inv, -ai / den * inv);
+  }
+  cx<T>* gv = gref + (size_t)jr * CL_MAXM;  // full-length row of the reflector store
+#pragma unroll
+  for (int h = 0; h < 3; ++h) {
+    const int col = jr + lane + 32 * h;
+    if (col > jr && col < m) {
+      const cx<T> v = col == jr + 1 ? mk<T>(1, 0) : cmul(conjg(x[h]), scale);
+      sh.v[slv][col] = v;
+      gv[col] = v;
+    }
+  }
+  for (int rr = lane; rr <= jr; rr += 32) gv[rr] = mk<T>(0, 0);
+  for (int rr = m + lane; rr < CL_MAXM; rr += 32) gv[rr] = mk<T>(0, 0);
+  if (lane == 0) {
+    sh.d[jr] = x[0].x;
+    gref[(size_t)(CL_MAXM - 1) * CL_MAXM + jr] = tau;  // tau row
+    sh.tau[slv] = tau;
+    sh.e[jr] = beta;
+  }
+}
+
 __device__ __forceinline__ long long phase_clock() { return clock64(); }
 
 }  // namespace
@@ -333,7 +427,13 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
 #else
 #define LRET_SUBSTEP(k)
 #endif
-  for (int j = 0; j < m - 1; ++j) {
+  // The last steps act on a trailing block of at most TAIL_N rows: CTA 0 finishes
+  // them alone from shared memory (block barriers instead of cluster barriers).
+  const int s0 = m - 1 > TAIL_N ? m - 1 - TAIL_N : 0;
+#if defined(LRET_EIG_PROFILE) && LRET_EIG_PROFILE >= 3
+  const long long tloop0 = clock64();
+#endif
+  for (int j = 0; j < s0; ++j) {
     const int sl = j % 3, slp = (j + 2) % 3, sln = (j + 1) % 3;  // slots of steps j, j - 1, j + 1
     const int nx = j + 1;
     const cx<T> tau = sh.tau[sl];
@@ -437,6 +537,153 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     LRET_SUBSTEP(4)
   }
 #undef LRET_SUBSTEP
+#if defined(LRET_EIG_PROFILE) && LRET_EIG_PROFILE >= 3
+  const long long tloop1 = clock64();
+#endif
+  // ---- trailing block on CTA 0 ------------------------------------------------
+  // Rows and columns s0 + 1 .. m - 1 (updated through step s0 - 1; v_s0, tau_s0,
+  // d_s0, e_s0 are known to every CTA) go to CTA 0's scratch A, nt x nt.
+  const int nt = m - 1 - s0;
+  if (tid < RG) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  {
+    cx<T>* tb0 = &peer(0)->A[0][0];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int c = lane + 32 * e;
+      if (c > s0 && c < m) {
+        if (li0 < nrows && i0 > s0) tb0[(size_t)(i0 - s0 - 1) * nt + (c - s0 - 1)] = A0[e];
+        if (li1 < nrows && i1 > s0) tb0[(size_t)(i1 - s0 - 1) * nt + (c - s0 - 1)] = A1[e];
+      }
+    }
+  }
+  cluster.sync();
+#if defined(LRET_EIG_PROFILE) && LRET_EIG_PROFILE >= 3
+  // diagnostic build: cycles of the trailing block's sub-steps (3: thread 0, 4: thread 128)
+  __shared__ long long tdbg[6];
+  long long tp3[4] = {0, 0, 0, 0}, tq3 = clock64();
+  if (tid == 0) tdbg[1] = tq3;
+#define LRET_TAILSTEP(k) { const long long t2 = clock64(); tp3[k] += t2 - tq3; tq3 = t2; }
+#else
+#define LRET_TAILSTEP(k)
+#endif
+  if (rank == 0) {
+    cx<T>* tb = &sh.A[0][0];
+    auto trow = [&](int i) { return tb + (ptrdiff_t)(i - s0 - 1) * nt - (s0 + 1); };  // indexed by column
+    cx<T>* pq = &sh.nrow[0][0];  // matvec partials, four column quarters x 128 rows
+    for (int j = s0; j < m - 1; ++j) {
+      const int sl = j % 3, sln = (j + 1) % 3;
+      const cx<T> tau = sh.tau[sl];
+      const bool skip = (tau.x == (T)0 && tau.y == (T)0);
+      const int n1 = m - 1 - j;  // trailing rows and columns j + 1 .. m - 1
+      // A v by column quarters: thread (q, il) sums conj(A[c][i]) v_c = A[i][c] v_c over
+      // quarter q of the columns for row i = j + 1 + il (column reads: consecutive
+      // threads read consecutive entries of row c)
+      if (!skip) {
+        const int q = tid >> 7, il = tid & 127;
+        if (il < n1) {
+          const int len = (n1 + 3) >> 2;
+          const int ca = j + 1 + q * len, cb = min(ca + len, m);
+          const int i = j + 1 + il;
+          cx<T> acc0 = mk<T>(0, 0), acc1 = mk<T>(0, 0);
+          int c = ca;
+          for (; c + 1 < cb; c += 2) {
+            cfma(acc0, conjg(trow(c)[i]), sh.v[sl][c]);
+            cfma(acc1, conjg(trow(c + 1)[i]), sh.v[sl][c + 1]);
+          }
+          if (c < cb) cfma(acc0, conjg(trow(c)[i]), sh.v[sl][c]);
+          pq[q * 128 + il] = cadd(acc0, acc1);
+        }
+      }
+      LRET_TAILSTEP(0)
+      __syncthreads();
+      LRET_TAILSTEP(1)
+      // every warp: p_c = tau (A v)_c, v_c for its lanes' columns c = j + 1 + lane + 32 h,
+      // then cc = (1/2) Re(conj(tau) v^dag p) by its own (identical) reduction
+      cx<T> vv[3], ww[3];
+      T cc = 0;
+      {
+        cx<T> pp[3];
+        T dr = 0, di = 0;
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+          const int c = j + 1 + lane + 32 * h;
+          vv[h] = mk<T>(0, 0);
+          pp[h] = mk<T>(0, 0);
+          if (c < m && !skip) {
+            const int k = c - j - 1;
+            vv[h] = sh.v[sl][c];
+            pp[h] = cmul(tau, cadd(cadd(pq[k], pq[128 + k]), cadd(pq[256 + k], pq[384 + k])));
+            dr += vv[h].x * pp[h].x + vv[h].y * pp[h].y;
+            di += vv[h].x * pp[h].y - vv[h].y * pp[h].x;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          dr += __shfl_xor_sync(0xffffffffu, dr, o);
+          di += __shfl_xor_sync(0xffffffffu, di, o);
+        }
+        cc = (T)0.5 * (tau.x * dr + tau.y * di);
+#pragma unroll
+        for (int h = 0; h < 3; ++h) ww[h] = csub(pp[h], cscale(vv[h], cc));
+      }
+      if (warp == 0) {
+        // v_{j+1}, tau_{j+1} from row j + 1 with this step's update applied (or d_{m-1})
+        warp_reflector<T>(sh, trow(j + 1), j + 1, m, sln, vv, ww, !skip, gref, lane);
+      } else if (!skip) {
+        // rows j + 2 .. m - 1, columns j + 1 .. m - 1: A[i][c] -= v_i conj(w_c) + w_i conj(v_c)
+        // (column j + 1 is no longer read); three rows per batch, loads first
+        constexpr int UW = CL_NW - 1;
+        for (int i0 = j + 2 + (warp - 1); i0 < m; i0 += 3 * UW) {
+          cx<T> a[3][3], vi[3], wi[3];
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            const int i = i0 + t * UW;
+            const int k = i - j - 1, hk = k >> 5, lk = k & 31;  // row i's entry in the lanes' columns
+            const cx<T> vs = hk == 0 ? vv[0] : (hk == 1 ? vv[1] : vv[2]);
+            const cx<T> ws = hk == 0 ? ww[0] : (hk == 1 ? ww[1] : ww[2]);
+            vi[t] = mk<T>(__shfl_sync(0xffffffffu, vs.x, lk), __shfl_sync(0xffffffffu, vs.y, lk));
+            wi[t] = mk<T>(__shfl_sync(0xffffffffu, ws.x, lk), __shfl_sync(0xffffffffu, ws.y, lk));
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+              const int c = j + 1 + lane + 32 * h;
+              a[t][h] = (i < m && c < m) ? trow(i)[c] : mk<T>(0, 0);
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            const int i = i0 + t * UW;
+            if (i < m) {
+#pragma unroll
+              for (int h = 0; h < 3; ++h) {
+                const int c = j + 1 + lane + 32 * h;
+                if (c < m) {
+                  cx<T> x = csub(a[t][h], cadd(cmul(vi[t], conjg(ww[h])), cmul(wi[t], conjg(vv[h]))));
+                  if (c == i) x.y = 0;
+                  trow(i)[c] = x;
+                }
+              }
+            }
+          }
+        }
+      }
+      LRET_TAILSTEP(2)
+      __syncthreads();
+      LRET_TAILSTEP(3)
+    }
+#if defined(LRET_EIG_PROFILE) && LRET_EIG_PROFILE >= 3
+    if (tid == (LRET_EIG_PROFILE == 3 ? 0 : 128))
+      for (int q = 0; q < 4; ++q) tdbg[2 + q] = tp3[q];
+#endif
+#undef LRET_TAILSTEP
+    // the tail's diagonal and off-diagonal to the other CTAs
+    for (int q = 1; q < CL; ++q) {
+      ClusterShared<T>* pq = peer(q);
+      for (int i = s0 + 1 + tid; i < m; i += CL_THREADS) {
+        pq->d[i] = sh.d[i];
+        pq->e[i] = sh.e[i];
+      }
+    }
+  }
   cluster.sync();
   if (tid == 0) { const long long t1 = phase_clock(); t_ph[1] = t1 - t0; t0 = t1; }
 
@@ -958,7 +1205,11 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     for (int q = 0; q < 6; ++q) out->cycles[q] = t_ph[q];
 #ifdef LRET_EIG_PROFILE
     for (int q = 0; q < 6; ++q) out->cycles[q] = sp[q];
-#if LRET_EIG_PROFILE != 2
+#if LRET_EIG_PROFILE >= 3
+    out->cycles[0] = tloop1 - tloop0;      // cluster steps
+    out->cycles[1] = tdbg[1] - tloop1;     // gather
+    for (int q = 0; q < 4; ++q) out->cycles[2 + q] = tdbg[2 + q];  // matvec, barrier, group or update, barrier
+#elif LRET_EIG_PROFILE != 2
     out->cycles[2] = sh.gdbg[0];  // x and its updates
     out->cycles[3] = sh.gdbg[1];  // first group barrier
     out->cycles[4] = sh.gdbg[2];  // norms and scalars
