@@ -158,6 +158,24 @@ def test_truncated_circuit_parity(lr, dtype, case, solver):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("r", [22, 23], ids=["m88", "m92"])
+def test_cluster_solver_trailing_block_sizes(lr, dtype, r):
+    """The cluster eigensolver finishes the last 90 Householder steps on one CTA.
+    A depolarizing channel on r columns gives m = 4r: m = 88 runs the whole
+    reduction there (87 steps), m = 92 runs one cluster step and then the largest
+    trailing block (90 rows)."""
+    n = 9
+    ops, ref, seed = _pick(n, r, 2 if dtype == "c128" else 1, ("dep", 5e-3), 1005, dtype)
+    assert 4 * r in {e["m"] for e in ref.log}
+    sim = lr.LRSim(n, r, dtype=dtype)
+    sim.set_eigensolver("cluster")
+    lr.run_ops(sim, ops, r=r)
+    _compare(lr, sim, ref, n, random_pauli_sum(n, 16, seed=seed + 7), TOL[dtype])
+    assert abs(sim.info()["discarded"] - ref.discarded) < TOL[dtype]
+    assert sim.info()["converged"]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("case", CIRCUITS, ids=[f"n{c[0]}r{c[1]}d{c[2]}" for c in CIRCUITS])
 def test_structured_truncation_matches_oracle_and_expanded(lr, dtype, case):
     """The truncation without forming V' (Gram from row pairs, projection on
