@@ -469,7 +469,7 @@ def algorithmic():
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum, m = 256); the eigensolver's
 # traffic does not depend on the qubit count (it reads the m x m Gram matrix).
-NCU_TRAFFIC = {"eigh": 1188864}
+NCU_TRAFFIC = {"eigh": 1210112}
 
 
 def kernel_rooflines(kt, peaks):
