@@ -4,7 +4,24 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace lret {
+
+// Dynamic shared memory above the default for `func`. The attribute belongs to the
+// function on the current device, so it is set once per device (devices 0..63;
+// others every call); `done` is the caller's per-function bit set.
+template <typename F>
+inline cudaError_t set_dyn_smem_once(F* func, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 template <typename T> struct CT;
 template <> struct CT<float> { using type = float2; };

@@ -1229,11 +1229,10 @@ cudaError_t launch_eigh_cluster(const double2* G, int m, void* work, double* eva
                                 int r, double eps, int all_vecs, cudaStream_t s) {
   if (m < 2 || m > CL_MAXM) return cudaErrorInvalidValue;
   const size_t smem = sizeof(ClusterShared<T>);
-  static bool attr[2] = {false, false};
-  if (!attr[sizeof(T) == 8]) {
-    cudaError_t e = cudaFuncSetAttribute(k_eigh_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<uint64_t> attr_done{0};  // one per instantiation
+  {
+    cudaError_t e = set_dyn_smem_once(k_eigh_cluster<T>, (int)smem, attr_done);
     if (e != cudaSuccess) return e;
-    attr[sizeof(T) == 8] = true;
   }
   // work: reflectors (CL_MAXM x CL_MAXM complex; last row holds tau) then Z (m x m real)
   cx<T>* gref = (cx<T>*)work;

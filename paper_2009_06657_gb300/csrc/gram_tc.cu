@@ -239,11 +239,10 @@ cudaError_t launch_gram_pair_tc(const void* V, int ld, int c, int pairbit, int64
   int64_t rows = (N2 + splits - 1) / splits;
   rows = ((rows + TC_KC - 1) / TC_KC) * TC_KC;
   splits = (int)((N2 + rows - 1) / rows);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_pair_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  static std::atomic<uint64_t> attr_done{0};
+  {
+    cudaError_t e = set_dyn_smem_once(k_gram_pair_tc, TC_SMEM, attr_done);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   k_gram_pair_tc<<<splits, TC_THREADS, TC_SMEM, s>>>((const float2*)V, ld, c, pairbit, N2, rows, partials, status);
   note_launches(1);

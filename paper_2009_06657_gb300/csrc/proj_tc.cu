@@ -268,11 +268,10 @@ size_t proj_pair_tc_scratch_bytes(int c, int k) { return (size_t)2 * (4 * c) * (
 
 cudaError_t launch_proj_pair_tc(const void* V, int ld, int c, int k, int pairbit, int64_t N2, const double2* D,
                                 float* Bscratch, void* W, int* status, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_proj_pair_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM);
+  static std::atomic<uint64_t> attr_done{0};
+  {
+    cudaError_t e = set_dyn_smem_once(k_proj_pair_tc, PT_SMEM, attr_done);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   const int nel = (4 * k) * (4 * c);
   k_proj_prep<<<(nel + 255) / 256, 256, 0, s>>>(D, c, k, Bscratch);
