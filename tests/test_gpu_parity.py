@@ -358,6 +358,31 @@ def test_full_size_properties(lr):
     assert bool((d[:-1] >= d[1:] - 1e-6).all())  # descending eigenvalue order
 
 
+def test_full_size_mixed_path_matches_fp64_path(lr):
+    """20 qubits, r = 64, the benchmark's circuit family (first 12 channels: the
+    state reaches 256 columns and is truncated several times): the FP32-state
+    path against this library's FP64 path on the same ops. A cut among nearly
+    equal small eigenvalues may keep different vectors in the two precisions,
+    which moves rho by at most about the discarded mass, so the bound is the
+    FP32 tolerance plus twice the discarded mass."""
+    n, r = 20, 64
+    ops = _first_channels(random_layered(n, 1, seed=3000, noise=("dep", 5e-4)), 12)
+    terms = random_pauli_sum(n, 64, seed=3001)
+    out = {}
+    for dtype in ("c64", "c128"):
+        sim = lr.LRSim(n, r, dtype=dtype)
+        lr.run_ops(sim, ops, r=r)
+        info = sim.info()
+        assert info["columns"] == r and info["compressions"] >= 3 and info["converged"]
+        out[dtype] = (sim.probs().double().cpu().numpy(), sim.expect(terms), info["discarded"])
+        sim.close()
+    (p32, h32, d32), (p64, h64, d64) = out["c64"], out["c128"]
+    bound = TOL["c64"] + 2 * max(d32, d64)
+    assert abs(d32 - d64) < TOL["c64"]
+    assert np.sum(np.abs(p32 - p64)) < bound
+    assert abs(h32 - h64) < bound * sum(abs(c) for c, _ in terms)
+
+
 # 3xTF32 products (TF32 high part x FP32 remainder, the remainder itself
 # truncated to TF32, the remainder product dropped) carry about 2^-21 relative
 # error; the probe of the tensor-core Gram measured 3.5e-7 against FP64.
