@@ -70,6 +70,33 @@ def test_pauli_masks_encoding():
     assert int(xm[0]) == 0b0101 and int(zm[0]) == 0b1100 and cf[0] == 0.5
 
 
+def test_pauli_mask_action_matches_kronecker_product():
+    """The header's action of a Pauli string given by its masks,
+    P|x> = i^{#Y} (-1)^{popcount(x & zmask)} |x ^ xmask>, against the dense
+    Kronecker product of the single-qubit matrices (qubit q = bit q of x)."""
+    import numpy as np
+
+    from oracle import lret as O
+    from paper_2009_06657_gb300.sim import pauli_masks
+    from workloads import random_pauli_sum
+    n = 4
+    terms = random_pauli_sum(n, 12, seed=9) + [(1.0, [(1, "Y"), (3, "Y")]), (1.0, [(0, "Y"), (2, "Z")])]
+    xm, zm, _ = pauli_masks(terms, n)
+    for t, (_, string) in enumerate(terms):
+        mats = [O.I2] * n
+        for q, s in string:
+            mats[q] = O.PAULI[s]
+        dense = np.array([[1.0 + 0j]])
+        for q in range(n - 1, -1, -1):
+            dense = np.kron(dense, mats[q])
+        ny = sum(1 for _, s in string if s == "Y")
+        P = np.zeros((2 ** n, 2 ** n), dtype=complex)
+        for x in range(2 ** n):
+            sign = -1.0 if bin(x & int(zm[t])).count("1") % 2 else 1.0
+            P[x ^ int(xm[t]), x] = (1j ** ny) * sign
+        assert np.max(np.abs(P - dense)) < 1e-15
+
+
 def test_launch_counter_reads_without_device(lib):
     n = lib.lib.lr_launch_count()
     assert isinstance(n, int) and n >= 0
