@@ -70,6 +70,21 @@ def test_pauli_masks_encoding():
     assert int(xm[0]) == 0b0101 and int(zm[0]) == 0b1100 and cf[0] == 0.5
 
 
+def test_status_codes_match_header_and_have_messages(lib):
+    """The binding's status constants are the header's, and every code (including
+    the bounded-wait give-up, LR_ETIMEOUT) has its own message."""
+    src = open(os.path.join(ROOT, "include", "lret.h")).read()
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (LR_E[A-Z]+)\s+(-?\d+)", src)}
+    assert {"LR_EINVAL", "LR_EKRAUS", "LR_ECAPACITY", "LR_ETIMEOUT", "LR_ECUDA"} <= set(codes)
+    msgs = set()
+    for name, val in codes.items():
+        assert getattr(lib, name) == val, name
+        msg = lib.lib.lr_status_string(val).decode()
+        assert msg and msg not in msgs, name
+        msgs.add(msg)
+    assert "timed out" in lib.lib.lr_status_string(codes["LR_ETIMEOUT"]).decode()
+
+
 def test_pauli_mask_action_matches_kronecker_product():
     """The header's action of a Pauli string given by its masks,
     P|x> = i^{#Y} (-1)^{popcount(x & zmask)} |x ^ xmask>, against the dense
