@@ -95,3 +95,19 @@ def test_generators_are_deterministic_in_their_seed(gen):
     else:
         a, b, c = (hea(8, 2, seed=s)[0] for s in (7, 7, 8))
     assert a == b and a != c
+
+
+def test_batch_recipe_ranges_and_miniature():
+    """256 circuits: n in 8..18, r in {8, 16, 32, 64}, depth in 40..200; a scaled
+    batch draws the same n, r and depths (scaled), so it is a miniature of the full one."""
+    from workloads import batch_circuits
+    full = batch_circuits(count=256, depth_scale=1.0)
+    assert len(full) == 256
+    ns = [c["n"] for c in full]
+    assert min(ns) == 8 and max(ns) == 18
+    assert {c["r"] for c in full} == {8, 16, 32, 64}
+    assert all(40 <= c["depth"] <= 200 for c in full)
+    mini = batch_circuits(count=256, depth_scale=0.05)
+    for a, b in zip(full, mini):
+        assert (a["n"], a["r"]) == (b["n"], b["r"])
+        assert b["depth"] == max(1, int(round(a["depth"] * 0.05)))
