@@ -112,6 +112,25 @@ def test_pauli_mask_action_matches_kronecker_product():
         assert np.max(np.abs(P - dense)) < 1e-15
 
 
+def test_package_import_fails_loudly_without_the_library(tmp_path):
+    """A copy of the package without _lib/liblret.so must refuse to import:
+    there is no CPU or pure-Python fallback."""
+    import shutil
+    import subprocess
+    import sys
+    src = os.path.join(ROOT, "paper_2009_06657_gb300")
+    dst = tmp_path / "paper_2009_06657_gb300"
+    dst.mkdir()
+    for f in os.listdir(src):
+        if f.endswith(".py"):
+            shutil.copy(os.path.join(src, f), dst / f)
+    p = subprocess.run([sys.executable, "-c", "import paper_2009_06657_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=300,
+                       env={**os.environ, "PYTHONPATH": str(tmp_path)})
+    assert p.returncode != 0
+    assert "ImportError" in p.stderr and "liblret.so" in p.stderr
+
+
 def test_launch_counter_reads_without_device(lib):
     n = lib.lib.lr_launch_count()
     assert isinstance(n, int) and n >= 0
