@@ -137,6 +137,45 @@ def test_pauli_expectation_matches_dense_kron():
     assert abs(s.expect([(1.0, [(0, "Y")])]) - 1.0) < 1e-15
 
 
+def test_z_expect_matches_dense_kron_on_every_qubit():
+    # <Z_q> from Prob(x) (Eq. 9 weighted by (-1)^{x_q}) against Tr(Z_q rho) with Z_q a
+    # dense Kronecker product, on a random unnormalised low-rank state
+    rng = np.random.default_rng(21)
+    n = 5
+    L = rng.normal(size=(2 ** n, 3)) + 1j * rng.normal(size=(2 ** n, 3))
+    st = O.LRETState(n)
+    st.L = L
+    rho = L @ L.conj().T
+    z = st.z_expect()
+    assert z.shape == (n,)
+    for q in range(n):
+        ref = np.real(np.trace(kron_pauli(n, [(q, "Z")]) @ rho))
+        assert abs(z[q] - ref) < 1e-11
+        assert abs(z[q] - st.expect([(1.0, [(q, "Z")])])) < 1e-11
+    assert abs(st.trace() - np.real(np.trace(rho))) < 1e-11
+
+
+def test_z_expect_closed_forms_on_product_states():
+    # Ry(t_q) on every qubit, a depolarizing channel on qubit 1 and amplitude damping on
+    # the top qubit: <Z_q> = cos t_q, (1 - 4p/3) cos t_1 on qubit 1, and for the damped
+    # qubit (1 - g) (cos t - 1) + 1 = cos t + g (1 - cos t). An X on qubit 2 flips its
+    # sign. A wrong bit index or sign in the readout fails one of these.
+    n, p, g = 4, 0.05, 0.3
+    t = np.array([0.3, 1.1, 2.0, 0.8])
+    st = O.LRETState(n)
+    for q in range(n):
+        st.gate([q], O.rotation("Y", t[q]))
+    st.gate([2], O.PAULI["X"])
+    st.channel(1, O.depolarizing(p))
+    st.channel(n - 1, O.amplitude_damping(g))
+    expect = np.cos(t)
+    expect[1] *= 1 - 4 * p / 3
+    expect[2] *= -1.0
+    expect[n - 1] = np.cos(t[n - 1]) + g * (1 - np.cos(t[n - 1]))
+    assert np.max(np.abs(st.z_expect() - expect)) < 1e-14
+    assert abs(st.trace() - 1.0) < 1e-14
+
+
 # ---- exact evolution (Eq. 1) ----------------------------------------------
 
 def test_fdm_trace_positivity_and_sv():
