@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t mbar[TC_NS];   // slot free again: the MMAs that read it are done
   __shared__ __align__(8) uint64_t mfull[TC_NS];  // slot staged by all TC_SW threads
+  __shared__ __align__(8) uint64_t mdrain;        // every MMA issued by this CTA has completed
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int NR = 4 * c;               // real columns
   const int nacc = NR > 128 ? 2 : 1;  // 128-row accumulator blocks
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(smem_u32(&mbar[s]), 1);
       mbar_init(smem_u32(&mfull[s]), TC_SW);
     }
+    mbar_init(smem_u32(&mdrain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == TC_SW / 32) {
     // ---- MMA issue: chunk ch once all staging threads have stored it
     if (lane == 0) {
+      int issued = 0;
       for (int ch = 0; ch < nchunks && ok; ++ch) {
         const int s = ch % TC_NS;
         ok = mbar_wait(smem_u32(&mfull[s]), (uint32_t)((ch / TC_NS) & 1));
@@ -135,6 +138,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
         commit(smem_u32(&mbar[s]));
+        issued = ch + 1;
+      }
+      // whether or not a wait gave up, no MMA may still write tensor memory when
+      // it is freed: one more commit tracks all of them (bounded wait)
+      if (issued > 0) {
+        commit(smem_u32(&mdrain));
+        if (!mbar_wait(smem_u32(&mdrain), 0u)) ok = false;
       }
     }
     ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;

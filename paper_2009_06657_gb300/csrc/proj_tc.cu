@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
   float* stage = (float*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t mbar_mma[PT_NS], mbar_b[PT_NS], mfull[PT_NS];
+  __shared__ __align__(8) uint64_t mdrain;  // every MMA issued by this CTA has completed
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = 4 * c, N = 4 * k;
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       mbar_init(smem_u32(&mbar_b[s]), 1);
       mbar_init(smem_u32(&mfull[s]), PT_AW);
     }
+    mbar_init(smem_u32(&mdrain), 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
     // ---- MMA issue: chunk ch once its rows are staged and its D_r chunk landed
     if (lane == 0) {
       bool ok = true;
+      int issued = 0;
       for (int ch = 0; ch < nchunks && ok; ++ch) {
         const int s = ch % PT_NS;
         ok = mbar_wait(smem_u32(&mfull[s]), (uint32_t)((ch / PT_NS) & 1)) &&
@@ -177,6 +180,13 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
           }
         }
         commit(smem_u32(&mbar_mma[s]));
+        issued = ch + 1;
+      }
+      // whether or not a wait gave up, no MMA may still write tensor memory when
+      // it is freed: one more commit tracks all of them (bounded wait)
+      if (issued > 0) {
+        commit(smem_u32(&mdrain));
+        if (!mbar_wait(smem_u32(&mdrain), 0u)) ok = false;
       }
       if (!ok) s_fail = 1;
     }
