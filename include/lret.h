@@ -167,6 +167,23 @@ int lr_set_eps(lr_handle h, double eps);
 #define LR_EIG_CLUSTER 3
 int lr_set_eigensolver(lr_handle h, int which);
 
+/* Arithmetic of the truncation's eigensolve (Sec. II.B) for an LR_C64 state
+ * (an LR_C128 state always solves in FP64 and ignores this setting).
+ * LR_EIGP_REFINED (default): the solver runs in FP32 and returns every
+ * eigenvector, then `iters` steps of an FP64 refinement of the kept ones on the
+ * FP64 Gram matrix: residual G X - X diag(mu) in FP64, mu the FP64 Rayleigh
+ * quotients; its components along the FP32 discarded eigenvectors divided by
+ * the eigenvalue differences; first-order re-orthonormalisation of the kept
+ * set. The kept eigenvalues become the FP64 Rayleigh quotients and the
+ * discarded mass trace(G) minus their sum. iters: 1..4 (2 by default; values
+ * outside are clamped).
+ * LR_EIGP_FP32: the FP32 solve alone (kept vectors and eigenvalues to FP32
+ * accuracy). LR_EIGP_FP64: the solver itself in FP64 arithmetic. */
+#define LR_EIGP_REFINED 0
+#define LR_EIGP_FP32 1
+#define LR_EIGP_FP64 2
+int lr_set_eig_precision(lr_handle h, int mode, int iters);
+
 /* Prob(x) = sum_v |V_xv|^2 (Eq. 9) into a caller-owned device buffer of 2^n
  * floats (LR_C64) or doubles (LR_C128). Asynchronous. */
 int lr_probs(lr_handle h, void* out_dev);
@@ -226,9 +243,8 @@ int64_t lr_device_bytes(lr_handle h);
 
 /* Allocation-free <H> for callers that cannot allocate device memory when they
  * read out (a server that reserved all device memory for its own pool up front,
- * code running while a CUDA graph capture is open on the device, or a thread
- * that must not take the device-wide synchronisation cudaMalloc/cudaFree
- * imply). The paper has no counterpart: this is an interface variant of
+ * or a thread that must not take the device-wide synchronisation that
+ * cudaMalloc/cudaFree imply). The paper has no counterpart: this is an interface variant of
  * lr_expect that computes the same sum_t coeff_t Tr(V^dag P_t V).
  *
  * V_dev: caller-owned device state, 2^n x c complex (row-major, leading

@@ -9,7 +9,6 @@
 //
 // Some callers cannot allocate device memory at the time they need a readout:
 // a serving loop that has reserved all device memory up front for its own pool,
-// code running while another component captures the device into a CUDA graph,
 // or a host thread that must not take the implicit device synchronisation that
 // cudaMalloc / cudaFree imply. This entry point reads a caller-owned device
 // state and keeps its scratch (term masks and per-block partial sums) in a

@@ -1,9 +1,8 @@
 """The allocation-free expectation entry point, lr_expect_static.
 
 It serves callers that cannot allocate device memory when they read out: a
-server that reserved all device memory for its own pool, code running while a
-CUDA graph capture is open on the device, or a thread that must not take the
-device-wide synchronisation of cudaMalloc/cudaFree. Its scratch is a fixed
+server that reserved all device memory for its own pool, or a thread that must
+not take the device-wide synchronisation of cudaMalloc/cudaFree. Its scratch is a fixed
 device array inside the library. This file is named to be collected last.
 """
 import ctypes as C
