@@ -238,6 +238,16 @@ int lr_get_state(lr_handle h, void* out_host);
  * six entries, unused ones 0). Synchronises. */
 int lr_last_eig_stats(lr_handle h, int* sweeps_out, long long* cycles_out);
 
+/* The last truncation's eigenproblem, for inspection: *m_out receives the Gram
+ * matrix size m (0 before the first truncation) and *k_out the kept count; G_out
+ * (m x m complex, row-major), evals_out (m doubles, descending) and evecs_out
+ * (m x m complex, row-major, column i = eigenvector i) receive the FP64 Gram
+ * matrix the eigensolver read and its output (after any refinement; with
+ * LR_EIGP_REFINED the kept columns and eigenvalues are refined, the others are
+ * the FP32 solver's). Each array pointer may be NULL; host buffers of at least
+ * 256 x 256 complex (evals: 256) always suffice. Synchronises. */
+int lr_last_eig(lr_handle h, int* m_out, int* k_out, double* G_out, double* evals_out, double* evecs_out);
+
 /* Upper bound on the device bytes the handle holds (for capacity planning). */
 int64_t lr_device_bytes(lr_handle h);
 
@@ -323,6 +333,7 @@ int lr_batch_free(lr_batch_handle b);
 #define LR_K_SMALL 6    /* small dense products of a truncation: Gram assembly from the
                            pair Gram, pair projection coefficients, deferred-projection
                            products */
+#define LR_K_EIGREFINE 7 /* FP64 refinement of the kept eigenvectors (LR_EIGP_REFINED) */
 #define LR_NKCLASS 8
 
 /* Bracket every forward kernel launch with CUDA events on the handle's stream

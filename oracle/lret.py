@@ -276,6 +276,14 @@ class SVState:
 # Low-rank evolution with eigenvalue truncation (Algorithm 1)
 # --------------------------------------------------------------------------
 
+def gram_eigh(G):
+    """Eigenpairs of the Hermitian Gram matrix of a truncation (Sec. II.B), FP64,
+    eigenvalues descending with the eigenvectors (columns) in the same order."""
+    G = 0.5 * (G + G.conj().T)
+    lam, U = np.linalg.eigh(G)
+    return lam[::-1].copy(), U[:, ::-1].copy()
+
+
 def choose_rank(lam, r=None, eps=None):
     """Number k of leading eigenvalues kept (Sec. II.B).
 
@@ -320,10 +328,7 @@ class LRETState:
     def compress(self, r=None, eps=None):
         L = self.L
         G = L.conj().T @ L
-        G = 0.5 * (G + G.conj().T)
-        lam, U = np.linalg.eigh(G)
-        lam = lam[::-1]
-        U = U[:, ::-1]
+        lam, U = gram_eigh(G)
         k = choose_rank(lam, r=r, eps=eps)
         dropped = float(np.clip(lam[k:], 0.0, None).sum())
         self.L = L @ U[:, :k]

@@ -26,7 +26,10 @@ LR_DEPOLARIZING = 0
 LR_AMPLITUDE_DAMPING = 1
 LR_BIT_FLIP = 2
 LR_STATIC_MAX_TERMS = 256
-KCLASSES = ["expand", "gram", "eigh", "project", "readout", "pauli", "small"]
+KCLASSES = ["expand", "gram", "eigh", "project", "readout", "pauli", "small", "refine"]
+LR_EIGP_REFINED = 0
+LR_EIGP_FP32 = 1
+LR_EIGP_FP64 = 2
 LR_NKCLASS = 8
 
 
@@ -83,6 +86,8 @@ _SIGS = {
     "lr_compress": (C.c_int, [_H, C.c_int, _D]),
     "lr_set_eps": (C.c_int, [_H, C.c_double]),
     "lr_set_eigensolver": (C.c_int, [_H, C.c_int]),
+    "lr_set_eig_precision": (C.c_int, [_H, C.c_int, C.c_int]),
+    "lr_last_eig": (C.c_int, [_H, _I, _I, _D, _D, _D]),
     "lr_set_path": (C.c_int, [_H, C.c_int]),
     "lr_set_tensor_cores": (C.c_int, [_H, C.c_int]),
     "lr_probs": (C.c_int, [_H, _P]),

@@ -1,0 +1,285 @@
+// FP64 refinement of the kept eigenvectors of a truncation (Sec. II.B: rho is
+// cut to the span of the leading eigenvectors of the Gram matrix G = V'^dag V',
+// Theorem 1 of App. B) after an eigensolve in FP32 arithmetic that returned
+// every eigenvector.
+//
+// The truncated rho = V' P V'^dag depends on the kept eigenvectors only through
+// the projector P onto their span, so only the components of the kept vectors
+// along the discarded ones need FP64 accuracy; rotations inside the kept set do
+// not matter, their orthonormality does. One refinement step, in the spirit of
+// Ogita and Aishima's refinement of a symmetric eigendecomposition by matrix
+// products (Japan J. Indust. Appl. Math. 35, 2018), restricted to the kept
+// columns X (m x k) and using the FP32 discarded vectors Xd as the basis of
+// the complement:
+//   W = G X, R = X^dag X                          (FP64; the only FP64 products)
+//   mu_i = Re(x_i^dag w_i) / R_ii                 (Rayleigh quotients)
+//   res_i = w_i - mu_i x_i                        (FP64; small, ~u32 |G|)
+//   e_ji = (xd_j^dag res_i) / (mu_i - lam_j)      (discarded j; FP32 product of
+//                                                  a small residual suffices)
+//   X <- X (I - (R - I) / 2) + Xd E               (first-order orthonormalisation
+//                                                  and the complement correction)
+// A pair whose correction is not small (|e_ji| > 1/2: the two eigenvalues are not
+// separated at the precision of the FP32 solve) is left alone: any basis of a tied
+// cluster is a correct truncation. Each step multiplies the error of the kept
+// subspace by about the FP32 error of the discarded basis over the cut gap; the
+// runtime runs two. The kept eigenvalues become the FP64 Rayleigh quotients and
+// the discarded mass trace(G) - sum of kept eigenvalues (FP64).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lret {
+
+namespace {
+
+constexpr int RT = 16;   // output tile (RT x RT), one output per thread
+constexpr int RK = 32;   // K chunk staged in shared memory
+constexpr int RF_SPLITS_MAX = 8;
+
+// P[s] = [G ; X^dag] X over the K chunk s (rows r < m: G[r][:], rows m + i: conj(X[:, i])).
+__global__ void __launch_bounds__(RT* RT)
+    k_rf_gemm64(const double2* __restrict__ G, int m, const double2* __restrict__ X, int ldx,
+                const EigOut* __restrict__ eo, int kmax, double2* __restrict__ P) {
+  const int k = eo->k < kmax ? eo->k : kmax;
+  const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT, s = blockIdx.z;
+  if (c0 >= k || r0 >= m + k) return;
+  __shared__ double2 As[RT][RK + 1];
+  __shared__ double2 Bs[RK][RT + 1];
+  const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
+  const int kb = s * RK;
+  for (int e = tid; e < RT * RK; e += RT * RT) {
+    const int rr = e / RK, kk = e % RK;
+    const int row = r0 + rr, kg = kb + kk;
+    double2 a = make_double2(0.0, 0.0);
+    if (kg < m) {
+      if (row < m) a = G[(size_t)row * m + kg];
+      else if (row < m + k) a = conjg(X[(size_t)kg * ldx + (row - m)]);
+    }
+    As[rr][kk] = a;
+  }
+  for (int e = tid; e < RK * RT; e += RT * RT) {
+    const int kk = e / RT, cc = e % RT;
+    const int kg = kb + kk, col = c0 + cc;
+    Bs[kk][cc] = (kg < m && col < k) ? X[(size_t)kg * ldx + col] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 8
+  for (int kk = 0; kk < RK; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
+  const int row = r0 + ty, col = c0 + tx;
+  if (row < m + k && col < k) P[((size_t)s * (m + kmax) + row) * kmax + col] = acc;
+}
+
+// One block per kept column i: W[:, i] and R[:, i] from the split partials (fixed
+// order), mu_i, res_i = w_i - mu_i x_i (stored in FP32), R (FP64).
+__global__ void __launch_bounds__(256)
+    k_rf_res(const double2* __restrict__ P, int splits, int m, const double2* __restrict__ X, int ldx,
+             const EigOut* __restrict__ eo, int kmax, double* __restrict__ mu, double2* __restrict__ R,
+             float2* __restrict__ Res) {
+  const int k = eo->k < kmax ? eo->k : kmax;
+  const int i = blockIdx.x;
+  if (i >= k) return;
+  __shared__ double red[32];
+  __shared__ double s_mu;
+  const int t = threadIdx.x;
+  const size_t sstride = (size_t)(m + kmax) * kmax;
+  double2 w = make_double2(0.0, 0.0), x = make_double2(0.0, 0.0);
+  double q = 0.0;
+  if (t < m) {
+    for (int s = 0; s < splits; ++s) w = cadd(w, P[s * sstride + (size_t)t * kmax + i]);
+    x = X[(size_t)t * ldx + i];
+    q = x.x * w.x + x.y * w.y;  // Re(conj(x) w)
+  }
+  if (t < k) {
+    double2 rv = make_double2(0.0, 0.0);
+    for (int s = 0; s < splits; ++s) rv = cadd(rv, P[s * sstride + (size_t)(m + t) * kmax + i]);
+    R[(size_t)t * kmax + i] = rv;
+  }
+  q = block_sum(q, red);
+  if (t == 0) {
+    double nrm = 0.0;
+    for (int s = 0; s < splits; ++s) nrm += P[s * sstride + (size_t)(m + i) * kmax + i].x;
+    const double v = nrm > 0.0 ? q / nrm : 0.0;
+    s_mu = v;
+    mu[i] = v;
+  }
+  __syncthreads();
+  if (t < m) {
+    const double2 rs = csub(w, cscale(x, s_mu));
+    Res[(size_t)t * kmax + i] = make_float2((float)rs.x, (float)rs.y);
+  }
+}
+
+// E (m x k): rows j < k: -(R - I)_ji / 2; rows j >= k: (xd_j^dag res_i) / (mu_i - lam_j),
+// left at zero where that is not small. The products are FP32 (res is small).
+__global__ void __launch_bounds__(RT* RT)
+    k_rf_corr(const double2* __restrict__ Xall, int m, const float2* __restrict__ Res, const double* __restrict__ mu,
+              const double* __restrict__ lam, const double2* __restrict__ R, const EigOut* __restrict__ eo,
+              int kmax, float2* __restrict__ E) {
+  const int k = eo->k < kmax ? eo->k : kmax;
+  const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT;
+  if (c0 >= k || r0 >= m) return;
+  __shared__ float2 As[RT][RK + 1];  // conj(Xall[kg][row])
+  __shared__ float2 Bs[RK][RT + 1];  // Res[kg][col]
+  const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
+  const int row = r0 + ty, col = c0 + tx;
+  const bool need = r0 + RT > k;  // the tile has discarded rows
+  float2 acc = make_float2(0.f, 0.f);
+  if (need) {
+    for (int kb = 0; kb < m; kb += RK) {
+      for (int e = tid; e < RT * RK; e += RT * RT) {
+        const int rr = e % RT, kk = e / RT;
+        const int kg = kb + kk, rw = r0 + rr;
+        float2 a = make_float2(0.f, 0.f);
+        if (kg < m && rw < m) {
+          const double2 v = Xall[(size_t)kg * m + rw];
+          a = make_float2((float)v.x, -(float)v.y);
+        }
+        As[rr][kk] = a;
+      }
+      for (int e = tid; e < RK * RT; e += RT * RT) {
+        const int kk = e / RT, cc = e % RT;
+        const int kg = kb + kk, cl = c0 + cc;
+        Bs[kk][cc] = (kg < m && cl < k) ? Res[(size_t)kg * kmax + cl] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < RK; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
+      __syncthreads();
+    }
+  }
+  if (row >= m || col >= k) return;
+  float2 e = make_float2(0.f, 0.f);
+  if (row < k) {
+    const double2 rv = R[(size_t)row * kmax + col];
+    e = make_float2((float)(-0.5 * (rv.x - (row == col ? 1.0 : 0.0))), (float)(-0.5 * rv.y));
+  } else {
+    const double den = mu[col] - lam[row];
+    if (den != 0.0) {
+      const double ex = (double)acc.x / den, ey = (double)acc.y / den;
+      if (ex * ex + ey * ey <= 0.25) e = make_float2((float)ex, (float)ey);
+    }
+  }
+  E[(size_t)row * kmax + col] = e;
+}
+
+// Xout = Xin + [Xin | Xd] E  (FP32 products accumulated onto the FP64 Xin)
+__global__ void __launch_bounds__(RT* RT)
+    k_rf_update(const double2* __restrict__ Xall, int m, const double2* __restrict__ Xin, int ldi,
+                const float2* __restrict__ E, const EigOut* __restrict__ eo, int kmax, double2* __restrict__ Xout,
+                int ldo) {
+  const int k = eo->k < kmax ? eo->k : kmax;
+  const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT;
+  if (c0 >= k || r0 >= m) return;
+  __shared__ float2 As[RT][RK + 1];  // [Xin | Xd][row][kg]
+  __shared__ float2 Bs[RK][RT + 1];  // E[kg][col]
+  const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int kb = 0; kb < m; kb += RK) {
+    for (int e = tid; e < RT * RK; e += RT * RT) {
+      const int rr = e / RK, kk = e % RK;
+      const int kg = kb + kk, rw = r0 + rr;
+      float2 a = make_float2(0.f, 0.f);
+      if (kg < m && rw < m) {
+        const double2 v = kg < k ? Xin[(size_t)rw * ldi + kg] : Xall[(size_t)rw * m + kg];
+        a = make_float2((float)v.x, (float)v.y);
+      }
+      As[rr][kk] = a;
+    }
+    for (int e = tid; e < RK * RT; e += RT * RT) {
+      const int kk = e / RT, cc = e % RT;
+      const int kg = kb + kk, cl = c0 + cc;
+      Bs[kk][cc] = (kg < m && cl < k) ? E[(size_t)kg * kmax + cl] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < RK; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
+    __syncthreads();
+  }
+  const int row = r0 + ty, col = c0 + tx;
+  if (row < m && col < k) {
+    const double2 x = Xin[(size_t)row * ldi + col];
+    Xout[(size_t)row * ldo + col] = make_double2(x.x + (double)acc.x, x.y + (double)acc.y);
+  }
+}
+
+// kept eigenvalues = Rayleigh quotients (FP64), discarded mass = trace(G) - their sum
+__global__ void __launch_bounds__(256)
+    k_rf_finish(const double* __restrict__ mu, double* __restrict__ evals, int m, EigOut* __restrict__ eo,
+                int kmax) {
+  __shared__ double red[32];
+  const int k = eo->k < kmax ? eo->k : kmax;
+  const int t = threadIdx.x;
+  double v = 0.0;
+  if (t < k) {
+    const double l = mu[t];
+    evals[t] = l;
+    v = l > 0.0 ? l : 0.0;
+  }
+  const double kept = block_sum(v, red);
+  if (t == 0) {
+    const double dropped = eo->trace - kept;
+    eo->kept = kept;
+    eo->dropped = dropped > 0.0 ? dropped : 0.0;
+    if (k < m) {
+      const double l1 = fabs(mu[0]) > 0.0 ? fabs(mu[0]) : 1.0;
+      eo->gap = (mu[k - 1] - evals[k]) / l1;
+    }
+  }
+}
+
+}  // namespace
+
+size_t eig_refine_work_bytes(int m) {
+  const size_t kmax = (size_t)m;
+  return (size_t)RF_SPLITS_MAX * (m + kmax) * kmax * sizeof(double2)  // P
+         + (size_t)m * kmax * sizeof(double2)                           // Xn
+         + (size_t)kmax * kmax * sizeof(double2)                        // R
+         + (size_t)m * kmax * sizeof(float2) * 2                        // Res, E
+         + (size_t)kmax * sizeof(double) + 256;                         // mu
+}
+
+cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* evecs, EigOut* eo, int kmax,
+                              int iters, void* work, cudaStream_t s) {
+  if (m < 2 || m > 256 || kmax < 1 || iters < 1) return cudaErrorInvalidValue;
+  if (kmax > m) kmax = m;
+  const int splits = (m + RK - 1) / RK;
+  char* p = (char*)work;
+  double2* P = (double2*)p;
+  p += (size_t)RF_SPLITS_MAX * (m + m) * m * sizeof(double2);
+  double2* Xn = (double2*)p;
+  p += (size_t)m * m * sizeof(double2);
+  double2* R = (double2*)p;
+  p += (size_t)m * m * sizeof(double2);
+  float2* Res = (float2*)p;
+  p += (size_t)m * m * sizeof(float2);
+  float2* E = (float2*)p;
+  p += (size_t)m * m * sizeof(float2);
+  double* mu = (double*)p;
+  const dim3 tb(RT * RT);
+  const dim3 g64((kmax + RT - 1) / RT, (m + kmax + RT - 1) / RT, splits);
+  const dim3 g32((kmax + RT - 1) / RT, (m + RT - 1) / RT);
+  // iterations alternate between evecs' kept columns and Xn; the last one ends in evecs
+  for (int it = 0; it < iters; ++it) {
+    const bool to_evecs = ((iters - 1 - it) % 2) == 0;
+    const double2* Xin = to_evecs ? Xn : evecs;
+    const int ldi = to_evecs ? kmax : m;
+    double2* Xout = to_evecs ? evecs : Xn;
+    const int ldo = to_evecs ? m : kmax;
+    if (it == 0 && to_evecs) {
+      // an odd number of steps starts from a copy so input and output differ
+      cudaError_t e = cudaMemcpy2DAsync(Xn, kmax * sizeof(double2), evecs, m * sizeof(double2),
+                                        kmax * sizeof(double2), m, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return e;
+    }
+    k_rf_gemm64<<<g64, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, P);
+    k_rf_res<<<kmax, 256, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, mu, R, Res);
+    k_rf_corr<<<g32, tb, 0, s>>>(evecs, m, Res, mu, evals, R, eo, kmax, E);
+    k_rf_update<<<g32, tb, 0, s>>>(evecs, m, Xin, ldi, E, eo, kmax, Xout, ldo);
+    note_launches(4);
+  }
+  k_rf_finish<<<1, 256, 0, s>>>(mu, evals, m, eo, kmax);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace lret

@@ -193,6 +193,14 @@ cudaError_t launch_eigh_cluster(const double2* G, int m, void* work, double* eva
                                 int r, double eps, int all_vecs, cudaStream_t s);
 size_t eigh_cluster_work_bytes(bool fp64);
 
+// ---- FP64 refinement of the kept eigenvectors after an FP32 solve that returned
+// all m eigenvectors (evecs m x m, columns descending; evals m): `iters` steps on
+// the FP64 Gram matrix G, in place on the kept columns (k = eo->k <= kmax), kept
+// eigenvalues and the accounting in *eo rewritten in FP64. work: eig_refine_work_bytes(m).
+cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* evecs, EigOut* eo, int kmax,
+                              int iters, void* work, cudaStream_t s);
+size_t eig_refine_work_bytes(int m);
+
 // ---- adjoint of a truncation: builds Mcat ((k+m) x m complex128) =
 // [U_r^dag ; B + B^dag] with B = U_d (F o (U_d^dag C)) U_r^dag, F_ji = 1/(lam_i - lam_j).
 cudaError_t launch_trunc_adj_small(const double2* C, const double2* U, const double* lam, int m,

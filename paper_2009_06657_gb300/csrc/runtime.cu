@@ -67,7 +67,11 @@ struct lr_ctx {
   int chan_q = 0, chan_K = 0;
   zc chan_M[4][4];
   double eps = 0.0;
-  int solver = 0;  // 0 auto, 1 Jacobi, 2 tridiagonal
+  int solver = 0;  // 0 auto, 1 Jacobi, 2 tridiagonal, 3 cluster
+  int eig_prec = LR_EIGP_REFINED;  // LR_C64: FP32 solve + FP64 refinement, FP32 only, or FP64 solve
+  int eig_iters = 2;
+  void* rf_work = nullptr;         // refinement workspace (allocated on first use)
+  int last_m = 0;                  // size of the last eigenproblem (lr_last_eig)
   int path = 0;    // 0 structured truncation where it applies, 1 always expand V'
   double2* S = nullptr;   // pair Gram (2c x 2c)
   int* tc_status = nullptr;  // set by tensor-core kernels when a bounded wait gives up
@@ -414,27 +418,44 @@ int upload_terms(lr_ctx* h, int T, const uint64_t* xm, const uint64_t* zm, const
 // Eigensolve of the m x m Gram matrix in h->G (Sec. II.B), rank choice, FP64
 // accounting; *k_out receives the kept count (synchronises only for the eps rule).
 int run_eigh(lr_ctx* h, int m, int r_eff, double eps, int* k_out) {
-  const int te = tbeg(h);
-  const bool fp64 = h->dtype == LR_C128;
+  h->last_m = m;
+  int te = tbeg(h);
+  // arithmetic of the solver: FP64 for an FP64 state or when asked; the FP32 solve
+  // of an FP32 state is followed by the FP64 refinement of the kept vectors unless
+  // that is switched off
+  const bool fp64 = h->dtype == LR_C128 || h->eig_prec == LR_EIGP_FP64;
+  const int kmax = r_eff > 0 ? (r_eff < m ? r_eff : m) : m;
+  const bool refine = !fp64 && h->eig_prec == LR_EIGP_REFINED && kmax < m;
+  const int all_vecs = (h->record || refine) ? 1 : 0;
+  const int sdt = fp64 ? LR_C128 : LR_C64;
   const bool small = m <= (fp64 ? 64 : 32);
   const bool use_cluster = h->solver == 3 || (h->solver == 0 && !small);
   const bool use_tri = h->solver == 2;
   if (use_cluster) {
-    CK(by_dtype(h->dtype, [&](auto t) {
+    CK(by_dtype(sdt, [&](auto t) {
       return launch_eigh_cluster<decltype(t)>(h->G, m, h->eig_work, h->evals, h->evecs, h->eo, r_eff, eps,
-                                              h->record ? 1 : 0, h->stream);
+                                              all_vecs, h->stream);
     }));
   } else if (use_tri) {
-    CK(by_dtype(h->dtype, [&](auto t) {
-      return launch_eigh_tri<decltype(t)>(h->G, m, h->eig_work, h->evals, h->evecs, h->eo, r_eff, eps,
-                                          h->record ? 1 : 0, h->stream);
+    CK(by_dtype(sdt, [&](auto t) {
+      return launch_eigh_tri<decltype(t)>(h->G, m, h->eig_work, h->evals, h->evecs, h->eo, r_eff, eps, all_vecs,
+                                          h->stream);
     }));
   } else {
-    CK(by_dtype(h->dtype, [&](auto t) {
+    CK(by_dtype(sdt, [&](auto t) {
       return launch_eigh<decltype(t)>(h->G, m, h->eig_work, h->evals, h->evecs, h->eo, r_eff, eps, h->stream);
     }));
   }
   tend(h, LR_K_EIGH, te);
+  if (refine) {
+    if (!h->rf_work) {
+      int rc = dmalloc(h, &h->rf_work, eig_refine_work_bytes(256));
+      if (rc) return rc;
+    }
+    te = tbeg(h);
+    CK(launch_eig_refine(h->G, m, h->evals, h->evecs, h->eo, kmax, h->eig_iters, h->rf_work, h->stream));
+    tend(h, LR_K_EIGREFINE, te);
+  }
   k_accum<<<1, 1, 0, h->stream>>>(h->eo, h->acc);
   note_launches(1);
   CK(cudaGetLastError());
@@ -829,6 +850,7 @@ int lr_free(lr_handle h) {
   dfree((void*&)h->evecs);
   dfree((void*&)h->eo);
   dfree(h->eig_work);
+  dfree(h->rf_work);
   dfree((void*&)h->acc);
   dfree((void*&)h->dscratch);
   dfree((void*&)h->samp);
@@ -1041,6 +1063,13 @@ int lr_kraus_preset(int kind, double p, double* out, int* K_out) {
 int lr_set_eigensolver(lr_handle h, int which) {
   if (!h || which < 0 || which > 3) return LR_EINVAL;
   h->solver = which;
+  return LR_OK;
+}
+
+int lr_set_eig_precision(lr_handle h, int mode, int iters) {
+  if (!h || mode < LR_EIGP_REFINED || mode > LR_EIGP_FP64) return LR_EINVAL;
+  h->eig_prec = mode;
+  h->eig_iters = iters < 1 ? 1 : (iters > 4 ? 4 : iters);
   return LR_OK;
 }
 
@@ -1386,6 +1415,21 @@ int lr_get_state(lr_handle h, void* out_host) {
 }
 
 int64_t lr_device_bytes(lr_handle h) { return h ? (int64_t)h->bytes : 0; }
+
+int lr_last_eig(lr_handle h, int* m_out, int* k_out, double* G_out, double* evals_out, double* evecs_out) {
+  if (!h || !m_out || !k_out) return LR_EINVAL;
+  const int m = h->last_m;
+  CK(cudaMemcpyAsync(h->h_eo, h->eo, sizeof(EigOut), cudaMemcpyDeviceToHost, h->stream));
+  if (m > 0) {
+    if (G_out) CK(cudaMemcpyAsync(G_out, h->G, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, h->stream));
+    if (evals_out) CK(cudaMemcpyAsync(evals_out, h->evals, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+    if (evecs_out) CK(cudaMemcpyAsync(evecs_out, h->evecs, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  *m_out = m;
+  *k_out = m > 0 ? h->h_eo->k : 0;
+  return LR_OK;
+}
 
 int lr_last_eig_stats(lr_handle h, int* sweeps_out, long long* cycles_out) {
   if (!h || !sweeps_out || !cycles_out) return LR_EINVAL;

@@ -152,6 +152,24 @@ class LRSim:
         check(lib.lr_set_eigensolver(self.h, {"auto": 0, "jacobi": 1, "tridiag": 2, "cluster": 3}[which]),
               "lr_set_eigensolver")
 
+    def set_eig_precision(self, mode, iters=2):
+        """Eigensolve of an FP32 state: "refined" (FP32 solve + FP64 refinement of the
+        kept eigenvectors, `iters` steps; the default), "fp32" or "fp64" (lr_set_eig_precision)."""
+        check(lib.lr_set_eig_precision(self.h, {"refined": 0, "fp32": 1, "fp64": 2}[mode], int(iters)),
+              "lr_set_eig_precision")
+
+    def last_eig(self):
+        """(G, evals, evecs, k) of the last truncation's eigenproblem (lr_last_eig)."""
+        m, k = C.c_int(0), C.c_int(0)
+        G = np.zeros((256, 256), dtype=np.complex128)
+        ev = np.zeros(256, dtype=np.float64)
+        U = np.zeros((256, 256), dtype=np.complex128)
+        check(lib.lr_last_eig(self.h, C.byref(m), C.byref(k), G.ctypes.data_as(C.POINTER(C.c_double)),
+                              _dptr(ev), U.ctypes.data_as(C.POINTER(C.c_double))), "lr_last_eig")
+        mm = m.value
+        return (G.reshape(-1)[: mm * mm].reshape(mm, mm).copy(), ev[:mm].copy(),
+                U.reshape(-1)[: mm * mm].reshape(mm, mm).copy(), k.value)
+
     def set_path(self, which):
         """"auto" (truncate without forming V' where possible) or "expand"."""
         check(lib.lr_set_path(self.h, {"auto": 0, "expand": 1}[which]), "lr_set_path")
