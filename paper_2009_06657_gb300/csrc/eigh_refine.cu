@@ -14,16 +14,23 @@
 //   W = G X, R = X^dag X                          (FP64; the only FP64 products)
 //   mu_i = Re(x_i^dag w_i) / R_ii                 (Rayleigh quotients)
 //   res_i = w_i - mu_i x_i                        (FP64; small, ~u32 |G|)
-//   e_ji = (xd_j^dag res_i) / (mu_i - lam_j)      (discarded j; FP32 product of
-//                                                  a small residual suffices)
+//   e_ji = (xd_j^dag res_i) / (mu_i - lam_j)      (discarded j, lam_j its FP32
+//                                                  eigenvalue; an FP32 product of the
+//                                                  small residual suffices)
 //   X <- X (I - (R - I) / 2) + Xd E               (first-order orthonormalisation
 //                                                  and the complement correction)
-// A pair whose correction is not small (|e_ji| > 1/2: the two eigenvalues are not
-// separated at the precision of the FP32 solve) is left alone: any basis of a tied
-// cluster is a correct truncation. Each step multiplies the error of the kept
-// subspace by about the FP32 error of the discarded basis over the cut gap; the
-// runtime runs two. The kept eigenvalues become the FP64 Rayleigh quotients and
-// the discarded mass trace(G) - sum of kept eigenvalues (FP64).
+// A kept/discarded pair closer than the FP32 solve resolves (|mu_i - lam_j| <=
+// 2^-24 |mu_1|), or whose correction is not small (|e_ji| > 1/2), is left alone:
+// there the FP32 basis cannot tell the two apart (and any basis of a tied cluster
+// is a correct truncation). The FP32 error of
+// the numerators and of the discarded basis makes each step reduce the error of
+// the kept subspace by a factor of about u32 |G| / gap; the runtime runs two.
+// Kept vectors are not rotated among themselves (that leaves rho unchanged), so a
+// kept eigenvalue inside a cluster the FP32 solve did not resolve (spread below
+// about u32 |G|) is the Rayleigh quotient of a vector of that cluster; the sum of
+// the kept eigenvalues, trace(X^dag G X), is accurate in FP64 either way. The kept
+// eigenvalues become the FP64 Rayleigh quotients and the discarded mass
+// trace(G) - their sum.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -109,63 +116,68 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// E (m x k): rows j < k: -(R - I)_ji / 2; rows j >= k: (xd_j^dag res_i) / (mu_i - lam_j),
-// left at zero where that is not small. The products are FP32 (res is small).
+// A = Xall^dag Res (m x k): x_j^dag res_i for every column j of the FP32 solve, an
+// FP32 product (res is small).
 __global__ void __launch_bounds__(RT* RT)
-    k_rf_corr(const double2* __restrict__ Xall, int m, const float2* __restrict__ Res, const double* __restrict__ mu,
-              const double* __restrict__ lam, const double2* __restrict__ R, const EigOut* __restrict__ eo,
-              int kmax, float2* __restrict__ E) {
+    k_rf_proj(const double2* __restrict__ Xall, int m, const float2* __restrict__ Res,
+              const EigOut* __restrict__ eo, int kmax, float2* __restrict__ A) {
   const int k = eo->k < kmax ? eo->k : kmax;
   const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT;
   if (c0 >= k || r0 >= m) return;
   __shared__ float2 As[RT][RK + 1];  // conj(Xall[kg][row])
   __shared__ float2 Bs[RK][RT + 1];  // Res[kg][col]
   const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
-  const int row = r0 + ty, col = c0 + tx;
-  const bool need = r0 + RT > k;  // the tile has discarded rows
   float2 acc = make_float2(0.f, 0.f);
-  if (need) {
-    for (int kb = 0; kb < m; kb += RK) {
-      for (int e = tid; e < RT * RK; e += RT * RT) {
-        const int rr = e % RT, kk = e / RT;
-        const int kg = kb + kk, rw = r0 + rr;
-        float2 a = make_float2(0.f, 0.f);
-        if (kg < m && rw < m) {
-          const double2 v = Xall[(size_t)kg * m + rw];
-          a = make_float2((float)v.x, -(float)v.y);
-        }
-        As[rr][kk] = a;
+  for (int kb = 0; kb < m; kb += RK) {
+    for (int e = tid; e < RT * RK; e += RT * RT) {
+      const int rr = e % RT, kk = e / RT;
+      const int kg = kb + kk, rw = r0 + rr;
+      float2 a = make_float2(0.f, 0.f);
+      if (kg < m && rw < m) {
+        const double2 v = Xall[(size_t)kg * m + rw];
+        a = make_float2((float)v.x, -(float)v.y);
       }
-      for (int e = tid; e < RK * RT; e += RT * RT) {
-        const int kk = e / RT, cc = e % RT;
-        const int kg = kb + kk, cl = c0 + cc;
-        Bs[kk][cc] = (kg < m && cl < k) ? Res[(size_t)kg * kmax + cl] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
+      As[rr][kk] = a;
+    }
+    for (int e = tid; e < RK * RT; e += RT * RT) {
+      const int kk = e / RT, cc = e % RT;
+      const int kg = kb + kk, cl = c0 + cc;
+      Bs[kk][cc] = (kg < m && cl < k) ? Res[(size_t)kg * kmax + cl] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
 #pragma unroll 8
-      for (int kk = 0; kk < RK; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
-      __syncthreads();
-    }
+    for (int kk = 0; kk < RK; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
+    __syncthreads();
   }
-  if (row >= m || col >= k) return;
-  float2 e = make_float2(0.f, 0.f);
-  if (row < k) {
-    const double2 rv = R[(size_t)row * kmax + col];
-    e = make_float2((float)(-0.5 * (rv.x - (row == col ? 1.0 : 0.0))), (float)(-0.5 * rv.y));
-  } else {
-    const double den = mu[col] - lam[row];
-    if (den != 0.0) {
-      const double ex = (double)acc.x / den, ey = (double)acc.y / den;
-      if (ex * ex + ey * ey <= 0.25) e = make_float2((float)ex, (float)ey);
-    }
-  }
-  E[(size_t)row * kmax + col] = e;
+  const int row = r0 + ty, col = c0 + tx;
+  if (row < m && col < k) A[(size_t)row * kmax + col] = acc;
 }
 
-// Xout = Xin + [Xin | Xd] E  (FP32 products accumulated onto the FP64 Xin)
+// e_ji of the update: kept j: the orthonormalising term -(R - I)_ji / 2 (FP64 R);
+// discarded j: x_j^dag res_i / (mu_i - lambda_j) where that is small (|e| <= 1/2).
+__device__ __forceinline__ float2 rf_coef(int j, int i, int k, const float2* __restrict__ A,
+                                          const double* __restrict__ mu, const double* __restrict__ lam,
+                                          const double2* __restrict__ R, int kmax) {
+  if (j < k) {
+    const double2 rv = R[(size_t)j * kmax + i];
+    return make_float2((float)(-0.5 * (rv.x - (j == i ? 1.0 : 0.0))), (float)(-0.5 * rv.y));
+  }
+  // eigenvalue differences within the FP32 solve's resolution (unit roundoff x
+  // lambda_1) are not resolved: there the FP32 basis and numerators are noise
+  const double den = mu[i] - lam[j];
+  if (!(fabs(den) > 5.9604644775390625e-8 * fabs(mu[0]))) return make_float2(0.f, 0.f);
+  const float2 a = A[(size_t)j * kmax + i];
+  const double ex = (double)a.x / den, ey = (double)a.y / den;
+  if (ex * ex + ey * ey > 0.25) return make_float2(0.f, 0.f);
+  return make_float2((float)ex, (float)ey);
+}
+
+// Xout = Xin + [Xin | Xd] E, E formed while staged (rf_coef); FP32 products
+// accumulated onto the FP64 Xin
 __global__ void __launch_bounds__(RT* RT)
     k_rf_update(const double2* __restrict__ Xall, int m, const double2* __restrict__ Xin, int ldi,
-                const float2* __restrict__ E, const EigOut* __restrict__ eo, int kmax, double2* __restrict__ Xout,
+                const float2* __restrict__ A, const double* __restrict__ mu, const double* __restrict__ lam,
+                const double2* __restrict__ R, const EigOut* __restrict__ eo, int kmax, double2* __restrict__ Xout,
                 int ldo) {
   const int k = eo->k < kmax ? eo->k : kmax;
   const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT;
@@ -188,7 +200,7 @@ __global__ void __launch_bounds__(RT* RT)
     for (int e = tid; e < RK * RT; e += RT * RT) {
       const int kk = e / RT, cc = e % RT;
       const int kg = kb + kk, cl = c0 + cc;
-      Bs[kk][cc] = (kg < m && cl < k) ? E[(size_t)kg * kmax + cl] : make_float2(0.f, 0.f);
+      Bs[kk][cc] = (kg < m && cl < k) ? rf_coef(kg, cl, k, A, mu, lam, R, kmax) : make_float2(0.f, 0.f);
     }
     __syncthreads();
 #pragma unroll 8
@@ -234,7 +246,7 @@ size_t eig_refine_work_bytes(int m) {
   return (size_t)RF_SPLITS_MAX * (m + kmax) * kmax * sizeof(double2)  // P
          + (size_t)m * kmax * sizeof(double2)                           // Xn
          + (size_t)kmax * kmax * sizeof(double2)                        // R
-         + (size_t)m * kmax * sizeof(float2) * 2                        // Res, E
+         + (size_t)m * kmax * sizeof(float2) * 2                        // Res, A
          + (size_t)kmax * sizeof(double) + 256;                         // mu
 }
 
@@ -252,7 +264,7 @@ cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* e
   p += (size_t)m * m * sizeof(double2);
   float2* Res = (float2*)p;
   p += (size_t)m * m * sizeof(float2);
-  float2* E = (float2*)p;
+  float2* A = (float2*)p;  // Xall^dag Res
   p += (size_t)m * m * sizeof(float2);
   double* mu = (double*)p;
   const dim3 tb(RT * RT);
@@ -273,8 +285,8 @@ cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* e
     }
     k_rf_gemm64<<<g64, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, P);
     k_rf_res<<<kmax, 256, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, mu, R, Res);
-    k_rf_corr<<<g32, tb, 0, s>>>(evecs, m, Res, mu, evals, R, eo, kmax, E);
-    k_rf_update<<<g32, tb, 0, s>>>(evecs, m, Xin, ldi, E, eo, kmax, Xout, ldo);
+    k_rf_proj<<<g32, tb, 0, s>>>(evecs, m, Res, eo, kmax, A);
+    k_rf_update<<<g32, tb, 0, s>>>(evecs, m, Xin, ldi, A, mu, evals, R, eo, kmax, Xout, ldo);
     note_launches(4);
   }
   k_rf_finish<<<1, 256, 0, s>>>(mu, evals, m, eo, kmax);

@@ -6,7 +6,9 @@ eigenvectors in FP64 (lr_set_eig_precision). Every truncation of a 14-qubit run 
 the benchmark's circuit family (r = 64, 256-column Gram matrices) is read back
 through lr_last_eig and compared with the oracle's eigh of the same FP64 matrix:
 
-* kept eigenvalues to 1e-13 of lambda_1 and the discarded mass to 1e-13 of the trace;
+* the eigenvalues of the kept subspace (of X^dag G X) to 1e-13 of lambda_1, each
+  reported kept eigenvalue to the same up to the spread of an eigenvalue cluster
+  the FP32 solve cannot separate, and the discarded mass to 1e-13 of the trace;
 * the truncated state: rho_trunc = V' P V'^dag depends on the kept vectors only
   through the projector P, and ||V' (P - P0) V'^dag||_F = ||G^(1/2) (P - P0) G^(1/2)||_F,
   held to 1e-12 of the trace (a cut inside an eigenvalue tie, where any kept basis is
@@ -67,28 +69,41 @@ def _cuts(lr, n, r, nchan, mode, iters=2, seed=3000, solver="auto"):
     return out
 
 
+def _cluster_spread(lam, i, width):
+    """Largest distance from lam[i] to an eigenvalue within `width` of it."""
+    d = np.abs(lam - lam[i])
+    d = d[d <= width]
+    return float(d.max()) if d.size else 0.0
+
+
 @pytest.mark.parametrize("solver", ["auto", "tridiag"])
 def test_refined_eigensolve_matches_fp64(lr, solver):
     cuts = _cuts(lr, 14, 64, 16, "refined", solver=solver)
     assert len(cuts) >= 6
-    worst = {"lam": 0.0, "rho": 0.0, "orth": 0.0, "drop": 0.0}
+    rows = []
     for G, ev, U, k, dropped in cuts:
         lam0, U0 = O.gram_eigh(G)
         tr = float(np.real(np.trace(G)))
         l1 = lam0[0]
         gap = (lam0[k - 1] - lam0[k]) / l1
-        tied = 2.0 * lam0[k - 1] if gap < 1e-8 else 0.0
-        e_lam = float(np.max(np.abs(ev[:k] - lam0[:k]))) / l1
-        e_rho = _rho_err(G, U, U0, k)
-        e_orth = float(np.max(np.abs(U[:, :k].conj().T @ U[:, :k] - np.eye(k))))
+        X = U[:, :k]
+        # eigenvalues of the kept subspace (invariant to rotations inside it)
+        kc = np.linalg.eigvalsh(0.5 * ((X.conj().T @ G @ X) + (X.conj().T @ G @ X).conj().T))[::-1]
+        e_sub = float(np.max(np.abs(kc - lam0[:k]))) / l1
+        # each kept eigenvalue, up to the spread of a cluster the FP32 solve cannot resolve
+        e_lam = max(abs(ev[i] - lam0[i]) - _cluster_spread(lam0, i, 1e-6 * l1) for i in range(k)) / l1
+        e_rho = _rho_err(G, U, U0, k) / tr
+        e_orth = float(np.max(np.abs(X.conj().T @ X - np.eye(k))))
         e_drop = abs(dropped - float(np.clip(lam0[k:], 0.0, None).sum())) / tr
-        assert e_lam < 1e-13, e_lam
-        assert e_rho < 1e-12 * tr + tied, (e_rho, gap)
-        assert e_orth < 1e-13, e_orth
-        assert e_drop < 1e-13, e_drop
-        for key, v in (("lam", e_lam), ("rho", e_rho / tr), ("orth", e_orth), ("drop", e_drop)):
-            worst[key] = max(worst[key], v)
-    print("refined eigensolve, worst errors:", worst)
+        tied = 2.0 * lam0[k - 1] / tr if gap < 1e-8 else 0.0
+        rows.append((gap, e_sub, e_lam, e_rho, tied, e_orth, e_drop))
+    for r in rows:
+        print("gap %.1e  kept-subspace eigenvalues %.1e  eigenvalues %.1e  rho %.1e (+tie %.1e)  "
+              "orthonormality %.1e  discarded %.1e" % r)
+    for gap, e_sub, e_lam, e_rho, tied, e_orth, e_drop in rows:
+        assert e_sub < 1e-13 and e_lam < 1e-13
+        assert e_rho < 1e-12 + tied
+        assert e_orth < 1e-13 and e_drop < 1e-13
 
 
 def test_fp32_eigensolve_alone_is_at_fp32_level(lr):
