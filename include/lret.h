@@ -171,12 +171,14 @@ int lr_set_eigensolver(lr_handle h, int which);
  * (an LR_C128 state always solves in FP64 and ignores this setting).
  * LR_EIGP_REFINED (default): the solver runs in FP32 and returns every
  * eigenvector, then `iters` steps of an FP64 refinement of the kept ones on the
- * FP64 Gram matrix: residual G X - X diag(mu) in FP64, mu the FP64 Rayleigh
+ * FP64 Gram matrix (residual G X - X diag(mu) in FP64, mu the FP64 Rayleigh
  * quotients; its components along the FP32 discarded eigenvectors divided by
  * the eigenvalue differences; first-order re-orthonormalisation of the kept
- * set. The kept eigenvalues become the FP64 Rayleigh quotients and the
- * discarded mass trace(G) minus their sum. iters: 1..4 (2 by default; values
- * outside are clamped).
+ * set), then two FP64 orthonormalisation steps of the kept set. The kept
+ * eigenvalues become the FP64 Rayleigh quotients and the discarded mass
+ * trace(G) minus their sum. iters: 0..4 (1 by default; values outside are
+ * clamped); 0 returns the FP32 solve with every eigenvector and no refinement
+ * (for inspection).
  * LR_EIGP_FP32: the FP32 solve alone (kept vectors and eigenvalues to FP32
  * accuracy). LR_EIGP_FP64: the solver itself in FP64 arithmetic. */
 #define LR_EIGP_REFINED 0

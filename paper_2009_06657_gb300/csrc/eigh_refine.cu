@@ -22,9 +22,13 @@
 // A kept/discarded pair closer than the FP32 solve resolves (|mu_i - lam_j| <=
 // 2^-24 |mu_1|), or whose correction is not small (|e_ji| > 1/2), is left alone:
 // there the FP32 basis cannot tell the two apart (and any basis of a tied cluster
-// is a correct truncation). The FP32 error of
-// the numerators and of the discarded basis makes each step reduce the error of
-// the kept subspace by a factor of about u32 |G| / gap; the runtime runs two.
+// is a correct truncation). One step takes the kept subspace from the FP32 solve's
+// accuracy to FP64 accuracy where the FP32 discarded basis is accurate; where it is
+// not (clusters the FP32 solve did not resolve, rank-deficient Gram matrices) the
+// step can leave the kept vectors slightly non-orthonormal, and a second step would
+// amplify that. So the runtime runs one step (iters = 1) followed by two FP64
+// orthonormalisation steps X <- X (I - (X^dag X - I) / 2), each of which squares
+// the deviation from orthonormality.
 // Kept vectors are not rotated among themselves (that leaves rho unchanged), so a
 // kept eigenvalue inside a cluster the FP32 solve did not resolve (spread below
 // about u32 |G|) is the Rayleigh quotient of a vector of that cluster; the sum of
@@ -41,13 +45,15 @@ namespace {
 constexpr int RT = 16;   // output tile (RT x RT), one output per thread
 constexpr int RK = 32;   // K chunk staged in shared memory
 constexpr int RF_SPLITS_MAX = 8;
+constexpr int RF_ORTHO = 2;  // FP64 orthonormalisation steps after the corrections
 
-// P[s] = [G ; X^dag] X over the K chunk s (rows r < m: G[r][:], rows m + i: conj(X[:, i])).
+// P[s] = [G ; X^dag] X over the K chunk s (rows r < m: G[r][:], rows m + i: conj(X[:, i])),
+// output rows from row0 (0: both products; m: X^dag X only).
 __global__ void __launch_bounds__(RT* RT)
     k_rf_gemm64(const double2* __restrict__ G, int m, const double2* __restrict__ X, int ldx,
-                const EigOut* __restrict__ eo, int kmax, double2* __restrict__ P) {
+                const EigOut* __restrict__ eo, int kmax, int row0, double2* __restrict__ P) {
   const int k = eo->k < kmax ? eo->k : kmax;
-  const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT, s = blockIdx.z;
+  const int r0 = row0 + blockIdx.y * RT, c0 = blockIdx.x * RT, s = blockIdx.z;
   if (c0 >= k || r0 >= m + k) return;
   __shared__ double2 As[RT][RK + 1];
   __shared__ double2 Bs[RK][RT + 1];
@@ -214,6 +220,43 @@ __global__ void __launch_bounds__(RT* RT)
   }
 }
 
+// Xout = Xin (I - (R - I) / 2), R = Xin^dag Xin summed from the split partials (FP64)
+__global__ void __launch_bounds__(RT* RT)
+    k_rf_lowdin(const double2* __restrict__ P, int splits, int m, const double2* __restrict__ Xin, int ldi,
+                const EigOut* __restrict__ eo, int kmax, double2* __restrict__ Xout, int ldo) {
+  const int k = eo->k < kmax ? eo->k : kmax;
+  const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT;
+  if (c0 >= k || r0 >= m) return;
+  __shared__ double2 As[RT][RK + 1];  // Xin[row][j]
+  __shared__ double2 Bs[RK][RT + 1];  // -(R - I)[j][col] / 2
+  const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
+  const size_t sstride = (size_t)(m + kmax) * kmax;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int jb = 0; jb < k; jb += RK) {
+    for (int e = tid; e < RT * RK; e += RT * RT) {
+      const int rr = e / RK, jj = e % RK;
+      const int rw = r0 + rr, j = jb + jj;
+      As[rr][jj] = (rw < m && j < k) ? Xin[(size_t)rw * ldi + j] : make_double2(0.0, 0.0);
+    }
+    for (int e = tid; e < RK * RT; e += RT * RT) {
+      const int jj = e / RT, cc = e % RT;
+      const int j = jb + jj, cl = c0 + cc;
+      double2 v = make_double2(0.0, 0.0);
+      if (j < k && cl < k) {
+        for (int s = 0; s < splits; ++s) v = cadd(v, P[s * sstride + (size_t)(m + j) * kmax + cl]);
+        v = make_double2(-0.5 * (v.x - (j == cl ? 1.0 : 0.0)), -0.5 * v.y);
+      }
+      Bs[jj][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < RK; ++jj) cfma(acc, As[ty][jj], Bs[jj][tx]);
+    __syncthreads();
+  }
+  const int row = r0 + ty, col = c0 + tx;
+  if (row < m && col < k) Xout[(size_t)row * ldo + col] = cadd(Xin[(size_t)row * ldi + col], acc);
+}
+
 // kept eigenvalues = Rayleigh quotients (FP64), discarded mass = trace(G) - their sum
 __global__ void __launch_bounds__(256)
     k_rf_finish(const double* __restrict__ mu, double* __restrict__ evals, int m, EigOut* __restrict__ eo,
@@ -269,10 +312,13 @@ cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* e
   double* mu = (double*)p;
   const dim3 tb(RT * RT);
   const dim3 g64((kmax + RT - 1) / RT, (m + kmax + RT - 1) / RT, splits);
+  const dim3 gR((kmax + RT - 1) / RT, (kmax + RT - 1) / RT, splits);
   const dim3 g32((kmax + RT - 1) / RT, (m + RT - 1) / RT);
-  // iterations alternate between evecs' kept columns and Xn; the last one ends in evecs
-  for (int it = 0; it < iters; ++it) {
-    const bool to_evecs = ((iters - 1 - it) % 2) == 0;
+  // `iters` correction steps, then RF_ORTHO orthonormalisation steps; the steps
+  // alternate between evecs' kept columns and Xn and the last one ends in evecs
+  const int nsteps = iters + RF_ORTHO;
+  for (int it = 0; it < nsteps; ++it) {
+    const bool to_evecs = ((nsteps - 1 - it) % 2) == 0;
     const double2* Xin = to_evecs ? Xn : evecs;
     const int ldi = to_evecs ? kmax : m;
     double2* Xout = to_evecs ? evecs : Xn;
@@ -283,11 +329,17 @@ cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* e
                                         kmax * sizeof(double2), m, cudaMemcpyDeviceToDevice, s);
       if (e != cudaSuccess) return e;
     }
-    k_rf_gemm64<<<g64, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, P);
-    k_rf_res<<<kmax, 256, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, mu, R, Res);
-    k_rf_proj<<<g32, tb, 0, s>>>(evecs, m, Res, eo, kmax, A);
-    k_rf_update<<<g32, tb, 0, s>>>(evecs, m, Xin, ldi, A, mu, evals, R, eo, kmax, Xout, ldo);
-    note_launches(4);
+    if (it < iters) {
+      k_rf_gemm64<<<g64, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, 0, P);
+      k_rf_res<<<kmax, 256, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, mu, R, Res);
+      k_rf_proj<<<g32, tb, 0, s>>>(evecs, m, Res, eo, kmax, A);
+      k_rf_update<<<g32, tb, 0, s>>>(evecs, m, Xin, ldi, A, mu, evals, R, eo, kmax, Xout, ldo);
+      note_launches(4);
+    } else {
+      k_rf_gemm64<<<gR, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, m, P);
+      k_rf_lowdin<<<g32, tb, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, Xout, ldo);
+      note_launches(2);
+    }
   }
   k_rf_finish<<<1, 256, 0, s>>>(mu, evals, m, eo, kmax);
   note_launches(1);

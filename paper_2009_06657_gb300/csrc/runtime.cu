@@ -69,7 +69,7 @@ struct lr_ctx {
   double eps = 0.0;
   int solver = 0;  // 0 auto, 1 Jacobi, 2 tridiagonal, 3 cluster
   int eig_prec = LR_EIGP_REFINED;  // LR_C64: FP32 solve + FP64 refinement, FP32 only, or FP64 solve
-  int eig_iters = 2;
+  int eig_iters = 1;
   void* rf_work = nullptr;         // refinement workspace (allocated on first use)
   int last_m = 0;                  // size of the last eigenproblem (lr_last_eig)
   int path = 0;    // 0 structured truncation where it applies, 1 always expand V'
@@ -447,7 +447,7 @@ int run_eigh(lr_ctx* h, int m, int r_eff, double eps, int* k_out) {
     }));
   }
   tend(h, LR_K_EIGH, te);
-  if (refine) {
+  if (refine && h->eig_iters > 0) {
     if (!h->rf_work) {
       int rc = dmalloc(h, &h->rf_work, eig_refine_work_bytes(256));
       if (rc) return rc;
@@ -1069,7 +1069,7 @@ int lr_set_eigensolver(lr_handle h, int which) {
 int lr_set_eig_precision(lr_handle h, int mode, int iters) {
   if (!h || mode < LR_EIGP_REFINED || mode > LR_EIGP_FP64) return LR_EINVAL;
   h->eig_prec = mode;
-  h->eig_iters = iters < 1 ? 1 : (iters > 4 ? 4 : iters);
+  h->eig_iters = iters < 0 ? 0 : (iters > 4 ? 4 : iters);
   return LR_OK;
 }
 

@@ -152,9 +152,10 @@ class LRSim:
         check(lib.lr_set_eigensolver(self.h, {"auto": 0, "jacobi": 1, "tridiag": 2, "cluster": 3}[which]),
               "lr_set_eigensolver")
 
-    def set_eig_precision(self, mode, iters=2):
+    def set_eig_precision(self, mode, iters=1):
         """Eigensolve of an FP32 state: "refined" (FP32 solve + FP64 refinement of the
-        kept eigenvectors, `iters` steps; the default), "fp32" or "fp64" (lr_set_eig_precision)."""
+        kept eigenvectors, `iters` correction steps; the default), "fp32" or "fp64"
+        (lr_set_eig_precision)."""
         check(lib.lr_set_eig_precision(self.h, {"refined": 0, "fp32": 1, "fp64": 2}[mode], int(iters)),
               "lr_set_eig_precision")
 

@@ -11,8 +11,9 @@ through lr_last_eig and compared with the oracle's eigh of the same FP64 matrix:
   the FP32 solve cannot separate, and the discarded mass to 1e-13 of the trace;
 * the truncated state: rho_trunc = V' P V'^dag depends on the kept vectors only
   through the projector P, and ||V' (P - P0) V'^dag||_F = ||G^(1/2) (P - P0) G^(1/2)||_F,
-  held to 1e-12 of the trace (a cut inside an eigenvalue tie, where any kept basis is
-  a correct truncation, adds twice the tied eigenvalue);
+  held to 1e-12 of the trace where the cut gap exceeds 1e-6 of lambda_1 and to 1e-9
+  below it (a cut inside an eigenvalue tie, where any kept basis is a correct
+  truncation, adds twice the tied eigenvalue);
 * orthonormality of the kept vectors to 1e-13.
 The FP32 solve alone is checked to be at its own level on the same matrices, so the
 refinement is what reaches the FP64 bounds.
@@ -69,6 +70,13 @@ def _cuts(lr, n, r, nchan, mode, iters=2, seed=3000, solver="auto"):
     return out
 
 
+# Relative cut gap below which the FP32 solve's discarded basis does not separate the
+# kept and discarded eigenvectors well enough for one correction step to reach FP64
+# accuracy (its eigenvalues carry errors of order 2^-24 lambda_1 times a small
+# factor); there the refined state is held to 1e-9 of the trace instead of 1e-12.
+FP32_RES = 1e-6
+
+
 def _cluster_spread(lam, i, width):
     """Largest distance from lam[i] to an eigenvalue within `width` of it."""
     d = np.abs(lam - lam[i])
@@ -102,7 +110,7 @@ def test_refined_eigensolve_matches_fp64(lr, solver):
               "orthonormality %.1e  discarded %.1e" % r)
     for gap, e_sub, e_lam, e_rho, tied, e_orth, e_drop in rows:
         assert e_sub < 1e-13 and e_lam < 1e-13
-        assert e_rho < 1e-12 + tied
+        assert e_rho < (1e-12 if gap > FP32_RES else 1e-9) + tied
         assert e_orth < 1e-13 and e_drop < 1e-13
 
 
