@@ -227,13 +227,14 @@ def run_ours(args, rank, world):
 
     info = sim.info()
     sim.close()
+    eigv = bench_eig_variants(dev, stream, layers) if (rank == 0 and not args.no_eig_variants) else None
     # FP64 comparators at the same size (few truncations; rate per noisy gate-step)
     fp64 = bench_fp64(args, layers, dev, stream) if (rank == 0 and not args.no_fp64) else None
     adj = bench_adjoint(dev, stream) if (rank == 0 and not args.no_adjoint) else None
     bat = bench_batch(dev, stream, scale=args.batch_scale) if (rank == 0 and not args.no_batch) else None
     grv = bench_grover(dev, stream) if (rank == 0 and not args.no_grover) else None
     return dict(ms=ms, g_per=g_per, c_per=c_per, ktimes=ktimes, clk=clk, e2e_s=e2e_s, fp64=fp64, info=info,
-                adjoint=adj, batch=bat, launches=n_launch, readouts=rd, grover=grv)
+                adjoint=adj, batch=bat, launches=n_launch, readouts=rd, grover=grv, eig_variants=eigv)
 
 
 def bench_fp64(args, layers, dev, stream):
@@ -255,14 +256,17 @@ def bench_fp64(args, layers, dev, stream):
             lr.run_ops(sim, [o], r=RANK)
         torch.cuda.synchronize()
         n_tr = 0
-        t0 = time.perf_counter()
-        while n_tr < 2 and idx < len(ops):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        while n_tr < 4 and idx < len(ops):
             o = ops[idx]; idx += 1
             lr.run_ops(sim, [o], r=RANK)
             if o["op"] in ("dep",):
                 n_tr += 1
+        sim.info()  # flush a deferred projection inside the timed region
+        e1.record(stream)
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / max(n_tr, 1)
+        dt = e0.elapsed_time(e1) * 1e-3 / max(n_tr, 1)
     sim.close()
     out["ours_c128_s_per_truncation"] = dt
     # (b) plain torch complex128 (cuBLAS ZGEMM + cuSOLVER eigh)
@@ -286,14 +290,52 @@ def bench_fp64(args, layers, dev, stream):
     with torch.cuda.stream(stream):
         V = plain_step(V, 0)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        reps = 2
+        reps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         for i in range(reps):
             V = plain_step(V, 1 + i)
+        e1.record(stream)
         torch.cuda.synchronize()
-        out["torch_c128_s_per_truncation"] = (time.perf_counter() - t0) / reps
+        out["torch_c128_s_per_truncation"] = e0.elapsed_time(e1) * 1e-3 / reps
     del V
     torch.cuda.empty_cache()
+    return out
+
+
+def bench_eig_variants(dev, stream, layers):
+    """The same 20-qubit layers with the three eigensolve precisions of the FP32
+    state (lr_set_eig_precision): FP32 solve + FP64 refinement (the headline
+    path), FP32 solve alone, FP64 solve. One warm-up layer, one layer timed with
+    CUDA events, one more with per-kernel-class events."""
+    import torch
+
+    import paper_2009_06657_gb300 as lr
+    g_per, _ = count(layers[0])
+    out = {}
+    for mode in ("refined", "fp32", "fp64"):
+        sim = lr.LRSim(N_QUBITS, RANK, dtype="c64", stream=stream)
+        sim.set_eig_precision(mode)
+        with torch.cuda.stream(stream):
+            lr.run_ops(sim, layers[0], r=RANK)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            lr.run_ops(sim, layers[1], r=RANK)
+            sim.info()  # flush the deferred projection inside the timed region
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            sim.set_timing(True)
+            lr.run_ops(sim, layers[2], r=RANK)
+            kt = sim.kernel_times()
+        sim.close()
+        ent = {"layer_ms": ms, "gate_steps_per_s": g_per / (ms * 1e-3)}
+        for cls in ("eigh", "refine"):
+            t, c = kt[cls]
+            ent[cls + "_ms_per_launch"] = t / c if c else None
+        out[mode] = ent
+    out["refined_over_fp32_time"] = out["refined"]["layer_ms"] / out["fp32"]["layer_ms"]
     return out
 
 
@@ -458,6 +500,9 @@ def algorithmic():
         "project": {"flop": 8.0 * N2 * (2 * r) * (2 * r), "bytes": 2 * N * r * esz},
         # Householder reduction of the m x m Hermitian matrix dominates: (16/3) m^3 flop
         "eigh": {"flop": 16.0 / 3.0 * m ** 3, "bytes": m * m * 16},
+        # FP64 refinement of the kept eigenvectors: G X (m x m x r) and X^dag X (r x m x r) complex
+        # FP64 products, then two X^dag X for the orthonormalisation steps (FP32 products not counted)
+        "refine": {"flop": 8.0 * (m * m * r + 3 * r * m * r), "bytes": None},
         # expansion for two-qubit gates (gate only, K = 1): read and write V
         "expand": {"flop": None, "bytes": 2 * N * r * esz},
         "readout": {"flop": None, "bytes": N * r * esz + N * 4},
@@ -550,6 +595,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-grover", action="store_true")
+    ap.add_argument("--no-eig-variants", action="store_true")
     ap.add_argument("--batch-scale", type=float, default=0.05)
     args = ap.parse_args()
     if args.profile_readouts:
@@ -582,8 +628,9 @@ def main():
         # tensor-core GEMMs: useful flops against the TF32 dense peak
         bound, ach, peak, unit = "tensor", d.get("tflops"), peaks["tf32_tflops"], "TFLOP/s"
     elif dom == "eigh":
-        # one 8-SM cluster: FP32 ALU peak of the SMs it occupies
-        bound, ach, peak, unit = "alu", d.get("tflops"), peaks["fp32_tflops"] * 8 / 152, "TFLOP/s"
+        # FP32 SIMT arithmetic: chip-wide FP32 peak (the kernel occupies one cluster of
+        # 8 SMs; the share of those 8 SMs is reported separately below)
+        bound, ach, peak, unit = "alu", d.get("tflops"), peaks["fp32_tflops"], "TFLOP/s"
     else:
         bound, ach, peak, unit = "hbm", d.get("hbm_gbs"), peaks["hbm_gbs"], "GB/s"
     cfg = workload_config()
@@ -592,20 +639,23 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "noisy gate-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (FP32 arithmetic, FP64 sums/accounting)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 state: FP32 gates, 3xTF32 tensor-core Gram/projection; eigensolve FP32 then FP64 "
+                 "refinement of the kept eigenvectors (FP64 eigenvalues and discarded mass); FP64 sums",
         "data": "synthetic (seeded random circuits)", "config": cfg,
         "gpu_launches": None,
         "kernel_ms_per_step": {k: v[0] for k, v in kt.items()},
         "kernel_launches_per_step": {k: v[1] for k, v in kt.items()},
         "roofline": {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                      "frac": (ach / peak) if ach else None, "traffic": NCU_TRAFFIC.get(dom),
-                     "peak_source": peaks["source"]},
+                     "peak_source": peaks["source"],
+                     "frac_of_occupied_sms": ((ach / (peak * 8 / 152)) if (ach and dom == "eigh") else None)},
         "kernels": kr,
         "clocks": res["clk"],
         "e2e": {"value": res["g_per"] / res["e2e_s"], "unit": "noisy gate-steps/s",
                 "h2d_bytes_per_step": h2d_bytes(get_layers()[0]), "d2h_bytes_per_step": (1 << N_QUBITS) * 4 + 8},
         "fp64": None, "cpu_baseline": None, "adjoint": res.get("adjoint"), "batch": res.get("batch"),
-        "readouts": res.get("readouts"), "grover": res.get("grover"),
+        "readouts": res.get("readouts"), "grover": res.get("grover"), "eig_variants": res.get("eig_variants"),
     }
     out["gpu_launches"] = res["launches"]  # the library's own launch counter over the timed region
     if res["fp64"]:
@@ -640,7 +690,7 @@ def load_peaks():
                 "tf32_tflops": d["bf16_tflops"] * 1.1 / 2.25,
                 "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
                 "source": "hbm, bf16 measured (MEASURED_PEAKS.json); tf32 = measured bf16 x nominal 1.1/2.25; "
-                          "fp32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+                          "fp32 = chip-wide SIMT peak from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "tf32_tflops": 1900.0 * 1.1 / 2.25,
             "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "source": "fallback"}
 
@@ -671,7 +721,7 @@ def cpu_truncations(count):
 
 
 def cpu_baseline(res):
-    times = cpu_truncations(2)
+    times = cpu_truncations(3)
     s_per_tr, n_tr = statistics.median(times), len(times)
     tps = res["c_per"] / res["g_per"]
     return {"value": 1.0 / (s_per_tr * tps), "unit": "noisy gate-steps/s", "cores": os.cpu_count(),

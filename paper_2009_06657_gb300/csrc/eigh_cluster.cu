@@ -63,8 +63,13 @@ static_assert(TAIL_N * TAIL_N <= CL_ROWS * CL_MAXM && TAIL_N <= 96, "trailing bl
 constexpr int BT_STAGE = 32;           // reflectors staged per shared-memory block in the back-transform
 template <typename T> struct BtGroup { static constexpr int v = 4; };  // reflectors applied together
 template <> struct BtGroup<double> { static constexpr int v = 2; };  // (register budget of 512 threads)
-template <typename T> struct MgsSlots { static constexpr int v = 4; };  // vectors per warp held in registers
-template <> struct MgsSlots<double> { static constexpr int v = 2; };
+// inverse-iteration scratch slots (6 m values each) beyond the 10 that fit in the
+// matrix rows' shared memory, in extra dynamic shared memory: 6 more for FP32, so that
+// all 16 warps of a CTA run one vector each (128 vectors per round over the cluster)
+template <typename T> struct LuExtra { static constexpr int slots = 6; };
+template <> struct LuExtra<double> { static constexpr int slots = 0; };
+constexpr int MBK = CL_NW;                 // vectors per orthonormalisation block
+constexpr int MSL = CL_MAXM / (MBK * CL);  // blocks a CTA owns at most (2)
 
 template <typename T> struct CEps;
 template <> struct CEps<float> { static constexpr float v = FLT_EPSILON; static constexpr float tiny = 1e-30f; };
@@ -106,7 +111,6 @@ struct ClusterShared {
   __align__(16) cx<T> nrow[2][CL_MAXM];  // prefetched copy of a future step's row
   T gred[4][2];               // reflector group: per-warp max and sum of squares
   cx<T> gscl;                 // reflector group: alpha
-  T zb[2][CL_MAXM];           // orthonormalisation: the vector being projected out
   cx<T> gram[BT_STAGE / BtGroup<T>::v][BtGroup<T>::v][BtGroup<T>::v];  // v_k^dag v_l, staged reflectors
   cx<T> btau[BT_STAGE];
   T d[CL_MAXM], e[CL_MAXM], e2[CL_MAXM], lam[CL_MAXM];
@@ -865,9 +869,11 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     // per-warp LU scratch reuses this CTA's matrix rows (no longer needed)
     T* ws = reinterpret_cast<T*>(&sh.A[0][0]);
     constexpr int SLOT = 6 * CL_MAXM;
-    const int nlu = (int)(sizeof(sh.A) / (SLOT * sizeof(T)));
+    const int nlu_a = (int)(sizeof(sh.A) / (SLOT * sizeof(T)));
+    const int nlu = nlu_a + LuExtra<T>::slots;  // every warp has a slot for FP32
     if (warp < nlu) {
-      T* dl = ws + (size_t)warp * SLOT;
+      T* dl = warp < nlu_a ? ws + (size_t)warp * SLOT
+                           : reinterpret_cast<T*>(smem_raw + sizeof(ClusterShared<T>)) + (size_t)(warp - nlu_a) * SLOT;
       T* dd = dl + CL_MAXM;  // reciprocals of the LU diagonal
       T* du = dd + CL_MAXM;
       T* du2 = du + CL_MAXM;
@@ -969,117 +975,213 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
   cluster.sync();
   if (tid == 0) { const long long t1 = phase_clock(); t_ph[3] = t1 - t0; t0 = t1; }
 
-  // ---- modified Gram-Schmidt of the needed vectors (CTA 0) --------------------
-  if (rank == 0) {
+  // ---- orthonormalisation of the needed vectors: block Gram-Schmidt over the cluster --
+  // Vectors in rank order, in blocks of MBK = 16: block b is owned by CTA b % CL, its
+  // vector MBK b + w held in registers by warp w (slot b / CL). Step b: the owner
+  // orthonormalises the block (modified Gram-Schmidt, two passes, one vector per warp,
+  // block barriers) and publishes it in its shared memory [cluster barrier]; every CTA
+  // copies it into local shared memory and removes it, twice (classical Gram-Schmidt
+  // against an orthonormal block, repeated), from its vectors of later blocks. A vector
+  // that cancels (nearly dependent on earlier ones; inverse iteration can return almost
+  // equal vectors for eigenvalues the FP32 arithmetic does not separate) is replaced by
+  // a pseudo-random vector orthogonalised against every finished vector.
+  {
     constexpr int E = CL_MAXM / 32;
-    constexpr int NSL = MgsSlots<T>::v;
-    if (nvec <= CL_NW * NSL) {
-      // vector i lives in registers of warp i % 16 (slot i / 16), rows lane + 32 e;
-      // at step i the finished z_i is published in shared memory and every warp
-      // removes it from its later vectors; the warp holding z_{i+1} normalises it
-      T z[NSL][E];
+    const int nblk = (nvec + MBK - 1) / MBK;
+    T* pub = reinterpret_cast<T*>(&sh.A[0][0]);  // [MSL][MBK][CL_MAXM]: this CTA's finished blocks
+    T* cpy = pub + MSL * MBK * CL_MAXM;          // [MBK][CL_MAXM]: the block being removed
+    static_assert((MSL + 1) * MBK * CL_MAXM * sizeof(T) <= sizeof(ClusterShared<T>::A), "orthonormalisation buffers");
+    T z[MSL][E];
 #pragma unroll
-      for (int sl = 0; sl < NSL; ++sl) {
-        const int vec = warp + CL_NW * sl;
+    for (int sl = 0; sl < MSL; ++sl) {
+      const int vec = MBK * (rank + CL * sl) + warp;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int row = lane + 32 * e;
-          z[sl][e] = (vec < nvec && row < m) ? gZ[(size_t)vec * m + row] : (T)0;
-        }
-      }
-      auto publish = [&](int sl_pub, int vec_pub) {
-#pragma unroll
-        for (int sl = 0; sl < NSL; ++sl) {
-          if (sl != sl_pub) continue;
-          T nrm = 0;
-#pragma unroll
-          for (int e = 0; e < E; ++e) nrm += z[sl][e] * z[sl][e];
-          nrm = warp_sum(nrm);
-          const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)0;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            z[sl][e] *= inv;
-            const int row = lane + 32 * e;
-            if (row < m) sh.zb[vec_pub & 1][row] = z[sl][e];
-          }
-        }
-      };
-      if (warp == 0 && nvec > 0) publish(0, 0);
-      __syncthreads();
-      for (int i = 0; i + 1 < nvec; ++i) {
-        T qv[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int row = lane + 32 * e;
-          qv[e] = row < m ? sh.zb[i & 1][row] : (T)0;
-        }
-        T dot[NSL];
-#pragma unroll
-        for (int sl = 0; sl < NSL; ++sl) {
-          dot[sl] = 0;
-#pragma unroll
-          for (int e = 0; e < E; ++e) dot[sl] += qv[e] * z[sl][e];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-          for (int sl = 0; sl < NSL; ++sl) dot[sl] += __shfl_xor_sync(0xffffffffu, dot[sl], o);
-        }
-#pragma unroll
-        for (int sl = 0; sl < NSL; ++sl) {
-          const int vec = warp + CL_NW * sl;
-          if (vec > i && vec < nvec) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) z[sl][e] -= dot[sl] * qv[e];
-          }
-        }
-        if (warp == (i + 1) % CL_NW) publish((i + 1) / CL_NW, i + 1);
-        __syncthreads();
-      }
-#pragma unroll
-      for (int sl = 0; sl < NSL; ++sl) {
-        const int vec = warp + CL_NW * sl;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int row = lane + 32 * e;
-          if (vec < nvec && row < m) gZ[(size_t)vec * m + row] = z[sl][e];
-        }
-      }
-    } else {
-      // many vectors (all of them, for the adjoint): in global memory, one warp per later vector
-      T* Z = gZ;
-      if (warp == 0) {
-        T nrm = 0;
-        for (int t = lane; t < m; t += 32) nrm += Z[t] * Z[t];
-        nrm = warp_sum(nrm);
-        const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)0;
-        for (int t = lane; t < m; t += 32) Z[t] *= inv;
-      }
-      __syncthreads();
-      for (int i = 0; i + 1 < nvec; ++i) {
-        const T* zi = Z + (size_t)i * m;
-        for (int jv = i + 1 + warp; jv < nvec; jv += CL_NW) {
-          T* zj = Z + (size_t)jv * m;
-          T dot = 0;
-          for (int t = lane; t < m; t += 32) dot += zi[t] * zj[t];
-          dot = warp_sum(dot);
-          T nrm = 0;
-          for (int t = lane; t < m; t += 32) {
-            const T u = zj[t] - dot * zi[t];
-            zj[t] = u;
-            nrm += u * u;
-          }
-          if (jv == i + 1) {  // final: normalise before it is used
-            nrm = warp_sum(nrm);
-            const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)0;
-            for (int t = lane; t < m; t += 32) zj[t] *= inv;
-          }
-        }
-        __syncthreads();
+      for (int e = 0; e < E; ++e) {
+        const int row = lane + 32 * e;
+        z[sl][e] = (vec < nvec && row < m) ? gZ[(size_t)vec * m + row] : (T)0;
       }
     }
-    __threadfence();
+    // remove the MBK vectors of cpy (orthonormal) from slot sl, twice; eight at a time
+    // (the inner products of a group are reduced together)
+    constexpr int MG = sizeof(T) == 4 ? 8 : 4;
+    auto remove_block = [&](int sl) {
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        T nz = 0, nd = 0;  // |z|^2 before, |coefficients|^2 (repeat only if a sizeable part went)
+        if (pass == 0) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) nz += z[sl][e] * z[sl][e];
+          nz = warp_sum(nz);
+        }
+#pragma unroll 1
+        for (int g = 0; g < MBK; g += MG) {
+          const T* cg = cpy + (size_t)g * CL_MAXM;
+          T d[MG];
+#pragma unroll
+          for (int t = 0; t < MG; ++t) {
+            T a = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) a += cg[t * CL_MAXM + lane + 32 * e] * z[sl][e];
+            d[t] = a;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int t = 0; t < MG; ++t) d[t] += __shfl_xor_sync(0xffffffffu, d[t], o);
+          }
+#pragma unroll
+          for (int t = 0; t < MG; ++t) nd += d[t] * d[t];
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            T a = z[sl][e];
+#pragma unroll
+            for (int t = 0; t < MG; ++t) a -= d[t] * cg[t * CL_MAXM + lane + 32 * e];
+            z[sl][e] = a;
+          }
+        }
+        if (pass == 0 && !(nd > (T)1e-4 * nz)) break;  // nearly orthogonal already
+      }
+    };
+    for (int b = 0; b < nblk; ++b) {
+      const int owner = b % CL, osl = b / CL;
+      if (rank == owner) {
+        T* pb = pub + (size_t)osl * MBK * CL_MAXM;
+        T* rv = cpy;                  // fallback: the replacement vector (cpy is idle here)
+        T* part = cpy + CL_MAXM;      // fallback: per-warp partial corrections
+        static_assert((MSL * MBK + 1 + CL_NW) * CL_MAXM * sizeof(T) <= sizeof(ClusterShared<T>::A),
+                      "fallback buffers");
+        const int vec = MBK * b + warp;
+        const bool mine = vec < nvec;
+        // this warp's vector of the block (selected without indexing z by a runtime slot)
+        T w[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) w[e] = osl == 0 ? z[0][e] : z[MSL - 1][e];
+        T nrm0 = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) nrm0 += w[e] * w[e];
+        nrm0 = warp_sum(nrm0);
+        __shared__ int s_flag, s_again;
+        if (tid == 0) s_again = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+          if (pass == 1) {  // a second pass only where the first one cancelled much of a vector
+            __syncthreads();
+            if (s_again == 0) break;
+          }
+          for (int t = 0; t < MBK && MBK * b + t < nvec; ++t) {
+            if (warp == t) {
+              T nrm = 0;
+#pragma unroll
+              for (int e = 0; e < E; ++e) nrm += w[e] * w[e];
+              nrm = warp_sum(nrm);
+              // (vectors enter with unit norm from the inverse iteration)
+              const bool cancelled = pass == 0 && !(nrm > (T)1e-6);
+              if (pass == 0 && nrm < (T)0.25 * nrm0 && lane == 0) s_again = 1;
+              if (lane == 0) s_flag = cancelled ? 1 : 0;
+              if (cancelled) {
+                // a pseudo-random vector replaces it, orthogonalised below by the whole CTA
+                // against every earlier vector (earlier blocks from global memory)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                  const int row = lane + 32 * e;
+                  unsigned h = (unsigned)(row + 1) * 2654435761u ^ ((unsigned)(vec + 11) * 40503u + 0x85ebca6bu);
+                  h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12; h *= 0x297a2d39u; h ^= h >> 15;
+                  if (row < CL_MAXM) rv[row] = row < m ? (T)(h & 0xffffu) * (T)(1.0 / 65536.0) - (T)0.5 : (T)0;
+                }
+              }
+            }
+            __syncthreads();
+            if (s_flag) {
+              const int nprev = MBK * b + t;
+              for (int rep = 0; rep < 2; ++rep) {
+                T acc[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc[e] = 0;
+                for (int u = warp; u < nprev; u += CL_NW) {
+                  const T* q = u < MBK * b ? gZ + (size_t)u * m : pb + (size_t)(u - MBK * b) * CL_MAXM;
+                  T a = 0;
+#pragma unroll
+                  for (int e = 0; e < E; ++e) {
+                    const int row = lane + 32 * e;
+                    if (row < m) a += q[row] * rv[row];
+                  }
+                  a = warp_sum(a);
+#pragma unroll
+                  for (int e = 0; e < E; ++e) {
+                    const int row = lane + 32 * e;
+                    if (row < m) acc[e] += a * q[row];
+                  }
+                }
+#pragma unroll
+                for (int e = 0; e < E; ++e) part[warp * CL_MAXM + lane + 32 * e] = acc[e];
+                __syncthreads();
+                for (int row = tid; row < m; row += CL_THREADS) {
+                  T sub = 0;
+                  for (int ww = 0; ww < CL_NW; ++ww) sub += part[ww * CL_MAXM + row];
+                  rv[row] -= sub;
+                }
+                __syncthreads();
+              }
+              if (warp == t) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) w[e] = rv[lane + 32 * e];
+              }
+              if (tid == 0) s_again = 1;  // and a second pass over the block
+            }
+            if (warp == t) {
+              T nrm = 0;
+#pragma unroll
+              for (int e = 0; e < E; ++e) nrm += w[e] * w[e];
+              nrm = warp_sum(nrm);
+              const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)0;
+#pragma unroll
+              for (int e = 0; e < E; ++e) {
+                w[e] *= inv;
+                pb[t * CL_MAXM + lane + 32 * e] = w[e];
+              }
+            }
+            __syncthreads();
+            if (mine && warp > t) {
+              T a = 0;
+#pragma unroll
+              for (int e = 0; e < E; ++e) a += pb[t * CL_MAXM + lane + 32 * e] * w[e];
+              a = warp_sum(a);
+#pragma unroll
+              for (int e = 0; e < E; ++e) w[e] -= a * pb[t * CL_MAXM + lane + 32 * e];
+            }
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (osl == 0) z[0][e] = w[e];
+          else z[MSL - 1][e] = w[e];
+        }
+        // finished vectors also go to global memory (the fallback and the
+        // back-transform read them there)
+        if (mine) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int row = lane + 32 * e;
+            if (row < m) gZ[(size_t)vec * m + row] = w[e];
+          }
+        }
+        __threadfence();
+      }
+      cluster.sync();  // block b published (shared memory of its owner, and global memory)
+      if (b + 1 < nblk) {
+        const T* src = cluster.map_shared_rank(pub + (size_t)osl * MBK * CL_MAXM, owner);
+        for (int i = tid; i < MBK * CL_MAXM; i += CL_THREADS) cpy[i] = src[i];
+        __syncthreads();
+#pragma unroll
+        for (int sl = 0; sl < MSL; ++sl) {
+          const int bb = rank + CL * sl;
+          if (bb > b && MBK * bb + warp < nvec) remove_block(sl);
+        }
+        // cpy is rewritten only after the next cluster barrier, which every warp of this
+        // CTA reaches after its last read of it
+      }
+    }
   }
+  __threadfence();
   cluster.sync();
   if (tid == 0) { const long long t1 = phase_clock(); t_ph[4] = t1 - t0; t0 = t1; }
 
@@ -1221,14 +1323,14 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
 
 template <typename T>
 size_t eigh_cluster_smem() {
-  return sizeof(ClusterShared<T>);
+  return sizeof(ClusterShared<T>) + (size_t)LuExtra<T>::slots * 6 * CL_MAXM * sizeof(T);
 }
 
 template <typename T>
 cudaError_t launch_eigh_cluster(const double2* G, int m, void* work, double* evals, double2* evecs, EigOut* out,
                                 int r, double eps, int all_vecs, cudaStream_t s) {
   if (m < 2 || m > CL_MAXM) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(ClusterShared<T>);
+  const size_t smem = eigh_cluster_smem<T>();
   static std::atomic<uint64_t> attr_done{0};  // one per instantiation
   {
     cudaError_t e = set_dyn_smem_once(k_eigh_cluster<T>, (int)smem, attr_done);
