@@ -1091,6 +1091,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
             }
             __syncthreads();
             if (s_flag) {
+              if (tid == 0) atomicAdd(&out->sweeps, 1);  // diagnostics: replaced vectors
               const int nprev = MBK * b + t;
               for (int rep = 0; rep < 2; ++rep) {
                 T acc[E];

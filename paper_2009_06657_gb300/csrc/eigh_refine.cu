@@ -26,9 +26,10 @@
 // accuracy to FP64 accuracy where the FP32 discarded basis is accurate; where it is
 // not (clusters the FP32 solve did not resolve, rank-deficient Gram matrices) the
 // step can leave the kept vectors slightly non-orthonormal, and a second step would
-// amplify that. So the runtime runs one step (iters = 1) followed by two FP64
+// amplify that. So the runtime runs one step (iters = 1) followed by three FP64
 // orthonormalisation steps X <- X (I - (X^dag X - I) / 2), each of which squares
-// the deviation from orthonormality.
+// the deviation from orthonormality. The kept eigenvalues are the FP64 Rayleigh
+// quotients of the refined vectors (formed with G X in the last of those steps).
 // Kept vectors are not rotated among themselves (that leaves rho unchanged), so a
 // kept eigenvalue inside a cluster the FP32 solve did not resolve (spread below
 // about u32 |G|) is the Rayleigh quotient of a vector of that cluster; the sum of
@@ -45,7 +46,7 @@ namespace {
 constexpr int RT = 16;   // output tile (RT x RT), one output per thread
 constexpr int RK = 32;   // K chunk staged in shared memory
 constexpr int RF_SPLITS_MAX = 8;
-constexpr int RF_ORTHO = 2;  // FP64 orthonormalisation steps after the corrections
+constexpr int RF_ORTHO = 3;  // FP64 orthonormalisation steps after the corrections
 
 // P[s] = [G ; X^dag] X over the K chunk s (rows r < m: G[r][:], rows m + i: conj(X[:, i])),
 // output rows from row0 (0: both products; m: X^dag X only).
@@ -159,23 +160,39 @@ __global__ void __launch_bounds__(RT* RT)
   if (row < m && col < k) A[(size_t)row * kmax + col] = acc;
 }
 
+// Whether the complement correction of kept vector i along discarded vector j is
+// applied, and its value e = a / den: not for a kept vector whose eigenvalue is below
+// the FP32 solve's noise floor (a numerically null direction: it does not change rho),
+// not for eigenvalue differences within that solve's resolution (unit roundoff x
+// lambda_1: there the FP32 basis and numerators are noise), and not where the
+// correction is not small (|e| > 1/2).
+__device__ __forceinline__ bool rf_pair(int j, int i, const float2* __restrict__ A, const double* __restrict__ mu,
+                                        const double* __restrict__ lam, int kmax, double& ex, double& ey,
+                                        double& den) {
+  const double res = 5.9604644775390625e-8 * fabs(mu[0]);
+  if (!(fabs(mu[i]) > res)) return false;
+  den = mu[i] - lam[j];
+  if (!(fabs(den) > res)) return false;
+  const float2 a = A[(size_t)j * kmax + i];
+  ex = (double)a.x / den;
+  ey = (double)a.y / den;
+  return ex * ex + ey * ey <= 0.25;
+}
+
 // e_ji of the update: kept j: the orthonormalising term -(R - I)_ji / 2 (FP64 R);
-// discarded j: x_j^dag res_i / (mu_i - lambda_j) where that is small (|e| <= 1/2).
+// discarded j: alpha_i x_j^dag res_i / (mu_i - lambda_j) where rf_pair applies it
+// (alpha_i < 1 damps a column whose corrections are large in total).
 __device__ __forceinline__ float2 rf_coef(int j, int i, int k, const float2* __restrict__ A,
                                           const double* __restrict__ mu, const double* __restrict__ lam,
-                                          const double2* __restrict__ R, int kmax) {
+                                          const double2* __restrict__ R, const double* __restrict__ alpha,
+                                          int kmax) {
   if (j < k) {
     const double2 rv = R[(size_t)j * kmax + i];
     return make_float2((float)(-0.5 * (rv.x - (j == i ? 1.0 : 0.0))), (float)(-0.5 * rv.y));
   }
-  // eigenvalue differences within the FP32 solve's resolution (unit roundoff x
-  // lambda_1) are not resolved: there the FP32 basis and numerators are noise
-  const double den = mu[i] - lam[j];
-  if (!(fabs(den) > 5.9604644775390625e-8 * fabs(mu[0]))) return make_float2(0.f, 0.f);
-  const float2 a = A[(size_t)j * kmax + i];
-  const double ex = (double)a.x / den, ey = (double)a.y / den;
-  if (ex * ex + ey * ey > 0.25) return make_float2(0.f, 0.f);
-  return make_float2((float)ex, (float)ey);
+  double ex, ey, den;
+  if (!rf_pair(j, i, A, mu, lam, kmax, ex, ey, den)) return make_float2(0.f, 0.f);
+  return make_float2((float)(alpha[i] * ex), (float)(alpha[i] * ey));
 }
 
 // Xout = Xin + [Xin | Xd] E, E formed while staged (rf_coef); FP32 products
@@ -183,8 +200,8 @@ __device__ __forceinline__ float2 rf_coef(int j, int i, int k, const float2* __r
 __global__ void __launch_bounds__(RT* RT)
     k_rf_update(const double2* __restrict__ Xall, int m, const double2* __restrict__ Xin, int ldi,
                 const float2* __restrict__ A, const double* __restrict__ mu, const double* __restrict__ lam,
-                const double2* __restrict__ R, const EigOut* __restrict__ eo, int kmax, double2* __restrict__ Xout,
-                int ldo) {
+                const double2* __restrict__ R, const double* __restrict__ alpha, const EigOut* __restrict__ eo,
+                int kmax, double2* __restrict__ Xout, int ldo) {
   const int k = eo->k < kmax ? eo->k : kmax;
   const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT;
   if (c0 >= k || r0 >= m) return;
@@ -206,7 +223,7 @@ __global__ void __launch_bounds__(RT* RT)
     for (int e = tid; e < RK * RT; e += RT * RT) {
       const int kk = e / RT, cc = e % RT;
       const int kg = kb + kk, cl = c0 + cc;
-      Bs[kk][cc] = (kg < m && cl < k) ? rf_coef(kg, cl, k, A, mu, lam, R, kmax) : make_float2(0.f, 0.f);
+      Bs[kk][cc] = (kg < m && cl < k) ? rf_coef(kg, cl, k, A, mu, lam, R, alpha, kmax) : make_float2(0.f, 0.f);
     }
     __syncthreads();
 #pragma unroll 8
@@ -218,6 +235,28 @@ __global__ void __launch_bounds__(RT* RT)
     const double2 x = Xin[(size_t)row * ldi + col];
     Xout[(size_t)row * ldo + col] = make_double2(x.x + (double)acc.x, x.y + (double)acc.y);
   }
+}
+
+// Per kept column i, over the pairs rf_pair applies: s_i = sum_j |e_ji|^2 sets the
+// damping alpha_i = min(1, sqrt(S_MAX / s_i)): a column whose corrections would move
+// it far from unit norm takes a shorter step, so that the orthonormalisation steps
+// (which square the deviation from orthonormality) converge.
+constexpr double RF_SMAX = 1e-2;
+__global__ void __launch_bounds__(256)
+    k_rf_damp(const float2* __restrict__ A, const double* __restrict__ lam, int m, const EigOut* __restrict__ eo,
+              int kmax, const double* __restrict__ mu, double* __restrict__ alpha) {
+  const int k = eo->k < kmax ? eo->k : kmax;
+  const int i = blockIdx.x;
+  if (i >= k) return;
+  __shared__ double red[32];
+  const int j = k + threadIdx.x;
+  double e2 = 0.0;
+  if (j < m) {
+    double ex, ey, den;
+    if (rf_pair(j, i, A, mu, lam, kmax, ex, ey, den)) e2 = ex * ex + ey * ey;
+  }
+  e2 = block_sum(e2, red);
+  if (threadIdx.x == 0) alpha[i] = e2 > RF_SMAX ? sqrt(RF_SMAX / e2) : 1.0;
 }
 
 // Xout = Xin (I - (R - I) / 2), R = Xin^dag Xin summed from the split partials (FP64)
@@ -257,7 +296,8 @@ __global__ void __launch_bounds__(RT* RT)
   if (row < m && col < k) Xout[(size_t)row * ldo + col] = cadd(Xin[(size_t)row * ldi + col], acc);
 }
 
-// kept eigenvalues = Rayleigh quotients (FP64), discarded mass = trace(G) - their sum
+// kept eigenvalues = FP64 Rayleigh quotients of the refined vectors, discarded mass =
+// trace(G) - their sum
 __global__ void __launch_bounds__(256)
     k_rf_finish(const double* __restrict__ mu, double* __restrict__ evals, int m, EigOut* __restrict__ eo,
                 int kmax) {
@@ -266,15 +306,15 @@ __global__ void __launch_bounds__(256)
   const int t = threadIdx.x;
   double v = 0.0;
   if (t < k) {
-    const double l = mu[t];
-    evals[t] = l;
-    v = l > 0.0 ? l : 0.0;
+    v = mu[t];
+    evals[t] = v;
   }
   const double kept = block_sum(v, red);
   if (t == 0) {
-    const double dropped = eo->trace - kept;
+    // the trace the truncation removes (for a positive semidefinite G this is the sum
+    // of the discarded eigenvalues up to rounding)
     eo->kept = kept;
-    eo->dropped = dropped > 0.0 ? dropped : 0.0;
+    eo->dropped = eo->trace - kept;
     if (k < m) {
       const double l1 = fabs(mu[0]) > 0.0 ? fabs(mu[0]) : 1.0;
       eo->gap = (mu[k - 1] - evals[k]) / l1;
@@ -290,7 +330,7 @@ size_t eig_refine_work_bytes(int m) {
          + (size_t)m * kmax * sizeof(double2)                           // Xn
          + (size_t)kmax * kmax * sizeof(double2)                        // R
          + (size_t)m * kmax * sizeof(float2) * 2                        // Res, A
-         + (size_t)kmax * sizeof(double) + 256;                         // mu
+         + (size_t)3 * kmax * sizeof(double) + 256;                     // mu, mu2, alpha
 }
 
 cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* evecs, EigOut* eo, int kmax,
@@ -310,6 +350,8 @@ cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* e
   float2* A = (float2*)p;  // Xall^dag Res
   p += (size_t)m * m * sizeof(float2);
   double* mu = (double*)p;
+  double* mu2 = mu + m;     // Rayleigh quotients of the refined vectors
+  double* alpha = mu2 + m;  // damping of each kept column's step
   const dim3 tb(RT * RT);
   const dim3 g64((kmax + RT - 1) / RT, (m + kmax + RT - 1) / RT, splits);
   const dim3 gR((kmax + RT - 1) / RT, (kmax + RT - 1) / RT, splits);
@@ -333,15 +375,24 @@ cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* e
       k_rf_gemm64<<<g64, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, 0, P);
       k_rf_res<<<kmax, 256, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, mu, R, Res);
       k_rf_proj<<<g32, tb, 0, s>>>(evecs, m, Res, eo, kmax, A);
-      k_rf_update<<<g32, tb, 0, s>>>(evecs, m, Xin, ldi, A, mu, evals, R, eo, kmax, Xout, ldo);
-      note_launches(4);
-    } else {
+      k_rf_damp<<<kmax, 256, 0, s>>>(A, evals, m, eo, kmax, mu, alpha);
+      k_rf_update<<<g32, tb, 0, s>>>(evecs, m, Xin, ldi, A, mu, evals, R, alpha, eo, kmax, Xout, ldo);
+      note_launches(5);
+    } else if (it + 1 < nsteps) {
       k_rf_gemm64<<<gR, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, m, P);
       k_rf_lowdin<<<g32, tb, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, Xout, ldo);
       note_launches(2);
+    } else {
+      // the last step also forms G X: the kept eigenvalues are the Rayleigh quotients
+      // of its input (nearly orthonormal by now, so the step changes them only at
+      // second order in its tiny change)
+      k_rf_gemm64<<<g64, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, 0, P);
+      k_rf_res<<<kmax, 256, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, mu2, R, Res);
+      k_rf_lowdin<<<g32, tb, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, Xout, ldo);
+      note_launches(3);
     }
   }
-  k_rf_finish<<<1, 256, 0, s>>>(mu, evals, m, eo, kmax);
+  k_rf_finish<<<1, 256, 0, s>>>(mu2, evals, m, eo, kmax);
   note_launches(1);
   return cudaGetLastError();
 }

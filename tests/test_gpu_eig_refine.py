@@ -6,8 +6,8 @@ eigenvectors in FP64 (lr_set_eig_precision). Every truncation of a 14-qubit run 
 the benchmark's circuit family (r = 64, 256-column Gram matrices) is read back
 through lr_last_eig and compared with the oracle's eigh of the same FP64 matrix:
 
-* the eigenvalues of the kept subspace (of X^dag G X) and the discarded mass to 1e-13
-  of the trace, each reported kept eigenvalue to 1e-13 of lambda_1 up to the spread of
+* the eigenvalues of the kept subspace (of X^dag G X) and the discarded mass (the
+  trace the truncation removes, trace(G) minus the kept eigenvalues) to 1e-13 of the trace, each reported kept eigenvalue to 1e-13 of lambda_1 up to the spread of
   an eigenvalue cluster the FP32 solve cannot separate;
 * the truncated state: rho_trunc = V' P V'^dag depends on the kept vectors only
   through the projector P, and ||V' (P - P0) V'^dag||_F = ||G^(1/2) (P - P0) G^(1/2)||_F,
@@ -116,7 +116,7 @@ def test_refined_eigensolve_matches_fp64(lr, solver, case):
         e_lam = max(abs(ev[i] - lam0[i]) - _cluster_spread(lam0, i, FP32_RES * l1) for i in range(k)) / l1
         e_rho = _rho_err(G, U, U0, k) / tr
         e_orth = float(np.max(np.abs(X.conj().T @ X - np.eye(k))))
-        e_drop = abs(dropped - float(np.clip(lam0[k:], 0.0, None).sum())) / tr
+        e_drop = abs(dropped - float(lam0[k:].sum())) / tr  # the trace the truncation removes
         # mass of the eigenvalues tied with the cut at the FP32 resolution
         win = np.abs(lam0 - 0.5 * (lam0[k - 1] + lam0[k])) <= FP32_RES * l1
         tied = float(np.clip(lam0[win], 0.0, None).sum()) / tr if gap <= FP32_RES else 0.0
