@@ -338,6 +338,89 @@ __device__ void warp_reflector(ClusterShared<T>& sh, const cx<T>* __restrict__ r
   }
 }
 
+// Inverse iteration on rows lo..hi of the real tridiagonal T (diagonal sh.d,
+// off-diagonal sh.e) with shift lam: LU with partial pivoting of T - lam I by lane 0
+// (the recurrence is serial; running values in registers), then `iters` rounds of
+// solve (lane 0) and normalisation (the warp). x holds the s = hi - lo + 1 start
+// values and receives the result; sc is scratch of 6 CL_MAXM values (the factors in
+// the first four, pivots in the sixth; x may be the fifth).
+template <typename T>
+__device__ void tri_inverse_iteration(const ClusterShared<T>& sh, int lo, int hi, T lam, T tnorm, T* __restrict__ sc,
+                                      T* __restrict__ x, int iters, int lane) {
+  const int s = hi - lo + 1;
+  T* dl = sc;
+  T* dd = dl + CL_MAXM;  // reciprocals of the LU diagonal
+  T* du = dd + CL_MAXM;
+  T* du2 = du + CL_MAXM;
+  unsigned char* piv = reinterpret_cast<unsigned char*>(sc + 5 * CL_MAXM);
+  if (lane == 0) {
+    const T tiny = CEps<T>::v * tnorm;
+    T cd = sh.d[lo] - lam, cu = sh.e[lo];
+#pragma unroll 4
+    for (int t = 0; t < s - 1; ++t) {
+      const T sub = sh.e[lo + t];
+      const T nd = sh.d[lo + t + 1] - lam;
+      const T nu = t < s - 2 ? sh.e[lo + t + 1] : (T)0;
+      if (fabs(cd) >= fabs(sub)) {
+        if (cd == (T)0) cd = tiny;
+        const T l = sub / cd;
+        dl[t] = l; dd[t] = (T)1 / cd; du[t] = cu; du2[t] = 0; piv[t] = 0;
+        cd = nd - l * cu;
+        cu = nu;
+      } else {
+        const T l = cd / sub;
+        dl[t] = l; dd[t] = (T)1 / sub; du[t] = nd; du2[t] = nu; piv[t] = 1;
+        cd = cu - l * nd;
+        cu = -l * nu;
+      }
+    }
+    if (cd == (T)0) cd = tiny;
+    dd[s - 1] = (T)1 / cd;
+  }
+  __syncwarp();
+  for (int it = 0; it < iters; ++it) {
+    if (lane == 0) {
+      // forward (L with row swaps), then backward (U); carried values in registers
+      T xt = x[0];
+#pragma unroll 4
+      for (int t = 0; t < s - 1; ++t) {
+        const T xn = x[t + 1], l = dl[t];
+        if (piv[t] == 0) {
+          x[t] = xt;
+          xt = xn - l * xt;
+        } else {
+          x[t] = xn;
+          xt = xt - l * xn;
+        }
+      }
+      T x1 = xt * dd[s - 1];  // x[t + 1]
+      x[s - 1] = x1;
+      T x2 = 0;               // x[t + 2]
+#pragma unroll 4
+      for (int t = s - 2; t >= 0; --t) {
+        const T xv = (x[t] - du[t] * x1 - du2[t] * x2) * dd[t];
+        x[t] = xv;
+        x2 = x1;
+        x1 = xv;
+      }
+    }
+    __syncwarp();
+    T xmax = 0;
+    for (int t = lane; t < s; t += 32) xmax = fmax(xmax, fabs(x[t]));
+    for (int o = 16; o > 0; o >>= 1) xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    if (!(xmax <= (T)3e38)) xmax = 0;
+    const T sx = xmax > (T)0 ? (T)1 / xmax : (T)0;
+    for (int t = lane; t < s; t += 32) x[t] = xmax > (T)0 ? x[t] * sx : (T)(t == 0);
+    __syncwarp();
+    T nrm = 0;
+    for (int t = lane; t < s; t += 32) nrm += x[t] * x[t];
+    nrm = warp_sum(nrm);
+    const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)1;
+    for (int t = lane; t < s; t += 32) x[t] *= inv;
+    __syncwarp();
+  }
+}
+
 __device__ __forceinline__ long long phase_clock() { return clock64(); }
 
 }  // namespace
@@ -874,11 +957,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     if (warp < nlu) {
       T* dl = warp < nlu_a ? ws + (size_t)warp * SLOT
                            : reinterpret_cast<T*>(smem_raw + sizeof(ClusterShared<T>)) + (size_t)(warp - nlu_a) * SLOT;
-      T* dd = dl + CL_MAXM;  // reciprocals of the LU diagonal
-      T* du = dd + CL_MAXM;
-      T* du2 = du + CL_MAXM;
-      T* x = du2 + CL_MAXM;
-      unsigned char* piv = reinterpret_cast<unsigned char*>(x + CL_MAXM);
+      T* x = dl + 4 * CL_MAXM;  // the iterate (the factors before it, pivots after)
       const int wn = nlu < CL_NW ? nlu : CL_NW;
       for (int i = rank + CL * warp; i < nvec; i += CL * wn) {
         const int pos = sh.order[i];
@@ -892,32 +971,6 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
           continue;
         }
         const T lam = sh.lam[pos];
-        if (lane == 0) {
-          // LU with partial pivoting of T - lam I on rows lo..hi; the running
-          // diagonal and superdiagonal stay in registers (the recurrence is serial)
-          const T tiny = CEps<T>::v * tnorm;
-          T cd = sh.d[lo] - lam, cu = sh.e[lo];
-#pragma unroll 4
-          for (int t = 0; t < s - 1; ++t) {
-            const T sub = sh.e[lo + t];
-            const T nd = sh.d[lo + t + 1] - lam;
-            const T nu = t < s - 2 ? sh.e[lo + t + 1] : (T)0;
-            if (fabs(cd) >= fabs(sub)) {
-              if (cd == (T)0) cd = tiny;
-              const T l = sub / cd;
-              dl[t] = l; dd[t] = (T)1 / cd; du[t] = cu; du2[t] = 0; piv[t] = 0;
-              cd = nd - l * cu;
-              cu = nu;
-            } else {
-              const T l = cd / sub;
-              dl[t] = l; dd[t] = (T)1 / sub; du[t] = nd; du2[t] = nu; piv[t] = 1;
-              cd = cu - l * nd;
-              cu = -l * nu;
-            }
-          }
-          if (cd == (T)0) cd = tiny;
-          dd[s - 1] = (T)1 / cd;
-        }
         for (int t = lane; t < s; t += 32) {
           unsigned h = (unsigned)(t + 1) * 2654435761u ^ ((unsigned)(i + 7) * 40503u + 0x9e3779b9u);
           h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12; h *= 0x297a2d39u; h ^= h >> 15;
@@ -925,47 +978,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
           x[t] = (h & 0x10000u) ? -u : u;
         }
         __syncwarp();
-        for (int it = 0; it < 2; ++it) {
-          if (lane == 0) {
-            // forward (L with row swaps), then backward (U); carried values in registers
-            T xt = x[0];
-#pragma unroll 4
-            for (int t = 0; t < s - 1; ++t) {
-              const T xn = x[t + 1], l = dl[t];
-              if (piv[t] == 0) {
-                x[t] = xt;
-                xt = xn - l * xt;
-              } else {
-                x[t] = xn;
-                xt = xt - l * xn;
-              }
-            }
-            T x1 = xt * dd[s - 1];  // x[t + 1]
-            x[s - 1] = x1;
-            T x2 = 0;               // x[t + 2]
-#pragma unroll 4
-            for (int t = s - 2; t >= 0; --t) {
-              const T xv = (x[t] - du[t] * x1 - du2[t] * x2) * dd[t];
-              x[t] = xv;
-              x2 = x1;
-              x1 = xv;
-            }
-          }
-          __syncwarp();
-          T xmax = 0;
-          for (int t = lane; t < s; t += 32) xmax = fmax(xmax, fabs(x[t]));
-          for (int o = 16; o > 0; o >>= 1) xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-          if (!(xmax <= (T)3e38)) xmax = 0;
-          const T sx = xmax > (T)0 ? (T)1 / xmax : (T)0;
-          for (int t = lane; t < s; t += 32) x[t] = xmax > (T)0 ? x[t] * sx : (T)(t == 0);
-          __syncwarp();
-          T nrm = 0;
-          for (int t = lane; t < s; t += 32) nrm += x[t] * x[t];
-          nrm = warp_sum(nrm);
-          const T inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)1;
-          for (int t = lane; t < s; t += 32) x[t] *= inv;
-          __syncwarp();
-        }
+        tri_inverse_iteration<T>(sh, lo, hi, lam, tnorm, dl, x, 2, lane);
         for (int t = lane; t < s; t += 32) z[lo + t] = x[t];
         __syncwarp();
       }
@@ -1048,7 +1061,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
         T* pb = pub + (size_t)osl * MBK * CL_MAXM;
         T* rv = cpy;                  // fallback: the replacement vector (cpy is idle here)
         T* part = cpy + CL_MAXM;      // fallback: per-warp partial corrections
-        static_assert((MSL * MBK + 1 + CL_NW) * CL_MAXM * sizeof(T) <= sizeof(ClusterShared<T>::A),
+        static_assert((MSL * MBK + 1 + CL_NW + 6) * CL_MAXM * sizeof(T) <= sizeof(ClusterShared<T>::A),
                       "fallback buffers");
         const int vec = MBK * b + warp;
         const bool mine = vec < nvec;
@@ -1078,14 +1091,25 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
               if (pass == 0 && nrm < (T)0.25 * nrm0 && lane == 0) s_again = 1;
               if (lane == 0) s_flag = cancelled ? 1 : 0;
               if (cancelled) {
-                // a pseudo-random vector replaces it, orthogonalised below by the whole CTA
+                // inverse iteration from a new pseudo-random start, on the block of T
+                // that holds this eigenvalue, gives a vector of the same (nearly
+                // degenerate) eigenspace; it is orthogonalised below by the whole CTA
                 // against every earlier vector (earlier blocks from global memory)
+                const int pos = sh.order[vec];
+                const int lo = sh.sblo[pos], hi = sh.sbhi[pos], sblk = hi - lo + 1;
+                T* sc = pub + (size_t)(MSL * MBK + 1 + CL_NW) * CL_MAXM;  // LU scratch
+                T* xs = sc + 4 * CL_MAXM;
+                for (int r2 = lane; r2 < sblk; r2 += 32) {
+                  unsigned h = (unsigned)(r2 + 1) * 2654435761u ^ ((unsigned)(vec + 11) * 40503u + 0x85ebca6bu);
+                  h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12; h *= 0x297a2d39u; h ^= h >> 15;
+                  xs[r2] = (T)(h & 0xffffu) * (T)(1.0 / 65536.0) - (T)0.5;
+                }
+                __syncwarp();
+                if (sblk > 1) tri_inverse_iteration<T>(sh, lo, hi, sh.lam[pos], tnorm, sc, xs, 2, lane);
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                   const int row = lane + 32 * e;
-                  unsigned h = (unsigned)(row + 1) * 2654435761u ^ ((unsigned)(vec + 11) * 40503u + 0x85ebca6bu);
-                  h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12; h *= 0x297a2d39u; h ^= h >> 15;
-                  if (row < CL_MAXM) rv[row] = row < m ? (T)(h & 0xffffu) * (T)(1.0 / 65536.0) - (T)0.5 : (T)0;
+                  if (row < CL_MAXM) rv[row] = (row >= lo && row <= hi) ? xs[row - lo] : (T)0;
                 }
               }
             }
