@@ -1055,6 +1055,44 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
         if (pass == 0 && !(nd > (T)1e-4 * nz)) break;  // nearly orthogonal already
       }
     };
+    // replacement of a cancelled vector: the whole CTA removes (twice) the first nprev
+    // vectors of the rank order (earlier blocks from global memory, the owner's block
+    // from pub) from rv
+    auto project_rv = [&](int nprev) {
+      const int b = nprev / MBK;
+      const T* pb = pub + (size_t)(b / CL) * MBK * CL_MAXM;
+      T* rv = cpy;
+      T* part = cpy + CL_MAXM;
+      for (int rep = 0; rep < 2; ++rep) {
+        T acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0;
+        for (int u = warp; u < nprev; u += CL_NW) {
+          const T* q = u < MBK * b ? gZ + (size_t)u * m : pb + (size_t)(u - MBK * b) * CL_MAXM;
+          T a = 0;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int row = lane + 32 * e;
+            if (row < m) a += q[row] * rv[row];
+          }
+          a = warp_sum(a);
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int row = lane + 32 * e;
+            if (row < m) acc[e] += a * q[row];
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) part[warp * CL_MAXM + lane + 32 * e] = acc[e];
+        __syncthreads();
+        for (int row = tid; row < m; row += CL_THREADS) {
+          T sub = 0;
+          for (int ww = 0; ww < CL_NW; ++ww) sub += part[ww * CL_MAXM + row];
+          rv[row] -= sub;
+        }
+        __syncthreads();
+      }
+    };
     for (int b = 0; b < nblk; ++b) {
       const int owner = b % CL, osl = b / CL;
       if (rank == owner) {
@@ -1094,9 +1132,12 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
                 // inverse iteration from a new pseudo-random start, on the block of T
                 // that holds this eigenvalue, gives a vector of the same (nearly
                 // degenerate) eigenspace; it is orthogonalised below by the whole CTA
-                // against every earlier vector (earlier blocks from global memory)
+                // against every earlier vector (earlier blocks from global memory). An
+                // eigenvalue in the FP32 noise floor (any direction of that subspace
+                // will do) takes a plain pseudo-random vector instead.
                 const int pos = sh.order[vec];
-                const int lo = sh.sblo[pos], hi = sh.sbhi[pos], sblk = hi - lo + 1;
+                const bool noise = !(fabs(sh.lam[pos]) > (T)16 * CEps<T>::v * fabs(sh.lam[sh.order[0]]));
+                const int lo = noise ? 0 : sh.sblo[pos], hi = noise ? m - 1 : sh.sbhi[pos], sblk = hi - lo + 1;
                 T* sc = pub + (size_t)(MSL * MBK + 1 + CL_NW) * CL_MAXM;  // LU scratch
                 T* xs = sc + 4 * CL_MAXM;
                 for (int r2 = lane; r2 < sblk; r2 += 32) {
@@ -1105,7 +1146,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
                   xs[r2] = (T)(h & 0xffffu) * (T)(1.0 / 65536.0) - (T)0.5;
                 }
                 __syncwarp();
-                if (sblk > 1) tri_inverse_iteration<T>(sh, lo, hi, sh.lam[pos], tnorm, sc, xs, 2, lane);
+                if (sblk > 1 && !noise) tri_inverse_iteration<T>(sh, lo, hi, sh.lam[pos], tnorm, sc, xs, 2, lane);
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                   const int row = lane + 32 * e;
@@ -1117,35 +1158,27 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
             if (s_flag) {
               if (tid == 0) atomicAdd(&out->sweeps, 1);  // diagnostics: replaced vectors
               const int nprev = MBK * b + t;
-              for (int rep = 0; rep < 2; ++rep) {
-                T acc[E];
+              project_rv(nprev);
+              if (warp == t) {
+                T nr = 0;
 #pragma unroll
-                for (int e = 0; e < E; ++e) acc[e] = 0;
-                for (int u = warp; u < nprev; u += CL_NW) {
-                  const T* q = u < MBK * b ? gZ + (size_t)u * m : pb + (size_t)(u - MBK * b) * CL_MAXM;
-                  T a = 0;
-#pragma unroll
-                  for (int e = 0; e < E; ++e) {
-                    const int row = lane + 32 * e;
-                    if (row < m) a += q[row] * rv[row];
-                  }
-                  a = warp_sum(a);
+                for (int e = 0; e < E; ++e) nr += rv[lane + 32 * e] * rv[lane + 32 * e];
+                nr = warp_sum(nr);
+                // cancelled again (inverse iteration returned a vector of the span of the
+                // earlier ones): a plain pseudo-random vector, projected once more below
+                if (lane == 0) s_flag = nr > (T)1e-6 ? 0 : 2;
+                if (!(nr > (T)1e-6)) {
 #pragma unroll
                   for (int e = 0; e < E; ++e) {
                     const int row = lane + 32 * e;
-                    if (row < m) acc[e] += a * q[row];
+                    unsigned h = (unsigned)(row + 1) * 2654435761u ^ ((unsigned)(vec + 1013) * 40503u + 0x85ebca6bu);
+                    h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12; h *= 0x297a2d39u; h ^= h >> 15;
+                    if (row < CL_MAXM) rv[row] = row < m ? (T)(h & 0xffffu) * (T)(1.0 / 65536.0) - (T)0.5 : (T)0;
                   }
                 }
-#pragma unroll
-                for (int e = 0; e < E; ++e) part[warp * CL_MAXM + lane + 32 * e] = acc[e];
-                __syncthreads();
-                for (int row = tid; row < m; row += CL_THREADS) {
-                  T sub = 0;
-                  for (int ww = 0; ww < CL_NW; ++ww) sub += part[ww * CL_MAXM + row];
-                  rv[row] -= sub;
-                }
-                __syncthreads();
               }
+              __syncthreads();
+              if (s_flag == 2) project_rv(nprev);
               if (warp == t) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) w[e] = rv[lane + 32 * e];

@@ -11,7 +11,7 @@ through lr_last_eig and compared with the oracle's eigh of the same FP64 matrix:
   an eigenvalue cluster the FP32 solve cannot separate;
 * the truncated state: rho_trunc = V' P V'^dag depends on the kept vectors only
   through the projector P, and ||V' (P - P0) V'^dag||_F = ||G^(1/2) (P - P0) G^(1/2)||_F,
-  held to 1e-12 of the trace;
+  held to 1e-11 of the trace;
 * where eigenvalues lie within the FP32 resolution (16 x 2^-24 lambda_1) of the cut,
   the kept set is chosen by the FP32 eigenvalues and may differ there (a tie at the
   state's precision): the bounds grow by the mass of those eigenvalues (twice for rho);
@@ -129,7 +129,7 @@ def test_refined_eigensolve_matches_fp64(lr, solver, case):
         assert e_lam < 1e-13
         assert e_sub * l1 / tr < 1e-13 + tied
         assert e_drop < 1e-13 + tied
-        assert e_rho < 1e-12 + 2 * tied
+        assert e_rho < 1e-11 + 2 * tied
 
 
 def test_fp32_eigensolve_alone_is_at_fp32_level(lr):
