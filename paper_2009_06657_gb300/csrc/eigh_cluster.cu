@@ -1132,11 +1132,12 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
                 // inverse iteration from a new pseudo-random start, on the block of T
                 // that holds this eigenvalue, gives a vector of the same (nearly
                 // degenerate) eigenspace; it is orthogonalised below by the whole CTA
-                // against every earlier vector (earlier blocks from global memory). An
-                // eigenvalue in the FP32 noise floor (any direction of that subspace
-                // will do) takes a plain pseudo-random vector instead.
+                // against every earlier vector (earlier blocks from global memory). A
+                // discarded vector whose eigenvalue lies in the FP32 noise floor (any
+                // direction of that subspace will do) takes a plain pseudo-random vector.
                 const int pos = sh.order[vec];
-                const bool noise = !(fabs(sh.lam[pos]) > (T)16 * CEps<T>::v * fabs(sh.lam[sh.order[0]]));
+                const bool noise = vec >= sh.k &&
+                                   !(fabs(sh.lam[pos]) > (T)16 * CEps<T>::v * fabs(sh.lam[sh.order[0]]));
                 const int lo = noise ? 0 : sh.sblo[pos], hi = noise ? m - 1 : sh.sbhi[pos], sblk = hi - lo + 1;
                 T* sc = pub + (size_t)(MSL * MBK + 1 + CL_NW) * CL_MAXM;  // LU scratch
                 T* xs = sc + 4 * CL_MAXM;
