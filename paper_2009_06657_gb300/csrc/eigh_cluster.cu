@@ -421,6 +421,145 @@ __device__ void tri_inverse_iteration(const ClusterShared<T>& sh, int lo, int hi
   }
 }
 
+// Back-transform of the tridiagonal eigenvectors z (real, gZ) to those of the
+// Hermitian matrix, y = H_0 (H_1 (... H_{m-2} z)), into evecs (FP64 storage, column
+// normalised). Warp w of CTA `rank` carries the NC columns rank + CL (w + CL_NW c); the
+// reflectors (full-length rows of gref, tau in its last row) are staged BT_STAGE at a
+// time by one bulk asynchronous copy and applied in groups of BT_GROUP: the group's
+// inner products v_k^dag y are reduced together and corrected with the reflectors'
+// own inner products v_k^dag v_l. Returns false if the bounded wait on a copy gave up.
+template <typename T, int NC>
+__device__ __noinline__ bool back_transform(ClusterShared<T>& sh, const cx<T>* __restrict__ gref, const T* __restrict__ gZ,
+                               double2* __restrict__ evecs, int m, int nvec, int rank) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const cx<T>* taus = reinterpret_cast<const cx<T>*>(gref + (size_t)(CL_MAXM - 1) * CL_MAXM);
+  cx<T>* stage = reinterpret_cast<cx<T>*>(&sh.A[0][0]);  // BT_STAGE full-length reflectors
+  static_assert(BT_STAGE * CL_MAXM <= CL_ROWS * CL_MAXM, "staging buffer");
+  constexpr int E = CL_MAXM / 32;
+  // reflectors applied together (fewer for two columns: register budget of 512 threads)
+  constexpr int BT_GROUP = NC == 1 ? BtGroup<T>::v : BtGroup<T>::v / 2;
+  cx<T>* gram = &sh.gram[0][0][0];  // [BT_STAGE / BT_GROUP][BT_GROUP][BT_GROUP]
+  const int nref = m - 1;
+  bool bt_ok = true;
+  int bt_phase = 0;
+  int col[NC];
+  bool has[NC];
+  cx<T> y[NC][E];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    col[c] = rank + CL * (warp + CL_NW * c);
+    has[c] = col[c] < nvec;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int row = lane + 32 * e;
+      y[c][e] = mk<T>(has[c] && row < m ? gZ[(size_t)col[c] * m + row] : (T)0, 0);
+    }
+  }
+  const bool any = has[0];
+  // reflector blocks from the last one down: [b0, b0 + nb)
+  for (int top = nref; top > 0; top -= BT_STAGE) {
+    const int b0 = top - BT_STAGE > 0 ? top - BT_STAGE : 0;
+    const int nb = top - b0;
+    __syncthreads();  // the previous block is no longer read
+    if (tid == 0 && bt_ok) {
+      // rows b0 .. b0 + nb - 1 of the reflector store are full-length rows (zero
+      // outside each reflector's support): one bulk copy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc::bulk_load(tc::smem_u32(stage), gref + (size_t)b0 * CL_MAXM, (uint32_t)(nb * CL_MAXM * sizeof(cx<T>)),
+                    tc::smem_u32(&sh.mbar));
+    }
+    if (tid < BT_STAGE) sh.btau[tid] = tid < nb ? taus[b0 + tid] : mk<T>(0, 0);
+    if (bt_ok) bt_ok = tc::mbar_wait(tc::smem_u32(&sh.mbar), (uint32_t)(bt_phase & 1));
+    ++bt_phase;
+    bt_ok = __syncthreads_and(bt_ok) != 0;
+    if (!bt_ok) continue;
+    if (nb < BT_STAGE) {  // rows past the last reflector: zero, not stale
+      for (int e = nb * CL_MAXM + tid; e < BT_STAGE * CL_MAXM; e += CL_THREADS) stage[e] = mk<T>(0, 0);
+      __syncthreads();
+    }
+    // inner products of the reflectors within each group of BT_GROUP
+    for (int pr = warp; pr < (BT_STAGE / BT_GROUP) * BT_GROUP * BT_GROUP; pr += CL_NW) {
+      const int g = pr / (BT_GROUP * BT_GROUP), kk = (pr / BT_GROUP) % BT_GROUP, ll = pr % BT_GROUP;
+      if (ll <= kk) continue;
+      const cx<T>* vk = stage + (size_t)(g * BT_GROUP + kk) * CL_MAXM;
+      const cx<T>* vl = stage + (size_t)(g * BT_GROUP + ll) * CL_MAXM;
+      cx<T> acc = mk<T>(0, 0);
+      for (int t = lane; t < m; t += 32) cfmac(acc, vk[t], vl[t]);
+      acc.x = warp_sum(acc.x);
+      acc.y = warp_sum(acc.y);
+      if (lane == 0) gram[(g * BT_GROUP + kk) * BT_GROUP + ll] = acc;
+    }
+    __syncthreads();
+    if (any) {
+      for (int g = BT_STAGE / BT_GROUP - 1; g >= 0; --g) {
+        // s_k = v_k^dag y for the group's reflectors and the warp's columns, reduced together
+        T sre[NC][BT_GROUP], sim[NC][BT_GROUP];
+#pragma unroll
+        for (int kk = 0; kk < BT_GROUP; ++kk) {
+          const cx<T>* vk = stage + (size_t)(g * BT_GROUP + kk) * CL_MAXM;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            cx<T> acc = mk<T>(0, 0);
+#pragma unroll
+            for (int e = 0; e < E; ++e) cfmac(acc, vk[lane + 32 * e], y[c][e]);
+            sre[c][kk] = acc.x;
+            sim[c][kk] = acc.y;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+#pragma unroll
+            for (int kk = 0; kk < BT_GROUP; ++kk) {
+              sre[c][kk] += __shfl_xor_sync(0xffffffffu, sre[c][kk], o);
+              sim[c][kk] += __shfl_xor_sync(0xffffffffu, sim[c][kk], o);
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          // f_k = tau_k (s_k - sum_{l > k} (v_k^dag v_l) f_l), k descending
+          cx<T> f[BT_GROUP];
+#pragma unroll
+          for (int kk = BT_GROUP - 1; kk >= 0; --kk) {
+            cx<T> sk = mk<T>(sre[c][kk], sim[c][kk]);
+#pragma unroll
+            for (int ll = kk + 1; ll < BT_GROUP; ++ll)
+              sk = csub(sk, cmul(gram[(g * BT_GROUP + kk) * BT_GROUP + ll], f[ll]));
+            f[kk] = cmul(sh.btau[g * BT_GROUP + kk], sk);
+          }
+#pragma unroll
+          for (int kk = 0; kk < BT_GROUP; ++kk) {
+            const cx<T>* vk = stage + (size_t)(g * BT_GROUP + kk) * CL_MAXM;
+#pragma unroll
+            for (int e = 0; e < E; ++e) y[c][e] = csub(y[c][e], cmul(f[kk], vk[lane + 32 * e]));
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    if (has[c] && bt_ok) {
+      double nrm = 0.0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) nrm += (double)y[c][e].x * y[c][e].x + (double)y[c][e].y * y[c][e].y;
+      for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+      const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 1.0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int row = lane + 32 * e;
+        if (row < m) {
+          const double2 vv = to_d2(y[c][e]);
+          evecs[(size_t)row * m + col[c]] = make_double2(vv.x * inv, vv.y * inv);
+        }
+      }
+    }
+  }
+  return bt_ok;
+}
+
 __device__ __forceinline__ long long phase_clock() { return clock64(); }
 
 }  // namespace
@@ -1244,120 +1383,17 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
   cluster.sync();
   if (tid == 0) { const long long t1 = phase_clock(); t_ph[4] = t1 - t0; t0 = t1; }
 
-  // ---- back-transform y = H_0 (... (H_{m-2} z)); column rank + CL * warp -----
+  // ---- back-transform y = H_0 (... (H_{m-2} z)): column rank + CL (warp + CL_NW c) ---
   {
-    const cx<T>* taus = reinterpret_cast<const cx<T>*>(gref + (size_t)(CL_MAXM - 1) * CL_MAXM);
-    cx<T>* stage = reinterpret_cast<cx<T>*>(&sh.A[0][0]);  // BT_STAGE full-length reflectors
-    static_assert(BT_STAGE * CL_MAXM <= CL_ROWS * CL_MAXM, "staging buffer");
-    constexpr int E = CL_MAXM / 32;
-    constexpr int BT_GROUP = BtGroup<T>::v;
-    const int nref = m - 1;
-    const int npass = (nvec + CL * CL_NW - 1) / (CL * CL_NW);
     if (tid == 0) {
       tc::mbar_init(tc::smem_u32(&sh.mbar), 1);
       asm volatile("fence.mbarrier_init.release.cluster;");
     }
     __syncthreads();
-    bool bt_ok = true;
-    int bt_phase = 0;
-    for (int pass = 0; pass < npass; ++pass) {
-      const int col = rank + CL * (warp + CL_NW * pass);
-      const bool has = col < nvec;
-      cx<T> y[E];
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int row = lane + 32 * e;
-        y[e] = mk<T>(has && row < m ? gZ[(size_t)col * m + row] : (T)0, 0);
-      }
-      // reflector blocks from the last one down: [b0, b0 + nb)
-      for (int top = nref; top > 0; top -= BT_STAGE) {
-        const int b0 = top - BT_STAGE > 0 ? top - BT_STAGE : 0;
-        const int nb = top - b0;
-        __syncthreads();  // the previous block is no longer read
-        if (tid == 0 && bt_ok) {
-          // rows b0 .. b0 + nb - 1 of the reflector store are full-length rows (zero
-          // outside each reflector's support): one bulk copy
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          tc::bulk_load(tc::smem_u32(stage), gref + (size_t)b0 * CL_MAXM,
-                        (uint32_t)(nb * CL_MAXM * sizeof(cx<T>)), tc::smem_u32(&sh.mbar));
-        }
-        if (tid < BT_STAGE) sh.btau[tid] = tid < nb ? taus[b0 + tid] : mk<T>(0, 0);
-        if (bt_ok) bt_ok = tc::mbar_wait(tc::smem_u32(&sh.mbar), (uint32_t)(bt_phase & 1));
-        ++bt_phase;
-        bt_ok = __syncthreads_and(bt_ok) != 0;
-        if (!bt_ok) continue;
-        if (nb < BT_STAGE) {  // rows past the last reflector: zero, not stale
-          for (int e = nb * CL_MAXM + tid; e < BT_STAGE * CL_MAXM; e += CL_THREADS) stage[e] = mk<T>(0, 0);
-          __syncthreads();
-        }
-        // inner products of the reflectors within each group of BT_GROUP
-        for (int pr = warp; pr < (BT_STAGE / BT_GROUP) * BT_GROUP * BT_GROUP; pr += CL_NW) {
-          const int g = pr / (BT_GROUP * BT_GROUP), kk = (pr / BT_GROUP) % BT_GROUP, ll = pr % BT_GROUP;
-          if (ll <= kk) continue;
-          const cx<T>* vk = stage + (size_t)(g * BT_GROUP + kk) * CL_MAXM;
-          const cx<T>* vl = stage + (size_t)(g * BT_GROUP + ll) * CL_MAXM;
-          cx<T> acc = mk<T>(0, 0);
-          for (int t = lane; t < m; t += 32) cfmac(acc, vk[t], vl[t]);
-          acc.x = warp_sum(acc.x);
-          acc.y = warp_sum(acc.y);
-          if (lane == 0) sh.gram[g][kk][ll] = acc;
-        }
-        __syncthreads();
-        if (has) {
-          for (int g = BT_STAGE / BT_GROUP - 1; g >= 0; --g) {
-            // s_k = v_k^dag y for the group's reflectors, reduced together
-            T sre[BT_GROUP], sim[BT_GROUP];
-#pragma unroll
-            for (int kk = 0; kk < BT_GROUP; ++kk) {
-              const cx<T>* vk = stage + (size_t)(g * BT_GROUP + kk) * CL_MAXM;
-              cx<T> acc = mk<T>(0, 0);
-#pragma unroll
-              for (int e = 0; e < E; ++e) cfmac(acc, vk[lane + 32 * e], y[e]);
-              sre[kk] = acc.x;
-              sim[kk] = acc.y;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-              for (int kk = 0; kk < BT_GROUP; ++kk) {
-                sre[kk] += __shfl_xor_sync(0xffffffffu, sre[kk], o);
-                sim[kk] += __shfl_xor_sync(0xffffffffu, sim[kk], o);
-              }
-            }
-            // f_k = tau_k (s_k - sum_{l > k} (v_k^dag v_l) f_l), k descending
-            cx<T> f[BT_GROUP];
-#pragma unroll
-            for (int kk = BT_GROUP - 1; kk >= 0; --kk) {
-              cx<T> sk = mk<T>(sre[kk], sim[kk]);
-#pragma unroll
-              for (int ll = kk + 1; ll < BT_GROUP; ++ll) sk = csub(sk, cmul(sh.gram[g][kk][ll], f[ll]));
-              f[kk] = cmul(sh.btau[g * BT_GROUP + kk], sk);
-            }
-#pragma unroll
-            for (int kk = 0; kk < BT_GROUP; ++kk) {
-              const cx<T>* vk = stage + (size_t)(g * BT_GROUP + kk) * CL_MAXM;
-#pragma unroll
-              for (int e = 0; e < E; ++e) y[e] = csub(y[e], cmul(f[kk], vk[lane + 32 * e]));
-            }
-          }
-        }
-      }
-      if (has && bt_ok) {
-        double nrm = 0.0;
-#pragma unroll
-        for (int e = 0; e < E; ++e) nrm += (double)y[e].x * y[e].x + (double)y[e].y * y[e].y;
-        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-        const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 1.0;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int row = lane + 32 * e;
-          if (row < m) {
-            const double2 vv = to_d2(y[e]);
-            evecs[(size_t)row * m + col] = make_double2(vv.x * inv, vv.y * inv);
-          }
-        }
-      }
-    }
+    // one pass over the reflectors; a warp carries two columns when there are more
+    // than CL x CL_NW of them (every eigenvector for the FP64 refinement)
+    const bool bt_ok = nvec > CL * CL_NW ? back_transform<T, 2>(sh, gref, gZ, evecs, m, nvec, rank)
+                                         : back_transform<T, 1>(sh, gref, gZ, evecs, m, nvec, rank);
     if (!bt_ok && tid == 0) out->status = 3;  // a bounded wait gave up
   }
   cluster.sync();
