@@ -367,6 +367,15 @@ int lr_sample(lr_handle h, int shots, const double* uniforms, int64_t* out_host)
  * effective rank). More than 256 columns -> LR_ECAPACITY. Synchronises. */
 int lr_entropy(lr_handle h, double* out_host);
 
+/* Diagnostics, not in the paper: runs one kernel that waits on a shared-memory
+ * mbarrier with the same bounded wait (at most `polls` polls) that the tensor-core
+ * kernels and the cluster eigensolver use; `arrive` != 0 lets another thread arrive
+ * first, 0 leaves the barrier unsignalled so that the wait runs out. Returns LR_OK
+ * when the wait completed and LR_ETIMEOUT when it gave up (the kernel returns and the
+ * context stays usable), LR_EINVAL for polls < 1. Allocates and frees one int of device
+ * memory; synchronises `stream` (a cudaStream_t, NULL = the legacy default stream). */
+int lr_selftest_wait(long long polls, int arrive, void* stream);
+
 const char* lr_status_string(int status);
 
 /* Number of GPU kernels this library has launched in this process, over all

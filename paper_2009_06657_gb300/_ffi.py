@@ -112,6 +112,7 @@ _SIGS = {
                                  C.POINTER(C.c_int64)]),
     "lr_batch_free": (C.c_int, [_H]),
     "lr_status_string": (C.c_char_p, [C.c_int]),
+    "lr_selftest_wait": (C.c_int, [C.c_longlong, C.c_int, _P]),
     "lr_launch_count": (C.c_int64, []),
     "lr_sample": (C.c_int, [_H, C.c_int, _D, C.POINTER(C.c_int64)]),
     "lr_entropy": (C.c_int, [_H, _D]),

@@ -38,9 +38,10 @@ __device__ __forceinline__ void commit(uint32_t mbar_addr) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+// Bounded wait for the mbarrier phase `parity`: at most `limit` polls; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_n(uint32_t addr, uint32_t parity, long long limit) {
   uint32_t done = 0;
-  for (long long it = 0; it < TC_SPIN && !done; ++it) {
+  for (long long it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -48,6 +49,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
   }
   return done != 0;
 }
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) { return mbar_wait_n(addr, parity, TC_SPIN); }
 
 // one-shot bulk copy global -> shared (16-byte aligned, size a multiple of 16),
 // completion counted on an mbarrier that this thread arms with the byte count
