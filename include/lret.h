@@ -156,6 +156,23 @@ int lr_set_tensor_cores(lr_handle h, int on);
  * sum_{i<=k} lambda_i >= (1 - eps) * sum_i lambda_i. eps <= 0 disables it. */
 int lr_set_eps(lr_handle h, double eps);
 
+/* Per-truncation log (the rank history of Sec. II.B-C, from which the intermediate
+ * rank V_I of Eq. 8 follows): capacity > 0 allocates room for that many records and
+ * starts a new log (0 switches it off and frees it); lr_reset clears it. Every
+ * truncation then appends, on the device, LR_TRUNC_LOG_FIELDS doubles:
+ *   [0] m   columns before the truncation (the Gram matrix size)
+ *   [1] k   columns kept
+ *   [2] lambda_1, [3] lambda_k, [4] lambda_{k+1} (0 when nothing is dropped)
+ *   [5] discarded eigenvalue mass, [6] trace of the Gram matrix,
+ *   [7] (lambda_k - lambda_{k+1}) / lambda_1 (infinite when nothing is dropped).
+ * Truncations skipped because nothing would be dropped (m <= r) write no record.
+ * lr_get_trunc_log copies up to max_records records (row-major) into out_host and
+ * the number of truncations logged (possibly above the capacity: later ones are
+ * counted, not stored) into *count_out. It flushes queued work and synchronises. */
+#define LR_TRUNC_LOG_FIELDS 8
+int lr_set_trunc_log(lr_handle h, int capacity);
+int lr_get_trunc_log(lr_handle h, double* out_host, int max_records, int64_t* count_out);
+
 /* Eigensolver of the truncation: LR_EIG_AUTO (default: two-sided Jacobi for
  * small Gram matrices, the cluster tridiagonal solver above 32 columns (FP32
  * state) or 64 columns (FP64 state)), LR_EIG_JACOBI, LR_EIG_TRIDIAG

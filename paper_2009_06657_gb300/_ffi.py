@@ -27,6 +27,7 @@ LR_AMPLITUDE_DAMPING = 1
 LR_BIT_FLIP = 2
 LR_STATIC_MAX_TERMS = 256
 KCLASSES = ["expand", "gram", "eigh", "project", "readout", "pauli", "small", "refine"]
+LR_TRUNC_LOG_FIELDS = 8
 LR_EIGP_REFINED = 0
 LR_EIGP_FP32 = 1
 LR_EIGP_FP64 = 2
@@ -88,6 +89,8 @@ _SIGS = {
     "lr_set_eigensolver": (C.c_int, [_H, C.c_int]),
     "lr_set_eig_precision": (C.c_int, [_H, C.c_int, C.c_int]),
     "lr_last_eig": (C.c_int, [_H, _I, _I, _D, _D, _D]),
+    "lr_set_trunc_log": (C.c_int, [_H, C.c_int]),
+    "lr_get_trunc_log": (C.c_int, [_H, _D, C.c_int, C.POINTER(C.c_int64)]),
     "lr_set_path": (C.c_int, [_H, C.c_int]),
     "lr_set_tensor_cores": (C.c_int, [_H, C.c_int]),
     "lr_probs": (C.c_int, [_H, _P]),

@@ -72,6 +72,9 @@ struct lr_ctx {
   int eig_iters = 1;
   void* rf_work = nullptr;         // refinement workspace (allocated on first use)
   int last_m = 0;                  // size of the last eigenproblem (lr_last_eig)
+  double* tlog = nullptr;          // per-truncation log (lr_set_trunc_log): records
+  int64_t* tlog_n = nullptr;       // records written (device counter)
+  int tlog_cap = 0;
   int path = 0;    // 0 structured truncation where it applies, 1 always expand V'
   double2* S = nullptr;   // pair Gram (2c x 2c)
   int* tc_status = nullptr;  // set by tensor-core kernels when a bounded wait gives up
@@ -373,11 +376,30 @@ int flush_all(lr_ctx* h) {
   return flush_gate(h);
 }
 
-__global__ void k_accum(const EigOut* eo, double* acc) {
+// Per-truncation accounting; with a log buffer (cap > 0) also one record per truncation:
+// [m, k, lambda_1, lambda_k, lambda_{k+1}, discarded, trace, gap] (FP64).
+__global__ void k_accum(const EigOut* eo, const double* evals, int m, double* acc, double* log, int cap,
+                        int64_t* nlog) {
   acc[0] += eo->dropped;
   acc[1] = eo->gap;
   if ((double)eo->status > acc[2]) acc[2] = (double)eo->status;
   acc[3] += 1.0;
+  if (cap > 0) {
+    const int64_t i = *nlog;
+    if (i < cap) {
+      const int k = eo->k;
+      double* rec = log + i * LR_TRUNC_LOG_FIELDS;
+      rec[0] = m;
+      rec[1] = k;
+      rec[2] = evals[0];
+      rec[3] = k >= 1 ? evals[k - 1] : 0.0;
+      rec[4] = k < m ? evals[k] : 0.0;
+      rec[5] = eo->dropped;
+      rec[6] = eo->trace;
+      rec[7] = eo->gap;
+    }
+    *nlog = i + 1;
+  }
 }
 
 int ensure_masks(lr_ctx* h, int T) {
@@ -456,7 +478,7 @@ int run_eigh(lr_ctx* h, int m, int r_eff, double eps, int* k_out) {
     CK(launch_eig_refine(h->G, m, h->evals, h->evecs, h->eo, kmax, h->eig_iters, h->rf_work, h->stream));
     tend(h, LR_K_EIGREFINE, te);
   }
-  k_accum<<<1, 1, 0, h->stream>>>(h->eo, h->acc);
+  k_accum<<<1, 1, 0, h->stream>>>(h->eo, h->evals, m, h->acc, h->tlog, h->tlog_cap, h->tlog_n);
   note_launches(1);
   CK(cudaGetLastError());
   if (r_eff > 0) {
@@ -680,6 +702,7 @@ int set_initial_state(lr_ctx* h) {
     CK(cudaMemcpyAsync(h->V, one, sizeof(one), cudaMemcpyHostToDevice, h->stream));
   }
   CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 8, h->stream));
+  if (h->tlog_n) CK(cudaMemsetAsync(h->tlog_n, 0, sizeof(int64_t), h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->c = 1;
   h->has_gate = h->has_chan = false;
@@ -851,6 +874,8 @@ int lr_free(lr_handle h) {
   dfree((void*&)h->eo);
   dfree(h->eig_work);
   dfree(h->rf_work);
+  dfree((void*&)h->tlog);
+  dfree((void*&)h->tlog_n);
   dfree((void*&)h->acc);
   dfree((void*&)h->dscratch);
   dfree((void*&)h->samp);
@@ -1070,6 +1095,40 @@ int lr_set_eig_precision(lr_handle h, int mode, int iters) {
   if (!h || mode < LR_EIGP_REFINED || mode > LR_EIGP_FP64) return LR_EINVAL;
   h->eig_prec = mode;
   h->eig_iters = iters < 0 ? 0 : (iters > 4 ? 4 : iters);
+  return LR_OK;
+}
+
+int lr_set_trunc_log(lr_handle h, int capacity) {
+  if (!h || capacity < 0) return LR_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  dfree((void*&)h->tlog);
+  dfree((void*&)h->tlog_n);
+  h->tlog_cap = 0;
+  if (capacity == 0) return LR_OK;
+  int rc = dmalloc(h, (void**)&h->tlog, sizeof(double) * LR_TRUNC_LOG_FIELDS * (size_t)capacity);
+  if (!rc) rc = dmalloc(h, (void**)&h->tlog_n, sizeof(int64_t));
+  if (rc) return rc;
+  CK(cudaMemsetAsync(h->tlog_n, 0, sizeof(int64_t), h->stream));
+  h->tlog_cap = capacity;
+  return LR_OK;
+}
+
+int lr_get_trunc_log(lr_handle h, double* out_host, int max_records, int64_t* count_out) {
+  if (!h || !count_out || max_records < 0 || (max_records > 0 && !out_host)) return LR_EINVAL;
+  if (h->tlog_cap == 0) {
+    *count_out = 0;
+    return LR_OK;
+  }
+  int rc = flush_all(h);
+  if (rc) return rc;
+  int64_t n = 0;
+  CK(cudaMemcpyAsync(&n, h->tlog_n, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int64_t stored = n < h->tlog_cap ? n : h->tlog_cap;
+  const int64_t copy = stored < max_records ? stored : max_records;
+  if (copy > 0)
+    CK(cudaMemcpy(out_host, h->tlog, sizeof(double) * LR_TRUNC_LOG_FIELDS * (size_t)copy, cudaMemcpyDeviceToHost));
+  *count_out = n;
   return LR_OK;
 }
 

@@ -171,6 +171,32 @@ class LRSim:
         return (G.reshape(-1)[: mm * mm].reshape(mm, mm).copy(), ev[:mm].copy(),
                 U.reshape(-1)[: mm * mm].reshape(mm, mm).copy(), k.value)
 
+    def set_trunc_log(self, capacity=65536):
+        """Record every truncation on the device (lr_set_trunc_log); 0 switches it off."""
+        check(lib.lr_set_trunc_log(self.h, int(capacity)), "lr_set_trunc_log")
+        self._tlog_cap = int(capacity)
+
+    def trunc_log(self, group=1):
+        """The truncations recorded since set_trunc_log / reset, one dict each: m, k,
+        lambda_1, lambda_k, lambda_k1, discarded, trace, gap, and the intermediate rank
+        of Eq. 8 for Kraus groups of `group` channels, V_I = (n / M)^(1/3) m (the column
+        count m before a truncation is 4^M V for depolarizing groups)."""
+        cnt = C.c_int64(0)
+        check(lib.lr_get_trunc_log(self.h, None, 0, C.byref(cnt)), "lr_get_trunc_log")
+        n = int(cnt.value)
+        buf = np.zeros((max(n, 1), _ffi.LR_TRUNC_LOG_FIELDS), dtype=np.float64)
+        check(lib.lr_get_trunc_log(self.h, _dptr(buf), n, C.byref(cnt)), "lr_get_trunc_log")
+        keys = ("m", "k", "lambda_1", "lambda_k", "lambda_k1", "discarded", "trace", "gap")
+        vi = (self.n / float(group)) ** (1.0 / 3.0)
+        out = []
+        stored = min(n, getattr(self, "_tlog_cap", 0))
+        for row in buf[:stored]:
+            d = dict(zip(keys, (float(x) for x in row)))
+            d["m"], d["k"] = int(d["m"]), int(d["k"])
+            d["V_I"] = vi * d["m"]
+            out.append(d)
+        return out
+
     def set_path(self, which):
         """"auto" (truncate without forming V' where possible) or "expand"."""
         check(lib.lr_set_path(self.h, {"auto": 0, "expand": 1}[which]), "lr_set_path")
