@@ -471,15 +471,19 @@ def distortion(p_lret, p_exact, p_noiseless):
 def trace_distance_lowrank(LA, LB):
     """0.5 * || LA LA^dag - LB LB^dag ||_1 without forming 2^n x 2^n matrices.
 
-    With X = [LA LB] and S = diag(I, -I), LA LA^dag - LB LB^dag = X S X^dag,
-    whose nonzero eigenvalues are those of S X^dag X = S G (AB and BA share
-    their nonzero spectrum). S G is similar to G^(1/2) S G^(1/2), so they are real.
+    With the thin QR factorisation [LA LB] = Q [RA RB], the difference is
+    Q (RA RA^dag - RB RB^dag) Q^dag with Q orthonormal, so its nonzero eigenvalues
+    are those of the small Hermitian matrix RA RA^dag - RB RB^dag. Both steps are
+    backward stable, so nearly equal states keep an absolute error at the level of
+    the unit roundoff (the eigenvalues of the non-Hermitian S X^dag X, S = diag(I, -I),
+    are equal in exact arithmetic but nearly defective when LA ~ LB, which leaves an
+    error of order sqrt(unit roundoff)).
     """
-    X = np.hstack([LA, LB])
-    G = X.conj().T @ X
-    s = np.concatenate([np.ones(LA.shape[1]), -np.ones(LB.shape[1])])
-    ev = np.linalg.eigvals(s[:, None] * G)
-    return 0.5 * float(np.sum(np.abs(np.real(ev))))
+    ra = LA.shape[1]
+    _, R = np.linalg.qr(np.hstack([LA, LB]), mode="reduced")
+    RA, RB = R[:, :ra], R[:, ra:]
+    D = RA @ RA.conj().T - RB @ RB.conj().T
+    return 0.5 * float(np.sum(np.abs(np.linalg.eigvalsh(0.5 * (D + D.conj().T)))))
 
 
 def expect_lret(n, ops, thetas, terms, r=None, eps=None):

@@ -275,6 +275,21 @@ def test_lowrank_trace_distance_matches_dense():
     assert abs(O.trace_distance_lowrank(A, B) - dense) < 1e-10
 
 
+def test_lowrank_trace_distance_of_nearly_equal_states():
+    """Two states with the same eigenvectors and eigenvalues that differ by 1e-12:
+    the trace distance is half the sum of the eigenvalue differences exactly, a
+    case where a nearly defective eigenproblem would leave an error near 1e-8."""
+    rng = np.random.default_rng(10)
+    Q, _ = np.linalg.qr(rng.normal(size=(256, 8)) + 1j * rng.normal(size=(256, 8)))
+    lam = np.sort(rng.uniform(size=8))[::-1]
+    lam /= lam.sum()
+    dl = 1e-12 * rng.choice([-1.0, 1.0], size=8)
+    A = Q * np.sqrt(lam)
+    B = (Q * np.sqrt(lam + dl)) @ np.linalg.qr(rng.normal(size=(8, 8)))[0]  # other gauge
+    assert abs(O.trace_distance_lowrank(A, B) - 0.5 * np.sum(np.abs(dl))) < 1e-14
+    assert O.trace_distance_lowrank(A, A) < 1e-15
+
+
 # ---- gradients -------------------------------------------------------------
 
 def test_gradient_fd_full_rank_matches_parameter_shift():
