@@ -232,9 +232,10 @@ def run_ours(args, rank, world):
     fp64 = bench_fp64(args, layers, dev, stream) if (rank == 0 and not args.no_fp64) else None
     adj = bench_adjoint(dev, stream) if (rank == 0 and not args.no_adjoint) else None
     bat = bench_batch(dev, stream, scale=args.batch_scale) if (rank == 0 and not args.no_batch) else None
+    epsl = bench_eps(dev, stream) if (rank == 0 and not args.no_eps) else None
     grv = bench_grover(dev, stream) if (rank == 0 and not args.no_grover) else None
     return dict(ms=ms, g_per=g_per, c_per=c_per, ktimes=ktimes, clk=clk, e2e_s=e2e_s, fp64=fp64, info=info,
-                adjoint=adj, batch=bat, launches=n_launch, readouts=rd, grover=grv, eig_variants=eigv)
+                adjoint=adj, batch=bat, eps=epsl, launches=n_launch, readouts=rd, grover=grv, eig_variants=eigv)
 
 
 def bench_fp64(args, layers, dev, stream):
@@ -440,37 +441,51 @@ def bench_grover(dev, stream, reps=3):
     return out
 
 
-def bench_batch(dev, stream, scale=0.05, sample_single=12):
+def bench_batch(dev, stream, scale=1.0, sample_single=4, eig_precision="refined"):
     """256 seeded circuits (n ~ U{8..18}, r in {8,16,32,64}, depth ~ U{40..200}
     layers scaled by `scale`, mixed depolarizing 1e-3 / amplitude damping 2e-3),
-    complex64, advanced together by one CUDA-graph launch; against the same
-    circuits run one at a time through the single-circuit path (a sample of
-    them, rate per gate-step)."""
+    complex64, the eigensolve `eig_precision` (FP32 solve + FP64 refinement of the
+    kept eigenvectors by default), Gram split counts from the autotuned table,
+    advanced together by one CUDA-graph launch (timed once with CUDA events, after
+    a warm-up run of the same circuits at 2% depth); against the first
+    `sample_single` circuits run one at a time through the single-circuit path
+    (rate per gate-step)."""
     import torch
 
     import paper_2009_06657_gb300 as lr
+    from paper_2009_06657_gb300.autotune import DEFAULT_TABLE, BatchTable
     from workloads import batch_circuits
+    table = BatchTable.load_or_empty()
     circs = batch_circuits(count=256, depth_scale=scale)
+    splits = table.splits_for(circs)
     with torch.cuda.stream(stream):
+        warm = batch_circuits(count=256, depth_scale=0.02)
+        wb = lr.LRBatch(warm, dtype="c64", stream=stream, eig_precision=eig_precision,
+                        splits=table.splits_for(warm))
+        wb.run()
+        torch.cuda.synchronize()
+        wb.close()
         t0 = time.perf_counter()
-        b = lr.LRBatch(circs, dtype="c64", stream=stream)
+        b = lr.LRBatch(circs, dtype="c64", stream=stream, eig_precision=eig_precision, splits=splits)
         t_build = time.perf_counter() - t0
         st = b.stats()
-        b.run()  # warm-up
         torch.cuda.synchronize()
-        b.reset()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = lr.launch_count()
         e0.record(stream)
         b.run()
         e1.record(stream)
+        n_launch = lr.launch_count() - n0
         torch.cuda.synchronize()
         t_batch = e0.elapsed_time(e1) / 1e3
+        trunc = sum(b.info(i)["compressions"] for i in range(len(circs)))
         b.close()
         # one at a time (sample)
         gates = 0
         t1 = time.perf_counter()
         for cd in circs[:sample_single]:
             sim = lr.LRSim(cd["n"], cd["r"], dtype="c64", stream=stream)
+            sim.set_eig_precision(eig_precision)
             lr.run_ops(sim, cd["ops"], r=cd["r"])
             sim.info()
             gates += sum(1 for o in cd["ops"] if o["op"] in ("rx", "ry", "rz", "cnot", "cz"))
@@ -479,11 +494,57 @@ def bench_batch(dev, stream, scale=0.05, sample_single=12):
         t_single = time.perf_counter() - t1
     return {"workload": f"256 random circuits, n U{{8..18}}, r in {{8,16,32,64}}, depth U{{40..200}} x {scale}, "
                         "mixed depolarizing 1e-3 / amplitude damping 2e-3, complex64",
-            "gates": st["gates"], "truncations": st["truncations"], "schedule_steps": st["steps"],
-            "launches_per_run": st["launches"], "build_s": t_build, "batch_s": t_batch,
-            "batch_gate_steps_per_s": st["gates"] / t_batch,
+            "eig_precision": eig_precision,
+            "splits_table": os.path.basename(DEFAULT_TABLE) if table.entries else None,
+            "splits_table_device": table.device or None,
+            "gates": st["gates"], "truncations": st["truncations"], "truncations_done": trunc,
+            "schedule_steps": st["steps"], "graph_kernels_per_run": n_launch, "build_s": t_build,
+            "batch_s": t_batch, "batch_gate_steps_per_s": st["gates"] / t_batch,
             "single_gate_steps_per_s": gates / t_single, "single_sample_circuits": sample_single,
             "speedup": (st["gates"] / t_batch) / (gates / t_single)}
+
+
+def bench_eps(dev, stream, n=13, depth=12, p=1e-3, eps=1e-4):
+    """The eps rule at the paper's eps / p = 0.1 setting (Sec. III.A: p = 0.1 %,
+    eps = 1e-4, 12-13 qubits, depth 12): the random layered family with
+    depolarizing channels, complex64 (refined eigensolve), the kept rank chosen on
+    the device at every truncation; CUDA-event time of the whole circuit after one
+    untimed run, the rank history from the truncation log and V_I of Eq. 8."""
+    import numpy as np
+    import torch
+
+    import paper_2009_06657_gb300 as lr
+    from workloads import random_layered
+    ops = random_layered(n, depth, seed=SEED + 10, noise=("dep", p))
+    gates = sum(1 for o in ops if o["op"] in ("rx", "ry", "rz", "cnot", "cz"))
+    sim = lr.LRSim(n, 64, dtype="c64", capacity=256, stream=stream)
+    sim.set_eps(eps)
+    sim.set_trunc_log(1 << 16)
+    try:
+        with torch.cuda.stream(stream):
+            lr.run_ops(sim, ops, r=0)
+            sim.info()
+            sim.reset()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lr.run_ops(sim, ops, r=0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            log = sim.trunc_log()
+            info = sim.info()
+    except RuntimeError as ex:
+        sim.close()
+        return {"error": str(ex)}
+    sim.close()
+    ks = np.array([e["k"] for e in log]) if log else np.zeros(1)
+    return {"workload": f"{n} qubits, depth {depth} random layered family, depolarizing p = {p}, eps = {eps} "
+                        "(eps / p = 0.1), complex64",
+            "gate_steps_per_s": gates / t, "s": t, "gates": gates, "truncations": len(log),
+            "final_rank": int(info["columns"]), "max_rank": int(ks.max()), "mean_rank": float(ks.mean()),
+            "mean_V_I": float(np.mean([e["V_I"] for e in log])) if log else None,
+            "discarded": info["discarded"]}
 
 
 # Algorithmic work of one steady-state launch of each kernel class on the
@@ -535,20 +596,23 @@ def kernel_rooflines(kt, peaks):
     return out
 
 
-def profile_case(n):
+def profile_case(n, solver="auto", eig_precision="refined"):
     """A short run for profilers: the first 12 ops of the benchmark's circuit
     family on n qubits (r = 64), which reach 64 columns and then truncate the
-    256-column Gram matrix through the tensor-core Gram, the cluster
-    eigensolver and the tensor-core projection."""
+    256-column Gram matrix through the tensor-core Gram, the eigensolver
+    (`solver`: auto = the cluster solver at this size, or tridiag; `eig_precision`:
+    refined, fp32 or fp64) and the tensor-core projection."""
     import torch
 
     import paper_2009_06657_gb300 as lr
     from workloads import random_layered
     ops = random_layered(n, 1, seed=SEED, noise=("dep", P_DEP))
     sim = lr.LRSim(n, RANK, dtype="c64")
+    sim.set_eigensolver(solver)
+    sim.set_eig_precision(eig_precision)
     lr.run_ops(sim, ops[:12], r=RANK)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": n, "info": {k: v for k, v in sim.info().items() if isinstance(v, (int, float))}}))
+    print(json.dumps({"profile_case": n, "solver": solver, "eig_precision": eig_precision, "info": {k: v for k, v in sim.info().items() if isinstance(v, (int, float))}}))
     sim.close()
 
 
@@ -586,6 +650,10 @@ def main():
                     help="run only the dense-gate and readout kernels on an n-qubit state for profilers and exit")
     ap.add_argument("--profile-case", type=int, default=0,
                     help="run only a short n-qubit case for profilers (no timing) and exit")
+    ap.add_argument("--profile-solver", default="auto", choices=["auto", "tridiag", "cluster", "jacobi"],
+                    help="eigensolver of --profile-case")
+    ap.add_argument("--profile-eig-precision", default="refined", choices=["refined", "fp32", "fp64"],
+                    help="eigensolve precision of --profile-case")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -596,13 +664,14 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-grover", action="store_true")
     ap.add_argument("--no-eig-variants", action="store_true")
-    ap.add_argument("--batch-scale", type=float, default=0.05)
+    ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--no-eps", action="store_true")
     args = ap.parse_args()
     if args.profile_readouts:
         profile_readouts(args.profile_readouts)
         return
     if args.profile_case:
-        profile_case(args.profile_case)
+        profile_case(args.profile_case, args.profile_solver, args.profile_eig_precision)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -648,14 +717,14 @@ def main():
         "kernel_launches_per_step": {k: v[1] for k, v in kt.items()},
         "roofline": {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                      "frac": (ach / peak) if ach else None, "traffic": NCU_TRAFFIC.get(dom),
-                     "peak_source": peaks["source"],
-                     "frac_of_occupied_sms": ((ach / (peak * 8 / 152)) if (ach and dom == "eigh") else None)},
+                     "peak_source": peaks["source"]},
         "kernels": kr,
         "clocks": res["clk"],
         "e2e": {"value": res["g_per"] / res["e2e_s"], "unit": "noisy gate-steps/s",
                 "h2d_bytes_per_step": h2d_bytes(get_layers()[0]), "d2h_bytes_per_step": (1 << N_QUBITS) * 4 + 8},
         "fp64": None, "cpu_baseline": None, "adjoint": res.get("adjoint"), "batch": res.get("batch"),
         "readouts": res.get("readouts"), "grover": res.get("grover"), "eig_variants": res.get("eig_variants"),
+        "eps_rule": res.get("eps"),
     }
     out["gpu_launches"] = res["launches"]  # the library's own launch counter over the timed region
     if res["fp64"]:

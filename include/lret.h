@@ -283,9 +283,8 @@ int64_t lr_device_bytes(lr_handle h);
  *
  * Scratch (term masks and partial sums, about 2 MB) lives in one fixed device
  * array of this library, held by every GPU that loads it until the process
- * exits; the call allocates and frees nothing. The first call on a device looks
- * up that array's device address, so make the first call on each device before
- * any stream capture. All calls share the array, and the last call's contents
+ * exits; the call allocates and frees nothing (the first call on a device looks
+ * up that array's device address). All calls share the array, and the last call's contents
  * stay in it (every value a call reads is written by that call first): calls
  * that overlap on the GPU, from different streams or threads, race and must be
  * serialised by the caller. T > LR_STATIC_MAX_TERMS returns LR_ECAPACITY.
@@ -324,11 +323,32 @@ typedef struct lr_batch* lr_batch_handle;
 
 /* Lower, allocate, upload the task tables and (use_graph != 0) capture the
  * schedule into one CUDA graph. rows_per_split sets the Gram split size
- * (<= 0: 4096). Every circuit starts in |0...0>. A NULL stream with
+ * (<= 0: 4096). Every circuit starts in |0...0>. The eigensolve of an LR_C64
+ * batch is the refined one (lr_batch_create_ex chooses otherwise). A NULL stream with
  * use_graph != 0 gets a stream of the batch's own (the legacy default stream
  * cannot be captured); the batch calls synchronise it. */
 int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_per_split, int use_graph,
                     void* stream, lr_batch_handle* out);
+/* Options of lr_batch_create_ex (lr_batch_opts_default fills the defaults).
+ * dtype: LR_C64 or LR_C128. eig_precision (LR_C64 only; LR_C128 always solves in
+ * FP64): LR_EIGP_REFINED (default: FP32 solve of every eigenvector, then `eig_iters`
+ * steps of the FP64 refinement of the kept ones, as lr_set_eig_precision describes),
+ * LR_EIGP_FP32 or LR_EIGP_FP64 (the solver in FP64 arithmetic). rows_per_split: Gram
+ * split size of a circuit without its own entry in `splits` (<= 0: 4096). splits:
+ * NULL or one Gram split count per circuit (0 = from rows_per_split, else clamped to
+ * 1..64 and to the circuit's row pairs), for example from an autotuned table.
+ * use_graph, stream: as lr_batch_create. */
+typedef struct lr_batch_opts {
+  int dtype;
+  int eig_precision;
+  int eig_iters;
+  int rows_per_split;
+  const int* splits;
+  int use_graph;
+  void* stream;
+} lr_batch_opts;
+void lr_batch_opts_default(lr_batch_opts* o);
+int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opts* opts, lr_batch_handle* out);
 /* Run the whole schedule once (one graph launch). Asynchronous. */
 int lr_batch_run(lr_batch_handle b);
 /* Put every circuit back into |0...0> with zero discarded mass. Synchronises. */

@@ -54,6 +54,12 @@ class lr_circuit(C.Structure):
     _fields_ = [("n", C.c_int), ("r", C.c_int), ("nops", C.c_int), ("ops", C.POINTER(lr_op))]
 
 
+class lr_batch_opts(C.Structure):
+    _fields_ = [("dtype", C.c_int), ("eig_precision", C.c_int), ("eig_iters", C.c_int),
+                ("rows_per_split", C.c_int), ("splits", C.POINTER(C.c_int)), ("use_graph", C.c_int),
+                ("stream", C.c_void_p)]
+
+
 OP_KIND = {"rx": 0, "ry": 1, "rz": 2, "cnot": 3, "cz": 4, "dep": 5, "ad": 6, "bf": 7}
 
 
@@ -107,6 +113,8 @@ _SIGS = {
     "lr_kernel_times": (C.c_int, [_H, _D, C.POINTER(C.c_int64)]),
     "lr_expect_static": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _U64, _U64, _D, _D, _P]),
     "lr_batch_create": (C.c_int, [C.POINTER(lr_circuit), C.c_int, C.c_int, C.c_int, C.c_int, _P, C.POINTER(_H)]),
+    "lr_batch_opts_default": (None, [C.POINTER(lr_batch_opts)]),
+    "lr_batch_create_ex": (C.c_int, [C.POINTER(lr_circuit), C.c_int, C.POINTER(lr_batch_opts), C.POINTER(_H)]),
     "lr_batch_run": (C.c_int, [_H]),
     "lr_batch_reset": (C.c_int, [_H]),
     "lr_batch_info": (C.c_int, [_H, C.c_int, C.POINTER(lr_info)]),

@@ -38,12 +38,14 @@ struct Circ {
   double* evals = nullptr;
   EigOut* eo = nullptr;
   void* eigwork = nullptr;
+  void* rfwork = nullptr;  // FP64 refinement workspace (refined eigensolve)
   int64_t gates = 0, truncs = 0;
 };
 
 struct Step {
   int e_off = 0, e_cnt = 0, e_blocks = 0, eb_off = 0;
   int t_off = 0, t_cnt = 0, gram_blocks = 0, proj_blocks = 0, gb_off = 0, pb_off = 0, max_m2 = 0, max_d = 0;
+  int max_m = 0, max_k = 0;  // largest Gram size and rank of the step's truncations
 };
 
 
@@ -74,8 +76,10 @@ struct lr_batch {
   size_t esz = 0;
   std::vector<Circ> circ;
   std::vector<Step> steps;
+  int eig_prec = LR_EIGP_REFINED, eig_iters = 1;
   ExpandTask* d_et = nullptr;
   TruncTask* d_tt = nullptr;
+  RefineTask* d_rt = nullptr;  // one per truncation task, same order (refined eigensolve)
   int* d_bs = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -218,6 +222,9 @@ int init_states(lr_batch* b) {
   return LR_OK;
 }
 
+// the eigensolver's arithmetic: FP64 for a complex128 state or when asked for
+bool solve_fp64(const lr_batch* b) { return b->dtype == LR_C128 || b->eig_prec == LR_EIGP_FP64; }
+
 int enqueue(lr_batch* b) {
   const int dt = b->dtype;
   for (const Step& st : b->steps) {
@@ -233,7 +240,14 @@ int enqueue(lr_batch* b) {
         return launch_trunc_batch_gemms<decltype(t)>(tt, b->d_bs + st.gb_off, st.gram_blocks, b->d_bs + st.pb_off,
                                                      st.proj_blocks, st.t_cnt, st.max_m2, st.max_d, 0, b->stream);
       }));
-      BCK(by_dt(dt, [&](auto t) { return launch_eigh_tri_batch<decltype(t)>(tt, st.t_cnt, b->stream); }));
+      if (solve_fp64(b)) {
+        BCK(launch_eigh_tri_batch<double>(tt, st.t_cnt, 0, b->stream));
+      } else {
+        const int refine = b->eig_prec == LR_EIGP_REFINED;
+        BCK(launch_eigh_tri_batch<float>(tt, st.t_cnt, refine, b->stream));
+        if (refine)
+          BCK(launch_eig_refine_batch(b->d_rt + st.t_off, st.t_cnt, st.max_m, st.max_k, b->eig_iters, b->stream));
+      }
       BCK(by_dt(dt, [&](auto t) {
         return launch_trunc_batch_gemms<decltype(t)>(tt, b->d_bs + st.gb_off, st.gram_blocks, b->d_bs + st.pb_off,
                                                      st.proj_blocks, st.t_cnt, st.max_m2, st.max_d, 1, b->stream);
@@ -254,25 +268,55 @@ int lr_batch_free(lr_batch_handle b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (auto& C : b->circ) {
     for (int i = 0; i < 2; ++i) if (C.buf[i]) cudaFree(C.buf[i]);
-    void* ps[] = {C.acc, C.partials, C.G, C.evecs, C.D, C.evals, C.eo, C.eigwork};
+    void* ps[] = {C.acc, C.partials, C.G, C.evecs, C.D, C.evals, C.eo, C.eigwork, C.rfwork};
     for (void* p : ps) if (p) cudaFree(p);
   }
   if (b->d_et) cudaFree(b->d_et);
   if (b->d_tt) cudaFree(b->d_tt);
+  if (b->d_rt) cudaFree(b->d_rt);
   if (b->d_bs) cudaFree(b->d_bs);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
   return LR_OK;
 }
 
+void lr_batch_opts_default(lr_batch_opts* o) {
+  if (!o) return;
+  o->dtype = LR_C64;
+  o->eig_precision = LR_EIGP_REFINED;
+  o->eig_iters = 1;
+  o->rows_per_split = 0;
+  o->splits = nullptr;
+  o->use_graph = 1;
+  o->stream = nullptr;
+}
+
 int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_per_split, int use_graph,
                     void* stream, lr_batch_handle* out) {
-  if (!out || !circuits || count < 1 || (dtype != LR_C64 && dtype != LR_C128)) return LR_EINVAL;
+  lr_batch_opts o;
+  lr_batch_opts_default(&o);
+  o.dtype = dtype;
+  o.rows_per_split = rows_per_split;
+  o.use_graph = use_graph;
+  o.stream = stream;
+  return lr_batch_create_ex(circuits, count, &o, out);
+}
+
+int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opts* opts, lr_batch_handle* out) {
+  if (!out || !opts) return LR_EINVAL;
   *out = nullptr;
+  const int dtype = opts->dtype, use_graph = opts->use_graph;
+  int rows_per_split = opts->rows_per_split;
+  void* stream = opts->stream;
+  if (!circuits || count < 1 || (dtype != LR_C64 && dtype != LR_C128)) return LR_EINVAL;
+  if (opts->eig_precision < LR_EIGP_REFINED || opts->eig_precision > LR_EIGP_FP64) return LR_EINVAL;
+  if (opts->eig_precision == LR_EIGP_REFINED && (opts->eig_iters < 1 || opts->eig_iters > 4)) return LR_EINVAL;
   if (rows_per_split <= 0) rows_per_split = 4096;
   lr_batch* b = new lr_batch();
   b->count = count;
   b->dtype = dtype;
+  b->eig_prec = dtype == LR_C128 ? LR_EIGP_FP64 : opts->eig_precision;
+  b->eig_iters = opts->eig_iters;
   b->stream = (cudaStream_t)stream;
   if (!b->stream && use_graph) {
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -304,6 +348,8 @@ int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_p
     max_stages = std::max(max_stages, stages[i].size());
     const int64_t N2 = C.N / 2;
     int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, N2 / rows_per_split));
+    if (opts->splits && opts->splits[i] > 0)
+      splits = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)64, N2, (int64_t)opts->splits[i]}));
     C.splits = splits;
     const int m = 4 * cd.r, c2 = 2 * cd.r;
     const size_t slab = (size_t)C.N * C.cap * b->esz;
@@ -316,7 +362,8 @@ int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_p
     if (!rc) rc = bmalloc(b, (void**)&C.D, sizeof(double2) * (size_t)c2 * c2);
     if (!rc) rc = bmalloc(b, (void**)&C.evals, sizeof(double) * m);
     if (!rc) rc = bmalloc(b, (void**)&C.eo, sizeof(EigOut));
-    if (!rc) rc = bmalloc(b, &C.eigwork, eigh_work_bytes(m, dtype == LR_C128));
+    if (!rc) rc = bmalloc(b, &C.eigwork, eigh_work_bytes(m, solve_fp64(b)));
+    if (!rc && !solve_fp64(b) && b->eig_prec == LR_EIGP_REFINED) rc = bmalloc(b, &C.rfwork, eig_refine_work_bytes(m));
   }
   if (rc) {
     lr_batch_free(b);
@@ -325,6 +372,7 @@ int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_p
   // step-major task tables
   std::vector<ExpandTask> et;
   std::vector<TruncTask> tt;
+  std::vector<RefineTask> rt;
   std::vector<int> bs;
   b->steps.resize(max_stages);
   for (size_t s = 0; s < max_stages; ++s) {
@@ -379,6 +427,9 @@ int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_p
         t.D = C.D;
         t.acc = C.acc;
         tt.push_back(t);
+        rt.push_back(RefineTask{C.G, t.m, t.k, C.evals, C.evecs, C.eo, C.rfwork});
+        S.max_m = std::max(S.max_m, t.m);
+        S.max_k = std::max(S.max_k, t.k);
         gblocks.push_back(t.tiles * t.splits);
         pblocks.push_back(trunc_proj_blocks(t.N2, t.k));
         S.max_m2 = std::max(S.max_m2, t.m * t.m);
@@ -404,9 +455,11 @@ int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_p
       prefix(pblocks, &S.pb_off, &S.proj_blocks);
     }
     b->launches += (S.e_cnt ? 1 : 0) + (S.t_cnt ? 6 : 0);
+    if (S.t_cnt && !solve_fp64(b) && b->eig_prec == LR_EIGP_REFINED) b->launches += eig_refine_launches(b->eig_iters);
   }
   rc = bmalloc(b, (void**)&b->d_et, sizeof(ExpandTask) * std::max<size_t>(1, et.size()));
   if (!rc) rc = bmalloc(b, (void**)&b->d_tt, sizeof(TruncTask) * std::max<size_t>(1, tt.size()));
+  if (!rc) rc = bmalloc(b, (void**)&b->d_rt, sizeof(RefineTask) * std::max<size_t>(1, rt.size()));
   if (!rc) rc = bmalloc(b, (void**)&b->d_bs, sizeof(int) * std::max<size_t>(1, bs.size()));
   if (rc) {
     lr_batch_free(b);
@@ -416,8 +469,10 @@ int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_p
   if (!et.empty()) e = cudaMemcpy(b->d_et, et.data(), sizeof(ExpandTask) * et.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !tt.empty())
     e = cudaMemcpy(b->d_tt, tt.data(), sizeof(TruncTask) * tt.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !rt.empty())
+    e = cudaMemcpy(b->d_rt, rt.data(), sizeof(RefineTask) * rt.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !bs.empty()) e = cudaMemcpy(b->d_bs, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = by_dt(dtype, [&](auto t) { return prepare_eigh_tri_batch<decltype(t)>(); });
+  if (e == cudaSuccess) e = solve_fp64(b) ? prepare_eigh_tri_batch<double>() : prepare_eigh_tri_batch<float>();
   if (e != cudaSuccess) {
     lret::set_error("%s: %s", "batch setup", cudaGetErrorString(e));
     lr_batch_free(b);

@@ -29,7 +29,10 @@
 // amplify that. So the runtime runs one step (iters = 1) followed by three FP64
 // orthonormalisation steps X <- X (I - (X^dag X - I) / 2), each of which squares
 // the deviation from orthonormality. The kept eigenvalues are the FP64 Rayleigh
-// quotients of the refined vectors (formed with G X in the last of those steps).
+// quotients of the input of the last of those steps, from G X0 of the correction
+// step and a second-order FP32 term (rf_gdelta). Only G X, X^dag X and the Lowdin
+// product X (R - I) / 2 are FP64 products; the complement projections, the update and
+// the second-order term are FP32 products of small quantities.
 // Kept vectors are not rotated among themselves (that leaves rho unchanged), so a
 // kept eigenvalue inside a cluster the FP32 solve did not resolve (spread below
 // about u32 |G|) is the Rayleigh quotient of a vector of that cluster; the sum of
@@ -48,14 +51,69 @@ constexpr int RK = 32;   // K chunk staged in shared memory
 constexpr int RF_SPLITS_MAX = 8;
 constexpr int RF_ORTHO = 3;  // FP64 orthonormalisation steps after the corrections
 
+// One truncation's operands and its workspace, carved as eig_refine_work_bytes lays it
+// out. The steps read and write three buffers of kept columns: evecs (ld m; the FP32
+// solve's vectors X0, which stay there until the last step writes the result) and
+// the scratch buffers Xa, Xb (ld kmax). A step code st (the same for every
+// truncation of a launch) names the input (st & 3) and the output (st >> 2):
+// 0 = evecs, 1 = Xa, 2 = Xb.
+struct RfView {
+  const double2* G;
+  int m, kmax, splits;
+  double2 *evecs, *P, *Xa, *Xb, *R;
+  float2 *Res, *A;
+  double *evals, *mu, *mu2, *alpha;
+  EigOut* eo;
+};
+
+__host__ __device__ __forceinline__ RfView rf_view(const RefineTask& t) {
+  RfView v;
+  v.G = t.G;
+  v.m = t.m;
+  v.kmax = t.kmax < t.m ? t.kmax : t.m;
+  v.splits = (t.m + RK - 1) / RK;
+  v.evecs = t.evecs;
+  v.evals = t.evals;
+  v.eo = t.eo;
+  const size_t m = (size_t)t.m;
+  char* p = (char*)t.work;
+  v.P = (double2*)p;
+  p += (size_t)RF_SPLITS_MAX * (m + m) * m * sizeof(double2);
+  v.Xa = (double2*)p;
+  p += m * m * sizeof(double2);
+  v.Xb = (double2*)p;
+  p += m * m * sizeof(double2);
+  v.R = (double2*)p;
+  p += m * m * sizeof(double2);
+  v.Res = (float2*)p;
+  p += m * m * sizeof(float2);
+  v.A = (float2*)p;  // Xall^dag Res
+  p += m * m * sizeof(float2);
+  v.mu = (double*)p;
+  v.mu2 = v.mu + m;     // Rayleigh quotients of the refined vectors
+  v.alpha = v.mu2 + m;  // damping of each kept column's step
+  return v;
+}
+
+__device__ __forceinline__ int rf_k(const RfView& v) { return v.eo->k < v.kmax ? v.eo->k : v.kmax; }
+__device__ __forceinline__ double2* rf_buf(const RfView& v, int sel) {
+  return sel == 0 ? v.evecs : (sel == 1 ? v.Xa : v.Xb);
+}
+__device__ __forceinline__ const double2* rf_in(const RfView& v, int st) { return rf_buf(v, st & 3); }
+__device__ __forceinline__ int rf_ldin(const RfView& v, int st) { return (st & 3) == 0 ? v.m : v.kmax; }
+__device__ __forceinline__ double2* rf_out(const RfView& v, int st) { return rf_buf(v, st >> 2); }
+__device__ __forceinline__ int rf_ldout(const RfView& v, int st) { return (st >> 2) == 0 ? v.m : v.kmax; }
+
 // P[s] = [G ; X^dag] X over the K chunk s (rows r < m: G[r][:], rows m + i: conj(X[:, i])),
 // output rows from row0 (0: both products; m: X^dag X only).
-__global__ void __launch_bounds__(RT* RT)
-    k_rf_gemm64(const double2* __restrict__ G, int m, const double2* __restrict__ X, int ldx,
-                const EigOut* __restrict__ eo, int kmax, int row0, double2* __restrict__ P) {
-  const int k = eo->k < kmax ? eo->k : kmax;
-  const int r0 = row0 + blockIdx.y * RT, c0 = blockIdx.x * RT, s = blockIdx.z;
-  if (c0 >= k || r0 >= m + k) return;
+__device__ __forceinline__ void rf_gemm64(const RfView& v, int st, int x_rows_only, int bx, int by, int s) {
+  const int k = rf_k(v), m = v.m, kmax = v.kmax;
+  const double2* __restrict__ G = v.G;
+  const double2* __restrict__ X = rf_in(v, st);
+  const int ldx = rf_ldin(v, st);
+  const int row0 = x_rows_only ? m : 0;
+  const int r0 = row0 + by * RT, c0 = bx * RT;
+  if (s >= v.splits || c0 >= k || r0 >= m + k) return;
   __shared__ double2 As[RT][RK + 1];
   __shared__ double2 Bs[RK][RT + 1];
   const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
@@ -80,18 +138,18 @@ __global__ void __launch_bounds__(RT* RT)
 #pragma unroll 8
   for (int kk = 0; kk < RK; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
   const int row = r0 + ty, col = c0 + tx;
-  if (row < m + k && col < k) P[((size_t)s * (m + kmax) + row) * kmax + col] = acc;
+  if (row < m + k && col < k) v.P[((size_t)s * (m + kmax) + row) * kmax + col] = acc;
 }
 
 // One block per kept column i: W[:, i] and R[:, i] from the split partials (fixed
 // order), mu_i, res_i = w_i - mu_i x_i (stored in FP32), R (FP64).
-__global__ void __launch_bounds__(256)
-    k_rf_res(const double2* __restrict__ P, int splits, int m, const double2* __restrict__ X, int ldx,
-             const EigOut* __restrict__ eo, int kmax, double* __restrict__ mu, double2* __restrict__ R,
-             float2* __restrict__ Res) {
-  const int k = eo->k < kmax ? eo->k : kmax;
-  const int i = blockIdx.x;
+__device__ __forceinline__ void rf_res(const RfView& v, int st, int i) {
+  const int k = rf_k(v), m = v.m, kmax = v.kmax, splits = v.splits;
   if (i >= k) return;
+  const double2* __restrict__ P = v.P;
+  const double2* __restrict__ X = rf_in(v, st);
+  const int ldx = rf_ldin(v, st);
+  double* mu = v.mu;
   __shared__ double red[32];
   __shared__ double s_mu;
   const int t = threadIdx.x;
@@ -106,47 +164,52 @@ __global__ void __launch_bounds__(256)
   if (t < k) {
     double2 rv = make_double2(0.0, 0.0);
     for (int s = 0; s < splits; ++s) rv = cadd(rv, P[s * sstride + (size_t)(m + t) * kmax + i]);
-    R[(size_t)t * kmax + i] = rv;
+    v.R[(size_t)t * kmax + i] = rv;
   }
   q = block_sum(q, red);
   if (t == 0) {
     double nrm = 0.0;
     for (int s = 0; s < splits; ++s) nrm += P[s * sstride + (size_t)(m + i) * kmax + i].x;
-    const double v = nrm > 0.0 ? q / nrm : 0.0;
-    s_mu = v;
-    mu[i] = v;
+    const double val = nrm > 0.0 ? q / nrm : 0.0;
+    s_mu = val;
+    mu[i] = val;
   }
   __syncthreads();
   if (t < m) {
     const double2 rs = csub(w, cscale(x, s_mu));
-    Res[(size_t)t * kmax + i] = make_float2((float)rs.x, (float)rs.y);
+    v.Res[(size_t)t * kmax + i] = make_float2((float)rs.x, (float)rs.y);
   }
 }
 
+// Row tile of the FP32 products and of the FP64 orthonormalisation: TM rows x RT
+// columns per block (TM x RT threads, one output each), so that a 256 x 64 output
+// spreads over 256 blocks.
+constexpr int TM = 4;
+
 // A = Xall^dag Res (m x k): x_j^dag res_i for every column j of the FP32 solve, an
 // FP32 product (res is small).
-__global__ void __launch_bounds__(RT* RT)
-    k_rf_proj(const double2* __restrict__ Xall, int m, const float2* __restrict__ Res,
-              const EigOut* __restrict__ eo, int kmax, float2* __restrict__ A) {
-  const int k = eo->k < kmax ? eo->k : kmax;
-  const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT;
+__device__ __forceinline__ void rf_proj(const RfView& v, int bx, int by) {
+  const int k = rf_k(v), m = v.m, kmax = v.kmax;
+  const double2* __restrict__ Xall = v.evecs;
+  const float2* __restrict__ Res = v.Res;
+  const int r0 = by * TM, c0 = bx * RT;
   if (c0 >= k || r0 >= m) return;
-  __shared__ float2 As[RT][RK + 1];  // conj(Xall[kg][row])
+  __shared__ float2 As[TM][RK + 1];  // conj(Xall[kg][row])
   __shared__ float2 Bs[RK][RT + 1];  // Res[kg][col]
   const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
   float2 acc = make_float2(0.f, 0.f);
   for (int kb = 0; kb < m; kb += RK) {
-    for (int e = tid; e < RT * RK; e += RT * RT) {
-      const int rr = e % RT, kk = e / RT;
+    for (int e = tid; e < TM * RK; e += TM * RT) {
+      const int rr = e % TM, kk = e / TM;
       const int kg = kb + kk, rw = r0 + rr;
       float2 a = make_float2(0.f, 0.f);
       if (kg < m && rw < m) {
-        const double2 v = Xall[(size_t)kg * m + rw];
-        a = make_float2((float)v.x, -(float)v.y);
+        const double2 x = Xall[(size_t)kg * m + rw];
+        a = make_float2((float)x.x, -(float)x.y);
       }
       As[rr][kk] = a;
     }
-    for (int e = tid; e < RK * RT; e += RT * RT) {
+    for (int e = tid; e < RK * RT; e += TM * RT) {
       const int kk = e / RT, cc = e % RT;
       const int kg = kb + kk, cl = c0 + cc;
       Bs[kk][cc] = (kg < m && cl < k) ? Res[(size_t)kg * kmax + cl] : make_float2(0.f, 0.f);
@@ -157,7 +220,7 @@ __global__ void __launch_bounds__(RT* RT)
     __syncthreads();
   }
   const int row = r0 + ty, col = c0 + tx;
-  if (row < m && col < k) A[(size_t)row * kmax + col] = acc;
+  if (row < m && col < k) v.A[(size_t)row * kmax + col] = acc;
 }
 
 // Whether the complement correction of kept vector i along discarded vector j is
@@ -179,51 +242,37 @@ __device__ __forceinline__ bool rf_pair(int j, int i, const float2* __restrict__
   return ex * ex + ey * ey <= 0.25;
 }
 
-// e_ji of the update: kept j: the orthonormalising term -(R - I)_ji / 2 (FP64 R);
-// discarded j: alpha_i x_j^dag res_i / (mu_i - lambda_j) where rf_pair applies it
-// (alpha_i < 1 damps a column whose corrections are large in total).
-__device__ __forceinline__ float2 rf_coef(int j, int i, int k, const float2* __restrict__ A,
-                                          const double* __restrict__ mu, const double* __restrict__ lam,
-                                          const double2* __restrict__ R, const double* __restrict__ alpha,
-                                          int kmax) {
-  if (j < k) {
-    const double2 rv = R[(size_t)j * kmax + i];
-    return make_float2((float)(-0.5 * (rv.x - (j == i ? 1.0 : 0.0))), (float)(-0.5 * rv.y));
-  }
-  double ex, ey, den;
-  if (!rf_pair(j, i, A, mu, lam, kmax, ex, ey, den)) return make_float2(0.f, 0.f);
-  return make_float2((float)(alpha[i] * ex), (float)(alpha[i] * ey));
-}
-
-// Xout = Xin + [Xin | Xd] E, E formed while staged (rf_coef); FP32 products
-// accumulated onto the FP64 Xin
-__global__ void __launch_bounds__(RT* RT)
-    k_rf_update(const double2* __restrict__ Xall, int m, const double2* __restrict__ Xin, int ldi,
-                const float2* __restrict__ A, const double* __restrict__ mu, const double* __restrict__ lam,
-                const double2* __restrict__ R, const double* __restrict__ alpha, const EigOut* __restrict__ eo,
-                int kmax, double2* __restrict__ Xout, int ldo) {
-  const int k = eo->k < kmax ? eo->k : kmax;
-  const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT;
+// Xout = Xin + [Xin | Xd] E with E the coefficients rf_coefs wrote over A; FP32
+// products accumulated onto the FP64 Xin
+__device__ __forceinline__ void rf_update(const RfView& v, int st, int bx, int by) {
+  const int k = rf_k(v), m = v.m, kmax = v.kmax;
+  const double2* __restrict__ Xall = v.evecs;
+  const double2* __restrict__ Xin = rf_in(v, st);
+  const int ldi = rf_ldin(v, st);
+  double2* __restrict__ Xout = rf_out(v, st);
+  const int ldo = rf_ldout(v, st);
+  const float2* __restrict__ E = v.A;
+  const int r0 = by * TM, c0 = bx * RT;
   if (c0 >= k || r0 >= m) return;
-  __shared__ float2 As[RT][RK + 1];  // [Xin | Xd][row][kg]
+  __shared__ float2 As[TM][RK + 1];  // [Xin | Xd][row][kg]
   __shared__ float2 Bs[RK][RT + 1];  // E[kg][col]
   const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
   float2 acc = make_float2(0.f, 0.f);
   for (int kb = 0; kb < m; kb += RK) {
-    for (int e = tid; e < RT * RK; e += RT * RT) {
+    for (int e = tid; e < TM * RK; e += TM * RT) {
       const int rr = e / RK, kk = e % RK;
       const int kg = kb + kk, rw = r0 + rr;
       float2 a = make_float2(0.f, 0.f);
       if (kg < m && rw < m) {
-        const double2 v = kg < k ? Xin[(size_t)rw * ldi + kg] : Xall[(size_t)rw * m + kg];
-        a = make_float2((float)v.x, (float)v.y);
+        const double2 x = kg < k ? Xin[(size_t)rw * ldi + kg] : Xall[(size_t)rw * m + kg];
+        a = make_float2((float)x.x, (float)x.y);
       }
       As[rr][kk] = a;
     }
-    for (int e = tid; e < RK * RT; e += RT * RT) {
+    for (int e = tid; e < RK * RT; e += TM * RT) {
       const int kk = e / RT, cc = e % RT;
       const int kg = kb + kk, cl = c0 + cc;
-      Bs[kk][cc] = (kg < m && cl < k) ? rf_coef(kg, cl, k, A, mu, lam, R, alpha, kmax) : make_float2(0.f, 0.f);
+      Bs[kk][cc] = (kg < m && cl < k) ? E[(size_t)kg * kmax + cl] : make_float2(0.f, 0.f);
     }
     __syncthreads();
 #pragma unroll 8
@@ -237,55 +286,66 @@ __global__ void __launch_bounds__(RT* RT)
   }
 }
 
-// Per kept column i, over the pairs rf_pair applies: s_i = sum_j |e_ji|^2 sets the
-// damping alpha_i = min(1, sqrt(S_MAX / s_i)): a column whose corrections would move
-// it far from unit norm takes a shorter step, so that the orthonormalisation steps
-// (which square the deviation from orthonormality) converge.
+// Coefficients E of the update, one block per kept column i, thread j per row of E,
+// written over A (each entry by the thread that read it): kept j: the
+// orthonormalising term -(R - I)_ji / 2 (FP64 R); discarded j: alpha_i x_j^dag res_i /
+// (mu_i - lambda_j) where rf_pair applies it, else 0. Over the pairs rf_pair applies,
+// s_i = sum_j |e_ji|^2 sets the damping alpha_i = min(1, sqrt(S_MAX / s_i)): a column
+// whose corrections would move it far from unit norm takes a shorter step, so that
+// the orthonormalisation steps (which square the deviation from orthonormality)
+// converge.
 constexpr double RF_SMAX = 1e-2;
-__global__ void __launch_bounds__(256)
-    k_rf_damp(const float2* __restrict__ A, const double* __restrict__ lam, int m, const EigOut* __restrict__ eo,
-              int kmax, const double* __restrict__ mu, double* __restrict__ alpha) {
-  const int k = eo->k < kmax ? eo->k : kmax;
-  const int i = blockIdx.x;
+__device__ __forceinline__ void rf_coefs(const RfView& v, int i) {
+  const int k = rf_k(v), m = v.m, kmax = v.kmax;
   if (i >= k) return;
   __shared__ double red[32];
-  const int j = k + threadIdx.x;
-  double e2 = 0.0;
-  if (j < m) {
-    double ex, ey, den;
-    if (rf_pair(j, i, A, mu, lam, kmax, ex, ey, den)) e2 = ex * ex + ey * ey;
+  const int j = threadIdx.x;
+  double ex = 0.0, ey = 0.0, den, e2 = 0.0;
+  bool use = false;
+  if (j >= k && j < m) {
+    use = rf_pair(j, i, v.A, v.mu, v.evals, kmax, ex, ey, den);
+    if (use) e2 = ex * ex + ey * ey;
   }
-  e2 = block_sum(e2, red);
-  if (threadIdx.x == 0) alpha[i] = e2 > RF_SMAX ? sqrt(RF_SMAX / e2) : 1.0;
+  e2 = block_sum(e2, red);  // (its barriers also order every read of A before the writes)
+  const double alpha = e2 > RF_SMAX ? sqrt(RF_SMAX / e2) : 1.0;
+  if (j < k) {
+    const double2 rv = v.R[(size_t)j * kmax + i];
+    v.A[(size_t)j * kmax + i] = make_float2((float)(-0.5 * (rv.x - (j == i ? 1.0 : 0.0))), (float)(-0.5 * rv.y));
+  } else if (j < m) {
+    v.A[(size_t)j * kmax + i] = use ? make_float2((float)(alpha * ex), (float)(alpha * ey)) : make_float2(0.f, 0.f);
+  }
 }
 
 // Xout = Xin (I - (R - I) / 2), R = Xin^dag Xin summed from the split partials (FP64)
-__global__ void __launch_bounds__(RT* RT)
-    k_rf_lowdin(const double2* __restrict__ P, int splits, int m, const double2* __restrict__ Xin, int ldi,
-                const EigOut* __restrict__ eo, int kmax, double2* __restrict__ Xout, int ldo) {
-  const int k = eo->k < kmax ? eo->k : kmax;
-  const int r0 = blockIdx.y * RT, c0 = blockIdx.x * RT;
+__device__ __forceinline__ void rf_lowdin(const RfView& v, int st, int bx, int by) {
+  const int k = rf_k(v), m = v.m, kmax = v.kmax, splits = v.splits;
+  const double2* __restrict__ P = v.P;
+  const double2* __restrict__ Xin = rf_in(v, st);
+  const int ldi = rf_ldin(v, st);
+  double2* __restrict__ Xout = rf_out(v, st);
+  const int ldo = rf_ldout(v, st);
+  const int r0 = by * TM, c0 = bx * RT;
   if (c0 >= k || r0 >= m) return;
-  __shared__ double2 As[RT][RK + 1];  // Xin[row][j]
+  __shared__ double2 As[TM][RK + 1];  // Xin[row][j]
   __shared__ double2 Bs[RK][RT + 1];  // -(R - I)[j][col] / 2
   const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
   const size_t sstride = (size_t)(m + kmax) * kmax;
   double2 acc = make_double2(0.0, 0.0);
   for (int jb = 0; jb < k; jb += RK) {
-    for (int e = tid; e < RT * RK; e += RT * RT) {
+    for (int e = tid; e < TM * RK; e += TM * RT) {
       const int rr = e / RK, jj = e % RK;
       const int rw = r0 + rr, j = jb + jj;
       As[rr][jj] = (rw < m && j < k) ? Xin[(size_t)rw * ldi + j] : make_double2(0.0, 0.0);
     }
-    for (int e = tid; e < RK * RT; e += RT * RT) {
+    for (int e = tid; e < RK * RT; e += TM * RT) {
       const int jj = e / RT, cc = e % RT;
       const int j = jb + jj, cl = c0 + cc;
-      double2 v = make_double2(0.0, 0.0);
+      double2 x = make_double2(0.0, 0.0);
       if (j < k && cl < k) {
-        for (int s = 0; s < splits; ++s) v = cadd(v, P[s * sstride + (size_t)(m + j) * kmax + cl]);
-        v = make_double2(-0.5 * (v.x - (j == cl ? 1.0 : 0.0)), -0.5 * v.y);
+        for (int s = 0; s < splits; ++s) x = cadd(x, P[s * sstride + (size_t)(m + j) * kmax + cl]);
+        x = make_double2(-0.5 * (x.x - (j == cl ? 1.0 : 0.0)), -0.5 * x.y);
       }
-      Bs[jj][cc] = v;
+      Bs[jj][cc] = x;
     }
     __syncthreads();
 #pragma unroll 8
@@ -296,20 +356,103 @@ __global__ void __launch_bounds__(RT* RT)
   if (row < m && col < k) Xout[(size_t)row * ldo + col] = cadd(Xin[(size_t)row * ldi + col], acc);
 }
 
+// The last step's Rayleigh quotients without a second FP64 product with G: with
+// X the step's input, X0 the FP32 solve's vectors (still in evecs) and W0 = G X0
+// (the first step's FP64 product, whose split partials stay in P: later steps only
+// write X^dag X rows), Delta = X - X0 is small (about the FP32 solve's error), and
+//   x^dag G x = x0^dag w0 + 2 Re(Delta^dag w0) + Delta^dag (G Delta),
+// where the last term is second order in Delta, so G Delta is an FP32 product
+// (written over Res, idle after the first step).
+__device__ __forceinline__ void rf_gdelta(const RfView& v, int st, int bx, int by) {
+  const int k = rf_k(v), m = v.m, kmax = v.kmax;
+  const double2* __restrict__ G = v.G;
+  const double2* __restrict__ X = rf_in(v, st);
+  const int ldx = rf_ldin(v, st);
+  const double2* __restrict__ X0 = v.evecs;
+  const int r0 = by * TM, c0 = bx * RT;
+  if (c0 >= k || r0 >= m) return;
+  __shared__ float2 As[TM][RK + 1];  // G[row][kg]
+  __shared__ float2 Bs[RK][RT + 1];  // Delta[kg][col]
+  const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int kb = 0; kb < m; kb += RK) {
+    for (int e = tid; e < TM * RK; e += TM * RT) {
+      const int rr = e / RK, kk = e % RK;
+      const int kg = kb + kk, rw = r0 + rr;
+      float2 a = make_float2(0.f, 0.f);
+      if (kg < m && rw < m) {
+        const double2 g = G[(size_t)rw * m + kg];
+        a = make_float2((float)g.x, (float)g.y);
+      }
+      As[rr][kk] = a;
+    }
+    for (int e = tid; e < RK * RT; e += TM * RT) {
+      const int kk = e / RT, cc = e % RT;
+      const int kg = kb + kk, cl = c0 + cc;
+      float2 d = make_float2(0.f, 0.f);
+      if (kg < m && cl < k) {
+        const double2 x = X[(size_t)kg * ldx + cl], x0 = X0[(size_t)kg * m + cl];
+        d = make_float2((float)(x.x - x0.x), (float)(x.y - x0.y));
+      }
+      Bs[kk][cc] = d;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < RK; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
+    __syncthreads();
+  }
+  const int row = r0 + ty, col = c0 + tx;
+  if (row < m && col < k) v.Res[(size_t)row * kmax + col] = acc;
+}
+
+// mu2_i = x_i^dag G x_i / x_i^dag x_i (FP64 sums; x_i^dag x_i from the split partials of
+// the step's X^dag X); one block per kept column. direct = 0: from the expansion
+// above; direct = 1: from G X of this step's input, formed in P by the step's product.
+__device__ __forceinline__ void rf_mu2(const RfView& v, int st, int direct, int i) {
+  const int k = rf_k(v), m = v.m, kmax = v.kmax, splits = v.splits;
+  if (i >= k) return;
+  const double2* __restrict__ P = v.P;
+  const double2* __restrict__ X = rf_in(v, st);
+  const int ldx = rf_ldin(v, st);
+  __shared__ double red[32];
+  const int t = threadIdx.x;
+  const size_t sstride = (size_t)(m + kmax) * kmax;
+  double q = 0.0;
+  if (t < m) {
+    double2 w0 = make_double2(0.0, 0.0);
+    for (int s = 0; s < splits; ++s) w0 = cadd(w0, P[s * sstride + (size_t)t * kmax + i]);
+    const double2 x = X[(size_t)t * ldx + i];
+    if (direct) {
+      q = x.x * w0.x + x.y * w0.y;
+    } else {
+      const double2 x0 = v.evecs[(size_t)t * m + i];
+      const double2 d = csub(x, x0);
+      const float2 gd = v.Res[(size_t)t * kmax + i];
+      q = (x0.x * w0.x + x0.y * w0.y) + 2.0 * (d.x * w0.x + d.y * w0.y) + (d.x * (double)gd.x + d.y * (double)gd.y);
+    }
+  }
+  q = block_sum(q, red);
+  if (t == 0) {
+    double nrm = 0.0;
+    for (int s = 0; s < splits; ++s) nrm += P[s * sstride + (size_t)(m + i) * kmax + i].x;
+    v.mu2[i] = nrm > 0.0 ? q / nrm : 0.0;
+  }
+}
+
 // kept eigenvalues = FP64 Rayleigh quotients of the refined vectors, discarded mass =
 // trace(G) - their sum
-__global__ void __launch_bounds__(256)
-    k_rf_finish(const double* __restrict__ mu, double* __restrict__ evals, int m, EigOut* __restrict__ eo,
-                int kmax) {
+__device__ __forceinline__ void rf_finish(const RfView& v) {
   __shared__ double red[32];
-  const int k = eo->k < kmax ? eo->k : kmax;
+  const int k = rf_k(v), m = v.m;
+  const double* mu = v.mu2;
+  EigOut* eo = v.eo;
   const int t = threadIdx.x;
-  double v = 0.0;
+  double x = 0.0;
   if (t < k) {
-    v = mu[t];
-    evals[t] = v;
+    x = mu[t];
+    v.evals[t] = x;
   }
-  const double kept = block_sum(v, red);
+  const double kept = block_sum(x, red);
   if (t == 0) {
     // the trace the truncation removes (for a positive semidefinite G this is the sum
     // of the discarded eigenvalues up to rounding)
@@ -317,9 +460,118 @@ __global__ void __launch_bounds__(256)
     eo->dropped = eo->trace - kept;
     if (k < m) {
       const double l1 = fabs(mu[0]) > 0.0 ? fabs(mu[0]) : 1.0;
-      eo->gap = (mu[k - 1] - evals[k]) / l1;
+      eo->gap = (mu[k - 1] - v.evals[k]) / l1;
     }
   }
+}
+
+// Kernels: each phase as one truncation (task passed by value) or as a batch (task
+// blockIdx.z / zper of the array; zper = the blocks in z one truncation uses)
+enum RfPhase { RF_GEMM = 0, RF_RES, RF_PROJ, RF_COEFS, RF_UPDATE, RF_LOWDIN, RF_GDELTA, RF_MU2, RF_FINISH };
+
+template <int PHASE>
+__device__ __forceinline__ void rf_phase(const RefineTask& t, int a0, int a1, int bz) {
+  const RfView v = rf_view(t);
+  if constexpr (PHASE == RF_GEMM) rf_gemm64(v, a0, a1, blockIdx.x, blockIdx.y, bz);
+  else if constexpr (PHASE == RF_RES) rf_res(v, a0, blockIdx.x);
+  else if constexpr (PHASE == RF_PROJ) rf_proj(v, blockIdx.x, blockIdx.y);
+  else if constexpr (PHASE == RF_COEFS) rf_coefs(v, blockIdx.x);
+  else if constexpr (PHASE == RF_UPDATE) rf_update(v, a0, blockIdx.x, blockIdx.y);
+  else if constexpr (PHASE == RF_LOWDIN) rf_lowdin(v, a0, blockIdx.x, blockIdx.y);
+  else if constexpr (PHASE == RF_GDELTA) rf_gdelta(v, a0, blockIdx.x, blockIdx.y);
+  else if constexpr (PHASE == RF_MU2) rf_mu2(v, a0, a1, blockIdx.x);
+  else rf_finish(v);
+}
+
+template <int PHASE>
+__global__ void __launch_bounds__(256) k_rf(RefineTask t, int a0, int a1) {
+  rf_phase<PHASE>(t, a0, a1, blockIdx.z);
+}
+
+template <int PHASE>
+__global__ void __launch_bounds__(256) k_rf_batch(const RefineTask* __restrict__ tasks, int zper, int a0, int a1) {
+  rf_phase<PHASE>(tasks[blockIdx.z / zper], a0, a1, blockIdx.z % zper);
+}
+
+// Grid of one phase for a truncation of size m with kmax kept columns.
+struct RfGrid {
+  dim3 g;
+  int threads;
+};
+RfGrid rf_grid(int phase, int m, int kmax, int x_rows_only) {
+  const int kb = (kmax + RT - 1) / RT, splits = (m + RK - 1) / RK;
+  switch (phase) {
+    case RF_GEMM: return {dim3(kb, ((x_rows_only ? kmax : m + kmax) + RT - 1) / RT, splits), RT * RT};
+    case RF_RES: case RF_COEFS: case RF_MU2: return {dim3(kmax), 256};
+    case RF_PROJ: case RF_UPDATE: case RF_LOWDIN: case RF_GDELTA: return {dim3(kb, (m + TM - 1) / TM), TM * RT};
+    default: return {dim3(1), 256};
+  }
+}
+
+// Launches one phase: ntasks == 0 -> the single task t by value; else tasks[0..ntasks)
+// with the grid of the largest (m_max, kmax_max).
+template <int PHASE>
+void rf_launch(const RefineTask& t, const RefineTask* tasks, int ntasks, int m_max, int kmax_max, int a0, int a1,
+               cudaStream_t s) {
+  const int rows_only = PHASE == RF_GEMM ? a1 : 0;
+  RfGrid gr = ntasks == 0 ? rf_grid(PHASE, t.m, t.kmax < t.m ? t.kmax : t.m, rows_only)
+                          : rf_grid(PHASE, m_max, kmax_max, rows_only);
+  if (ntasks == 0) {
+    k_rf<PHASE><<<gr.g, gr.threads, 0, s>>>(t, a0, a1);
+  } else {
+    const int zper = (int)gr.g.z;
+    dim3 g = gr.g;
+    g.z = (unsigned)(zper * ntasks);
+    k_rf_batch<PHASE><<<g, gr.threads, 0, s>>>(tasks, zper, a0, a1);
+  }
+}
+
+// The whole refinement: `iters` correction steps, then RF_ORTHO orthonormalisation
+// steps. Step 0 reads evecs; step it > 0 reads Xa (it odd) or Xb (it even); every step
+// but the last writes the other scratch buffer, the last writes evecs.
+int rf_step_code(int it, int nsteps) {
+  const int in = it == 0 ? 0 : ((it - 1) % 2 == 0 ? 1 : 2);
+  const int out = it == nsteps - 1 ? 0 : (it % 2 == 0 ? 1 : 2);
+  return in | (out << 2);
+}
+
+cudaError_t rf_run(const RefineTask& t, const RefineTask* tasks, int ntasks, int m_max, int kmax_max, int iters,
+                   cudaStream_t s) {
+  const int nsteps = iters + RF_ORTHO;
+  long long launches = 0;
+  for (int it = 0; it < nsteps; ++it) {
+    const int st = rf_step_code(it, nsteps);
+    if (it < iters) {
+      rf_launch<RF_GEMM>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
+      rf_launch<RF_RES>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
+      rf_launch<RF_PROJ>(t, tasks, ntasks, m_max, kmax_max, 0, 0, s);
+      rf_launch<RF_COEFS>(t, tasks, ntasks, m_max, kmax_max, 0, 0, s);
+      rf_launch<RF_UPDATE>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
+      launches += 5;
+    } else if (it + 1 < nsteps) {
+      rf_launch<RF_GEMM>(t, tasks, ntasks, m_max, kmax_max, st, 1, s);
+      rf_launch<RF_LOWDIN>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
+      launches += 2;
+    } else if (iters == 1) {
+      // the last step's input is nearly orthonormal: its Rayleigh quotients (the kept
+      // eigenvalues) change only at second order in the step's tiny change; with one
+      // correction step, G X0 is still in P and the expansion of rf_gdelta applies
+      rf_launch<RF_GEMM>(t, tasks, ntasks, m_max, kmax_max, st, 1, s);
+      rf_launch<RF_GDELTA>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
+      rf_launch<RF_MU2>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
+      rf_launch<RF_LOWDIN>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
+      launches += 4;
+    } else {
+      // later correction steps overwrote G X0: form G X of this step's input in FP64
+      rf_launch<RF_GEMM>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
+      rf_launch<RF_MU2>(t, tasks, ntasks, m_max, kmax_max, st, 1, s);
+      rf_launch<RF_LOWDIN>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
+      launches += 3;
+    }
+  }
+  rf_launch<RF_FINISH>(t, tasks, ntasks, m_max, kmax_max, 0, 0, s);
+  note_launches(launches + 1);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -327,74 +579,27 @@ __global__ void __launch_bounds__(256)
 size_t eig_refine_work_bytes(int m) {
   const size_t kmax = (size_t)m;
   return (size_t)RF_SPLITS_MAX * (m + kmax) * kmax * sizeof(double2)  // P
-         + (size_t)m * kmax * sizeof(double2)                           // Xn
+         + (size_t)2 * m * kmax * sizeof(double2)                       // Xa, Xb
          + (size_t)kmax * kmax * sizeof(double2)                        // R
          + (size_t)m * kmax * sizeof(float2) * 2                        // Res, A
          + (size_t)3 * kmax * sizeof(double) + 256;                     // mu, mu2, alpha
 }
 
+int eig_refine_launches(int iters) { return 5 * iters + 2 * (RF_ORTHO - 1) + (iters == 1 ? 4 : 3) + 1; }
+
 cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* evecs, EigOut* eo, int kmax,
                               int iters, void* work, cudaStream_t s) {
   if (m < 2 || m > 256 || kmax < 1 || iters < 1) return cudaErrorInvalidValue;
-  if (kmax > m) kmax = m;
-  const int splits = (m + RK - 1) / RK;
-  char* p = (char*)work;
-  double2* P = (double2*)p;
-  p += (size_t)RF_SPLITS_MAX * (m + m) * m * sizeof(double2);
-  double2* Xn = (double2*)p;
-  p += (size_t)m * m * sizeof(double2);
-  double2* R = (double2*)p;
-  p += (size_t)m * m * sizeof(double2);
-  float2* Res = (float2*)p;
-  p += (size_t)m * m * sizeof(float2);
-  float2* A = (float2*)p;  // Xall^dag Res
-  p += (size_t)m * m * sizeof(float2);
-  double* mu = (double*)p;
-  double* mu2 = mu + m;     // Rayleigh quotients of the refined vectors
-  double* alpha = mu2 + m;  // damping of each kept column's step
-  const dim3 tb(RT * RT);
-  const dim3 g64((kmax + RT - 1) / RT, (m + kmax + RT - 1) / RT, splits);
-  const dim3 gR((kmax + RT - 1) / RT, (kmax + RT - 1) / RT, splits);
-  const dim3 g32((kmax + RT - 1) / RT, (m + RT - 1) / RT);
-  // `iters` correction steps, then RF_ORTHO orthonormalisation steps; the steps
-  // alternate between evecs' kept columns and Xn and the last one ends in evecs
-  const int nsteps = iters + RF_ORTHO;
-  for (int it = 0; it < nsteps; ++it) {
-    const bool to_evecs = ((nsteps - 1 - it) % 2) == 0;
-    const double2* Xin = to_evecs ? Xn : evecs;
-    const int ldi = to_evecs ? kmax : m;
-    double2* Xout = to_evecs ? evecs : Xn;
-    const int ldo = to_evecs ? m : kmax;
-    if (it == 0 && to_evecs) {
-      // an odd number of steps starts from a copy so input and output differ
-      cudaError_t e = cudaMemcpy2DAsync(Xn, kmax * sizeof(double2), evecs, m * sizeof(double2),
-                                        kmax * sizeof(double2), m, cudaMemcpyDeviceToDevice, s);
-      if (e != cudaSuccess) return e;
-    }
-    if (it < iters) {
-      k_rf_gemm64<<<g64, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, 0, P);
-      k_rf_res<<<kmax, 256, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, mu, R, Res);
-      k_rf_proj<<<g32, tb, 0, s>>>(evecs, m, Res, eo, kmax, A);
-      k_rf_damp<<<kmax, 256, 0, s>>>(A, evals, m, eo, kmax, mu, alpha);
-      k_rf_update<<<g32, tb, 0, s>>>(evecs, m, Xin, ldi, A, mu, evals, R, alpha, eo, kmax, Xout, ldo);
-      note_launches(5);
-    } else if (it + 1 < nsteps) {
-      k_rf_gemm64<<<gR, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, m, P);
-      k_rf_lowdin<<<g32, tb, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, Xout, ldo);
-      note_launches(2);
-    } else {
-      // the last step also forms G X: the kept eigenvalues are the Rayleigh quotients
-      // of its input (nearly orthonormal by now, so the step changes them only at
-      // second order in its tiny change)
-      k_rf_gemm64<<<g64, tb, 0, s>>>(G, m, Xin, ldi, eo, kmax, 0, P);
-      k_rf_res<<<kmax, 256, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, mu2, R, Res);
-      k_rf_lowdin<<<g32, tb, 0, s>>>(P, splits, m, Xin, ldi, eo, kmax, Xout, ldo);
-      note_launches(3);
-    }
-  }
-  k_rf_finish<<<1, 256, 0, s>>>(mu2, evals, m, eo, kmax);
-  note_launches(1);
-  return cudaGetLastError();
+  RefineTask t{G, m, kmax < m ? kmax : m, evals, evecs, eo, work};
+  return rf_run(t, nullptr, 0, 0, 0, iters, s);
+}
+
+cudaError_t launch_eig_refine_batch(const RefineTask* tasks, int ntasks, int m_max, int kmax_max, int iters,
+                                    cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (m_max < 2 || m_max > 256 || kmax_max < 1 || iters < 1) return cudaErrorInvalidValue;
+  RefineTask none{};
+  return rf_run(none, tasks, ntasks, m_max, kmax_max < m_max ? kmax_max : m_max, iters, s);
 }
 
 }  // namespace lret

@@ -625,7 +625,12 @@ __global__ void k_tadj_fa(const double2* __restrict__ C, const double2* __restri
   const double l1 = fabs(lam[0]) > 0 ? fabs(lam[0]) : 1.0;
   const double delta = lam[i] - lam[k + j];
   const double eta = 1e-12 * l1;
-  const double f = delta / (delta * delta + eta * eta);  // 1/delta, regularised at ties
+  // A discarded eigenvalue within the FP64 eigensolve's resolution of zero (4 m u64
+  // lambda_1) is a null direction of V' (V' u_j = 0 in exact arithmetic), and the pair's
+  // term, carried by V' u_j, vanishes; left in, the rounding-level |V' u_j| ~ sqrt(lambda_j)
+  // would be amplified by 1 / lambda_i for a small kept lambda_i.
+  const bool null_j = fabs(lam[k + j]) <= 4.0 * m * 1.1102230246251565e-16 * l1;
+  const double f = null_j ? 0.0 : delta / (delta * delta + eta * eta);  // 1/delta, regularised at ties
   FA[e] = make_double2(acc.x * f, acc.y * f);
 }
 

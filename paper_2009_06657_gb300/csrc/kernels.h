@@ -136,8 +136,10 @@ cudaError_t launch_trunc_batch_gemms(const TruncTask* tasks, const int* gram_bst
 int trunc_tiles(int c);
 int64_t trunc_chunk(int64_t N2, int splits);
 int trunc_proj_blocks(int64_t N2, int k);
+// T = the solver's arithmetic (float or double, independent of the state's type);
+// all_vecs != 0 returns every eigenvector (for a refinement that follows)
 template <typename T>
-cudaError_t launch_eigh_tri_batch(const TruncTask* tasks, int ntasks, cudaStream_t s);
+cudaError_t launch_eigh_tri_batch(const TruncTask* tasks, int ntasks, int all_vecs, cudaStream_t s);
 template <typename T>
 cudaError_t prepare_eigh_tri_batch();
 
@@ -200,6 +202,19 @@ size_t eigh_cluster_work_bytes(bool fp64);
 cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* evecs, EigOut* eo, int kmax,
                               int iters, void* work, cudaStream_t s);
 size_t eig_refine_work_bytes(int m);
+// The same for many truncations in the same launches (one task each; the grids are
+// sized for the largest m_max and kmax_max of the tasks).
+struct RefineTask {
+  const double2* G;
+  int m, kmax;
+  double* evals;
+  double2* evecs;
+  EigOut* eo;
+  void* work;  // eig_refine_work_bytes(m)
+};
+cudaError_t launch_eig_refine_batch(const RefineTask* tasks, int ntasks, int m_max, int kmax_max, int iters,
+                                    cudaStream_t s);
+int eig_refine_launches(int iters);  // kernel launches of one refinement
 
 // ---- adjoint of a truncation: builds Mcat ((k+m) x m complex128) =
 // [U_r^dag ; B + B^dag] with B = U_d (F o (U_d^dag C)) U_r^dag, F_ji = 1/(lam_i - lam_j).

@@ -360,7 +360,11 @@ class LRBatch:
     Semantics per circuit: truncation to rank r after every channel.
     """
 
-    def __init__(self, circuits, dtype="c64", rows_per_split=0, use_graph=True, stream=None):
+    def __init__(self, circuits, dtype="c64", rows_per_split=0, use_graph=True, stream=None,
+                 eig_precision="refined", eig_iters=1, splits=None):
+        """eig_precision (complex64): "refined" (FP32 solve + FP64 refinement of the kept
+        eigenvectors), "fp32" or "fp64". splits: None or one Gram split count per
+        circuit (0 = from rows_per_split), e.g. from autotune.BatchTable.splits_for."""
         if not torch.cuda.is_available():
             raise RuntimeError("liblret needs a CUDA device")
         self.dtype = _ffi.LR_C64 if dtype in ("c64", "complex64", _ffi.LR_C64) else _ffi.LR_C128
@@ -380,9 +384,23 @@ class LRBatch:
             self._keep.append(ops)
             arr[i].n, arr[i].r, arr[i].nops = int(cd["n"]), int(cd["r"]), len(cd["ops"])
             arr[i].ops = C.cast(ops, C.POINTER(_ffi.lr_op))
+        opts = _ffi.lr_batch_opts()
+        lib.lr_batch_opts_default(C.byref(opts))
+        opts.dtype = self.dtype
+        opts.eig_precision = {"refined": _ffi.LR_EIGP_REFINED, "fp32": _ffi.LR_EIGP_FP32,
+                              "fp64": _ffi.LR_EIGP_FP64}[eig_precision]
+        opts.eig_iters = int(eig_iters)
+        opts.rows_per_split = int(rows_per_split)
+        if splits is not None:
+            if len(splits) != len(circuits):
+                raise ValueError("splits needs one entry per circuit")
+            sp = (C.c_int * len(circuits))(*[int(x) for x in splits])
+            self._keep.append(sp)
+            opts.splits = C.cast(sp, C.POINTER(C.c_int))
+        opts.use_graph = 1 if use_graph else 0
+        opts.stream = self.stream.cuda_stream
         h = C.c_void_p()
-        check(lib.lr_batch_create(arr, len(circuits), self.dtype, int(rows_per_split), 1 if use_graph else 0,
-                                  C.c_void_p(self.stream.cuda_stream), C.byref(h)), "lr_batch_create")
+        check(lib.lr_batch_create_ex(arr, len(circuits), C.byref(opts), C.byref(h)), "lr_batch_create_ex")
         self.h = h
 
     def run(self):

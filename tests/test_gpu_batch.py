@@ -95,3 +95,58 @@ def test_heterogeneous_batch_workload_miniature(lr):
         assert float((sim.probs().double() - pb).abs().sum()) < inf["discarded"] + d1 + 1e-5
         sim.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["refined", "fp32", "fp64"])
+def test_batch_eigensolve_precisions_match_oracle(lr, prec):
+    """A complex64 batch with each eigensolve precision against the oracle: the
+    FP32 solve of every eigenvector with the FP64 refinement of the kept ones
+    (default), the FP32 solve alone, and the solver in FP64 arithmetic."""
+    circs = _small_batch()
+    b = lr.LRBatch(circs, dtype="c64", eig_precision=prec)
+    b.run()
+    for i, cd in enumerate(circs):
+        ref = O.run_lret(cd["n"], cd["ops"], r=cd["r"])
+        pb = b.probs(i).double().cpu().numpy()
+        inf = b.info(i)
+        assert inf["converged"]
+        assert np.sum(np.abs(pb - ref.probs())) < 1e-5, (prec, i)
+        assert abs(inf["discarded"] - ref.discarded) < 1e-5, (prec, i)
+    b.close()
+
+
+def test_refined_batch_matches_refined_single_runs(lr):
+    """The batched refinement (one launch per phase for all circuits of a step) and the
+    single-circuit refinement after the same tridiagonal FP32 solve."""
+    circs = _small_batch()
+    b = lr.LRBatch(circs, dtype="c64", eig_precision="refined")
+    b.run()
+    for i, cd in enumerate(circs):
+        sim = lr.LRSim(cd["n"], cd["r"], dtype="c64")
+        sim.set_eigensolver("tridiag")
+        sim.set_eig_precision("refined")
+        lr.run_ops(sim, cd["ops"], r=cd["r"])
+        p1 = sim.probs().double().cpu().numpy()
+        pb = b.probs(i).double().cpu().numpy()
+        # the two Gram matrices come from FP32 states through different kernels, so they
+        # (and the FP64 sums the refinement makes exact for each) differ at FP32 level
+        assert np.sum(np.abs(p1 - pb)) < 1e-5, i
+        assert abs(b.info(i)["discarded"] - sim.info()["discarded"]) < 1e-5, i
+        sim.close()
+    b.close()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_per_circuit_split_counts_do_not_change_results(lr, dtype):
+    """Per-circuit Gram split counts (as an autotuned table gives them) change only
+    the order of the Gram sums."""
+    circs = _small_batch()
+    tol = 1e-11 if dtype == "c128" else 1e-5
+    outs = []
+    for splits in (None, [64, 1, 3, 2, 16, 8]):
+        b = lr.LRBatch(circs, dtype=dtype, splits=splits)
+        b.run()
+        outs.append([(b.probs(i).double().cpu().numpy(), b.info(i)["discarded"]) for i in range(len(circs))])
+        b.close()
+    for (p0, d0), (p1, d1) in zip(*outs):
+        assert np.sum(np.abs(p0 - p1)) < tol and abs(d0 - d1) < tol

@@ -358,49 +358,59 @@ def test_full_size_properties(lr):
     assert bool((d[:-1] >= d[1:] - 1e-6).all())  # descending eigenvalue order
 
 
+# Width of the FP32 eigensolve's resolution window relative to lambda_1: eigenvalues
+# closer than this are tied for an FP32 solve, which may then keep either vector.
+RES32 = 16 * 2.0 ** -24
+
+
 def test_full_size_mixed_path_matches_fp64_path(lr):
     """20 qubits, r = 64, the benchmark's circuit family (first 12 channels: the
     state reaches 256 columns and is truncated several times): the FP32-state
-    path against this library's FP64 path on the same ops. A cut among nearly
-    equal small eigenvalues may keep different vectors in the two precisions,
-    which moves rho by at most about the discarded mass, so the bound is the
-    FP32 tolerance plus twice the discarded mass."""
+    path against this library's FP64 path on the same ops. At a cut whose gap
+    lambda_k - lambda_k+1 lies inside the FP32 resolution window the two
+    precisions may keep different vectors of the tied pair, which moves rho by at
+    most lambda_k + lambda_k+1 <= 2 lambda_k in trace norm; those cuts alone, read
+    from the FP64 path's truncation log, widen the FP32 tolerance."""
     n, r = 20, 64
     ops = _first_channels(random_layered(n, 1, seed=3000, noise=("dep", 5e-4)), 12)
     terms = random_pauli_sum(n, 64, seed=3001)
     out = {}
     for dtype in ("c64", "c128"):
         sim = lr.LRSim(n, r, dtype=dtype)
+        sim.set_trunc_log(4096)
         lr.run_ops(sim, ops, r=r)
         info = sim.info()
         assert info["columns"] == r and info["compressions"] >= 3 and info["converged"]
-        out[dtype] = (sim.probs().double().cpu().numpy(), sim.expect(terms), info["discarded"])
+        out[dtype] = (sim.probs().double().cpu().numpy(), sim.expect(terms), info["discarded"],
+                      sim.trunc_log())
         sim.close()
-    (p32, h32, d32), (p64, h64, d64) = out["c64"], out["c128"]
-    bound = TOL["c64"] + 2 * max(d32, d64)
+    (p32, h32, d32, log32), (p64, h64, d64, log64) = out["c64"], out["c128"]
+    assert [(e["m"], e["k"]) for e in log32] == [(e["m"], e["k"]) for e in log64]
+    tied = sum(2.0 * e["lambda_k"] for e in log64
+               if e["k"] < e["m"] and e["lambda_k"] - e["lambda_k1"] <= RES32 * e["lambda_1"])
+    bound = TOL["c64"] + tied
+    print(f"tied-cut allowance {tied:.3e}; L1 {np.sum(np.abs(p32 - p64)):.3e}; "
+          f"|dH|/sum|c| {abs(h32 - h64) / sum(abs(c) for c, _ in terms):.3e}")
     assert abs(d32 - d64) < TOL["c64"]
     assert np.sum(np.abs(p32 - p64)) < bound
     assert abs(h32 - h64) < bound * sum(abs(c) for c, _ in terms)
 
 
-# 3xTF32 products (TF32 high part x FP32 remainder, the remainder itself
-# truncated to TF32, the remainder product dropped) carry about 2^-21 relative
-# error; the probe of the tensor-core Gram measured 3.5e-7 against FP64.
-UNIT_TC = 5e-7
-
-
 @pytest.mark.parametrize("r,nchan,seed", [(32, 12, 3139), (64, 24, 3166)])
 def test_tensor_core_truncation_matches_oracle(lr, r, nchan, seed):
     """The tcgen05 Gram and projection of the row pairs (FP32 state, from 2^12
-    row pairs up) against the oracle and against the SIMT kernels. The bound is
-    the tolerance plus the predicted effect of the 3xTF32 rounding at the cuts
-    (unit roundoff x cut sensitivity, see _cut_sensitivity)."""
+    row pairs up; r = 64 reaches the benchmark's 256-column truncation) against the
+    oracle and against the SIMT kernels, at the FP32 tolerance itself. 3xTF32
+    products carry about 2^-21 relative error (TF32 high part x FP32 remainder, the
+    remainder truncated to TF32, the remainder product dropped); on 16 consecutive
+    seeds of the r = 64 case (3160-3175) the measured L1 error of Prob(x) against the
+    oracle was 2.3e-6 to 3.3e-6 (the SIMT FP32 kernels: 2e-7 to 7e-7)."""
     n = 14
     ops = random_layered(n, 1, seed=seed, noise=("dep", 5e-4), qubit_jitter=(0.5, 1.5))
     chans = [i for i, o in enumerate(ops) if O.is_channel(o)]
     ops = ops[: chans[nchan - 1] + 1]
     ref = O.run_lret(n, ops, r=r)
-    bound = 1e-5 + UNIT_TC * _cut_sensitivity(ref)
+    bound = TOL["c64"]
     out = {}
     for tc in (True, False):
         sim = lr.LRSim(n, r, dtype="c64")
