@@ -181,10 +181,10 @@ __device__ __forceinline__ void rf_res(const RfView& v, int st, int i) {
   }
 }
 
-// Row tile of the FP32 products and of the FP64 orthonormalisation: TM rows x RT
-// columns per block (TM x RT threads, one output each), so that a 256 x 64 output
-// spreads over 256 blocks.
-constexpr int TM = 4;
+// Row tile of the m x k products: TM rows x RT columns per block (TM x RT threads, one
+// output each; four-row tiles, measured, restage every coefficient four times as often
+// and ran slower)
+constexpr int TM = 16;
 
 // A = Xall^dag Res (m x k): x_j^dag res_i for every column j of the FP32 solve, an
 // FP32 product (res is small).
@@ -316,7 +316,14 @@ __device__ __forceinline__ void rf_coefs(const RfView& v, int i) {
   }
 }
 
-// Xout = Xin (I - (R - I) / 2), R = Xin^dag Xin summed from the split partials (FP64)
+// Xout = Xin (I - (R - I) / 2), R = Xin^dag Xin summed from the split partials (FP64).
+// The product Xin (R - I) / 2 is formed in FP64 where a coefficient of this block's
+// columns exceeds RF_LOW32 and in FP32 otherwise: with |R - I| <= 1e-9 the FP32
+// rounding of Xin and of the sums moves a column by at most about
+// 2^-24 sqrt(k) 1e-9 ~ 5e-16, below the FP64 accuracy the steps aim at. After the
+// correction step the deviation is the square of the corrections (1e-14 for
+// undamped columns), so the FP64 products are needed only behind damped columns.
+constexpr double RF_LOW32 = 1e-9;
 __device__ __forceinline__ void rf_lowdin(const RfView& v, int st, int bx, int by) {
   const int k = rf_k(v), m = v.m, kmax = v.kmax, splits = v.splits;
   const double2* __restrict__ P = v.P;
@@ -328,9 +335,29 @@ __device__ __forceinline__ void rf_lowdin(const RfView& v, int st, int bx, int b
   if (c0 >= k || r0 >= m) return;
   __shared__ double2 As[TM][RK + 1];  // Xin[row][j]
   __shared__ double2 Bs[RK][RT + 1];  // -(R - I)[j][col] / 2
+  __shared__ int s_big;
   const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
   const size_t sstride = (size_t)(m + kmax) * kmax;
+  auto coef = [&](int j, int cl) {
+    double2 x = make_double2(0.0, 0.0);
+    for (int s = 0; s < splits; ++s) x = cadd(x, P[s * sstride + (size_t)(m + j) * kmax + cl]);
+    return make_double2(-0.5 * (x.x - (j == cl ? 1.0 : 0.0)), -0.5 * x.y);
+  };
+  if (tid == 0) s_big = 0;
+  __syncthreads();
+  bool big = false;
+  for (int e = tid; e < k * RT; e += TM * RT) {
+    const int j = e / RT, cl = c0 + e % RT;
+    if (cl < k) {
+      const double2 x = coef(j, cl);
+      if (fabs(x.x) > RF_LOW32 || fabs(x.y) > RF_LOW32) big = true;
+    }
+  }
+  if (big) s_big = 1;
+  __syncthreads();
+  const bool f64 = s_big != 0;
   double2 acc = make_double2(0.0, 0.0);
+  float2 acc32 = make_float2(0.f, 0.f);
   for (int jb = 0; jb < k; jb += RK) {
     for (int e = tid; e < TM * RK; e += TM * RT) {
       const int rr = e / RK, jj = e % RK;
@@ -340,18 +367,22 @@ __device__ __forceinline__ void rf_lowdin(const RfView& v, int st, int bx, int b
     for (int e = tid; e < RK * RT; e += TM * RT) {
       const int jj = e / RT, cc = e % RT;
       const int j = jb + jj, cl = c0 + cc;
-      double2 x = make_double2(0.0, 0.0);
-      if (j < k && cl < k) {
-        for (int s = 0; s < splits; ++s) x = cadd(x, P[s * sstride + (size_t)(m + j) * kmax + cl]);
-        x = make_double2(-0.5 * (x.x - (j == cl ? 1.0 : 0.0)), -0.5 * x.y);
-      }
-      Bs[jj][cc] = x;
+      Bs[jj][cc] = (j < k && cl < k) ? coef(j, cl) : make_double2(0.0, 0.0);
     }
     __syncthreads();
+    if (f64) {
 #pragma unroll 8
-    for (int jj = 0; jj < RK; ++jj) cfma(acc, As[ty][jj], Bs[jj][tx]);
+      for (int jj = 0; jj < RK; ++jj) cfma(acc, As[ty][jj], Bs[jj][tx]);
+    } else {
+#pragma unroll 8
+      for (int jj = 0; jj < RK; ++jj) {
+        const double2 a = As[ty][jj], b = Bs[jj][tx];
+        cfma(acc32, make_float2((float)a.x, (float)a.y), make_float2((float)b.x, (float)b.y));
+      }
+    }
     __syncthreads();
   }
+  if (!f64) acc = make_double2((double)acc32.x, (double)acc32.y);
   const int row = r0 + ty, col = c0 + tx;
   if (row < m && col < k) Xout[(size_t)row * ldo + col] = cadd(Xin[(size_t)row * ldi + col], acc);
 }
@@ -484,12 +515,12 @@ __device__ __forceinline__ void rf_phase(const RefineTask& t, int a0, int a1, in
 }
 
 template <int PHASE>
-__global__ void __launch_bounds__(256) k_rf(RefineTask t, int a0, int a1) {
+__global__ void __launch_bounds__(256, 1) k_rf(RefineTask t, int a0, int a1) {
   rf_phase<PHASE>(t, a0, a1, blockIdx.z);
 }
 
 template <int PHASE>
-__global__ void __launch_bounds__(256) k_rf_batch(const RefineTask* __restrict__ tasks, int zper, int a0, int a1) {
+__global__ void __launch_bounds__(256, 1) k_rf_batch(const RefineTask* __restrict__ tasks, int zper, int a0, int a1) {
   rf_phase<PHASE>(tasks[blockIdx.z / zper], a0, a1, blockIdx.z % zper);
 }
 

@@ -378,6 +378,18 @@ int flush_all(lr_ctx* h) {
 
 // Per-truncation accounting; with a log buffer (cap > 0) also one record per truncation:
 // [m, k, lambda_1, lambda_k, lambda_{k+1}, discarded, trace, gap] (FP64).
+// U[a][k + j] -= T[a][j] (a < m, j < m - k): the discarded columns of the eigenvector
+// matrix made orthogonal to the kept ones (T = U_r (U_r^dag U_d))
+__global__ void k_sub_cols(double2* __restrict__ U, int m, int k, const double2* __restrict__ T) {
+  const int d = m - k;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * d) return;
+  const int a = e / d, j = e % d;
+  const double2 t = T[e];
+  double2& u = U[(size_t)a * m + k + j];
+  u = make_double2(u.x - t.x, u.y - t.y);
+}
+
 __global__ void k_accum(const EigOut* eo, const double* evals, int m, double* acc, double* log, int cap,
                         int64_t* nlog) {
   acc[0] += eo->dropped;
@@ -476,6 +488,19 @@ int run_eigh(lr_ctx* h, int m, int r_eff, double eps, int* k_out) {
     }
     te = tbeg(h);
     CK(launch_eig_refine(h->G, m, h->evals, h->evecs, h->eo, kmax, h->eig_iters, h->rf_work, h->stream));
+    if (h->record) {
+      // the adjoint (App. B derivative of the truncation) needs a complement basis
+      // orthogonal to the refined kept vectors: the FP32 discarded vectors carry
+      // components of about 2^-24 along them, which the 1 / (lambda_i - lambda_j) terms
+      // would amplify (one classical Gram-Schmidt pass in FP64; the workspace is free)
+      double2* W = (double2*)h->rf_work;
+      double2* T = W + (size_t)m * m;
+      const int d = m - kmax;
+      CK(launch_zgemm_small(h->evecs, m, 1, h->evecs + kmax, m, W, d, kmax, d, m, h->stream));
+      CK(launch_zgemm_small(h->evecs, m, 0, W, d, T, d, m, d, kmax, h->stream));
+      k_sub_cols<<<(m * d + 255) / 256, 256, 0, h->stream>>>(h->evecs, m, kmax, T);
+      note_launches(1);
+    }
     tend(h, LR_K_EIGREFINE, te);
   }
   k_accum<<<1, 1, 0, h->stream>>>(h->eo, h->evals, m, h->acc, h->tlog, h->tlog_cap, h->tlog_n);

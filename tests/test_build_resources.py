@@ -22,6 +22,7 @@ HOT = {
     "readout.cu": ["k_pauli_expect_gIfLi2E"],
     "expand.cu": ["k_expandIfLi4E"],
     "gemm.cu": ["k_gram_reduce_herm_f32x4"],
+    "eigh_refine.cu": ["k_rfILi", "k_rf_batchILi"],
 }
 
 
