@@ -557,15 +557,21 @@ def algorithmic():
     N, r, K, esz = 1 << N_QUBITS, RANK, 4, 8
     N2, m = N // 2, 4 * RANK
     return {
-        # Gram of the row pairs: (2r x 2r) Hermitian, N/2 rows, complex MAC = 8 flop, half by symmetry
-        "gram": {"flop": 8.0 * N2 * (2 * r) ** 2 / 2, "bytes": N * r * esz},
-        # projection on the row pairs: (N/2 x 2r) x (2r x 2r), read V and write V_new
-        "project": {"flop": 8.0 * N2 * (2 * r) * (2 * r), "bytes": 2 * N * r * esz},
+        # Gram of the row pairs: (2r x 2r) Hermitian, N/2 rows, complex MAC = 8 flop, half by symmetry.
+        # Issued tensor work: the real view (N/2 x 4r) Gram's upper triangle by 128-row blocks
+        # (128 x 256 + 128 x 128 at 4r = 256), three TF32 passes (hi hi, hi lo, lo hi)
+        "gram": {"flop": 8.0 * N2 * (2 * r) ** 2 / 2, "bytes": N * r * esz,
+                 "mma_flop": 3 * 2.0 * N2 * (128 * 4 * r + 128 * (4 * r - 128))},
+        # projection on the row pairs: (N/2 x 2r) x (2r x 2r), read V and write V_new; issued:
+        # the real (N/2 x 4r) x (4r x 4r) product, three TF32 passes
+        "project": {"flop": 8.0 * N2 * (2 * r) * (2 * r), "bytes": 2 * N * r * esz,
+                    "mma_flop": 3 * 2.0 * N2 * (4 * r) * (4 * r)},
         # Householder reduction of the m x m Hermitian matrix dominates: (16/3) m^3 flop
         "eigh": {"flop": 16.0 / 3.0 * m ** 3, "bytes": m * m * 16},
         # FP64 refinement of the kept eigenvectors: G X (m x m x r) and X^dag X (r x m x r) complex
-        # FP64 products, then two X^dag X for the orthonormalisation steps (FP32 products not counted)
-        "refine": {"flop": 8.0 * (m * m * r + 3 * r * m * r), "bytes": None},
+        # FP64 products, then X^dag X and the Lowdin product for each of the three
+        # orthonormalisation steps (FP32 products not counted)
+        "refine": {"flop": 8.0 * (m * m * r + 4 * r * m * r + 3 * m * r * r), "bytes": None},
         # expansion for two-qubit gates (gate only, K = 1): read and write V
         "expand": {"flop": None, "bytes": 2 * N * r * esz},
         "readout": {"flop": None, "bytes": N * r * esz + N * 4},
@@ -594,6 +600,10 @@ def kernel_rooflines(kt, peaks):
             e["hbm_frac"] = e["hbm_gbs"] / peaks["hbm_gbs"]
         if a["flop"]:
             e["tflops"] = a["flop"] / t / 1e12
+        if a.get("mma_flop"):
+            # tensor work the kernel issues (3xTF32 on the real view) against the TF32 dense peak
+            e["tensor_issued_tflops"] = a["mma_flop"] / t / 1e12
+            e["tensor_issued_frac"] = e["tensor_issued_tflops"] / peaks["tf32_tflops"]
         out[k] = e
     return out
 

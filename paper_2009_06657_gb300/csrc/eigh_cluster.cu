@@ -421,6 +421,40 @@ __device__ void tri_inverse_iteration(const ClusterShared<T>& sh, int lo, int hi
   }
 }
 
+// Out-of-line retry of a replacement vector that cancelled against the earlier ones
+// (a rarely taken path of the orthonormalisation, kept out of the kernel's register
+// allocation). Vector vec of the rank order, rv its remainder after the projection
+// with squared norm nr. A kept vector, or a discarded one above the FP32 noise floor,
+// on a block of T with more than one row: one inverse-iteration solve on that block
+// from the normalised remainder (the directions the earlier vectors do not span), so
+// repeated rounds deflate the members of an unresolved cluster that are already taken.
+// Otherwise (any direction of the noise-floor subspace will do) a pseudo-random vector.
+template <typename T>
+__device__ __noinline__ void replace_step(const ClusterShared<T>& sh, int vec, int m, const T* tnorm_p, T* rv, T nr,
+                                          int att) {
+  const int lane = threadIdx.x & 31;
+  const T tnorm = *tnorm_p;
+  T* sc = const_cast<T*>(reinterpret_cast<const T*>(&sh.A[0][0])) + (size_t)(MSL * MBK + 1 + CL_NW) * CL_MAXM;
+  const int pos = sh.order[vec];
+  const bool noise = vec >= sh.k && !(fabs(sh.lam[pos]) > (T)16 * CEps<T>::v * fabs(sh.lam[sh.order[0]]));
+  const int lo = sh.sblo[pos], hi = sh.sbhi[pos], sblk = hi - lo + 1;
+  if (!noise && sblk > 1 && att < 3) {
+    T* xs = sc + 4 * CL_MAXM;
+    const T inv = nr > (T)0 ? (T)1 / sqrt(nr) : (T)0;
+    for (int r2 = lane; r2 < sblk; r2 += 32) xs[r2] = nr > (T)0 ? rv[lo + r2] * inv : (T)(r2 == att);
+    __syncwarp();
+    tri_inverse_iteration<T>(sh, lo, hi, sh.lam[pos], tnorm, sc, xs, 1, lane);
+    for (int row = lane; row < CL_MAXM; row += 32) rv[row] = (row >= lo && row <= hi) ? xs[row - lo] : (T)0;
+  } else {
+    for (int row = lane; row < CL_MAXM; row += 32) {
+      unsigned h = (unsigned)(row + 1) * 2654435761u ^ ((unsigned)(vec + 1013 + att) * 40503u + 0x85ebca6bu);
+      h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12; h *= 0x297a2d39u; h ^= h >> 15;
+      rv[row] = row < m ? (T)(h & 0xffffu) * (T)(1.0 / 65536.0) - (T)0.5 : (T)0;
+    }
+  }
+  __syncwarp();
+}
+
 // Back-transform of the tridiagonal eigenvectors z (real, gZ) to those of the
 // Hermitian matrix, y = H_0 (H_1 (... H_{m-2} z)), into evecs (FP64 storage, column
 // normalised). Warp w of CTA `rank` carries the NC columns rank + CL (w + CL_NW c); the
@@ -1299,26 +1333,32 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
               if (tid == 0) atomicAdd(&out->sweeps, 1);  // diagnostics: replaced vectors
               const int nprev = MBK * b + t;
               project_rv(nprev);
-              if (warp == t) {
-                T nr = 0;
+              // cancelled again: inverse iteration on one eigenvalue of a cluster the FP32
+              // arithmetic does not separate keeps returning the member nearest the shift,
+              // which the earlier vectors already hold. Deflated inverse iteration: the
+              // remainder after the projection (the directions the earlier vectors do not
+              // span), normalised, starts another solve, projected again, up to four
+              // rounds. Only a discarded vector in the FP32 noise floor (any direction of
+              // that subspace will do) or a one-row block takes a plain pseudo-random vector.
+              // (the round count lives in shared memory: registers are tight here)
+              __shared__ int s_att;
+              if (tid == 0) s_att = 0;
+              for (;;) {
+                if (warp == t) {
+                  T nr = 0;
 #pragma unroll
-                for (int e = 0; e < E; ++e) nr += rv[lane + 32 * e] * rv[lane + 32 * e];
-                nr = warp_sum(nr);
-                // cancelled again (inverse iteration returned a vector of the span of the
-                // earlier ones): a plain pseudo-random vector, projected once more below
-                if (lane == 0) s_flag = nr > (T)1e-6 ? 0 : 2;
-                if (!(nr > (T)1e-6)) {
-#pragma unroll
-                  for (int e = 0; e < E; ++e) {
-                    const int row = lane + 32 * e;
-                    unsigned h = (unsigned)(row + 1) * 2654435761u ^ ((unsigned)(vec + 1013) * 40503u + 0x85ebca6bu);
-                    h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12; h *= 0x297a2d39u; h ^= h >> 15;
-                    if (row < CL_MAXM) rv[row] = row < m ? (T)(h & 0xffffu) * (T)(1.0 / 65536.0) - (T)0.5 : (T)0;
-                  }
+                  for (int e = 0; e < E; ++e) nr += rv[lane + 32 * e] * rv[lane + 32 * e];
+                  nr = warp_sum(nr);
+                  const bool ok = nr > (T)1e-6 || s_att >= 4;
+                  __syncwarp();
+                  if (lane == 0) s_flag = ok ? 0 : 2;
+                  if (!ok) replace_step<T>(sh, vec, m, &s_tnorm, rv, nr, s_att);
                 }
+                __syncthreads();
+                if (s_flag == 0) break;
+                if (tid == 0) ++s_att;
+                project_rv(nprev);
               }
-              __syncthreads();
-              if (s_flag == 2) project_rv(nprev);
               if (warp == t) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) w[e] = rv[lane + 32 * e];

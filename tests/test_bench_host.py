@@ -31,7 +31,7 @@ def test_algorithmic_work_per_launch():
 
 
 def test_kernel_rooflines_rates():
-    peaks = {"hbm_gbs": 6000.0}
+    peaks = {"hbm_gbs": 6000.0, "tf32_tflops": 900.0}
     kt = {"gram": (10.0, 40), "eigh": (60.0, 60), "pauli": (7.5, 1), "unknown": (1.0, 1), "readout": (0.0, 0)}
     out = bench.kernel_rooflines(kt, peaks)
     assert set(out) == {"gram", "eigh", "pauli"}  # no launches or no model: no row
@@ -40,6 +40,10 @@ def test_kernel_rooflines_rates():
     assert g["hbm_gbs"] == pytest.approx(536_870_912 / 0.25e-3 / 1e9)
     assert g["hbm_frac"] == pytest.approx(g["hbm_gbs"] / 6000.0)
     assert g["tflops"] == pytest.approx(8 * 2**19 * 128 * 128 / 2 / 0.25e-3 / 1e12)
+    # issued 3xTF32 work: three passes over the real view's upper triangle by 128-row blocks
+    issued = 3 * 2 * 2**19 * (128 * 256 + 128 * 128)
+    assert g["tensor_issued_tflops"] == pytest.approx(issued / 0.25e-3 / 1e12)
+    assert g["tensor_issued_frac"] == pytest.approx(g["tensor_issued_tflops"] / 900.0)
     e = out["eigh"]
     assert e["tflops"] == pytest.approx(16 / 3 * 256**3 / 1e-3 / 1e12)  # 1 ms per solve: 0.0895 TFLOP/s
     assert "tflops" not in out["pauli"]

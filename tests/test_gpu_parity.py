@@ -498,3 +498,24 @@ def test_deferred_projection_matches_oracle_and_eager_projection(lr, dtype):
     p1 = sim.probs().double().cpu().numpy()
     p2 = sim2.probs().double().cpu().numpy()
     assert np.sum(np.abs(p1 - p2)) < tol
+
+
+@pytest.mark.parametrize("solver", ["auto", "cluster", "tridiag"])
+def test_highly_degenerate_kept_clusters(lr, solver):
+    """A depolarizing channel with p = 0.5 on every qubit of a 6-qubit state, then an
+    ansatz layer stack with identical channels: at full rank (r = 64) every truncation
+    keeps a product-like spectrum with clusters of up to 20 equal eigenvalues (the
+    binomial multiplicities of (2/3, 1/3)^6) and drops 192 null directions. Inverse
+    iteration on such a cluster keeps returning the member nearest the shift; the
+    solvers must still return an orthonormal basis of the whole cluster (complex64 state,
+    FP32 solve with the FP64 refinement)."""
+    n = 6
+    ops, _ = hea(n, 6, seed=4100, noise=("dep", 1e-2))
+    ops = [{"op": "dep", "q": q, "p": 0.5} for q in range(n)] + ops
+    terms = random_pauli_sum(n, 20, seed=4101)
+    ref = O.run_lret(n, ops, r=2 ** n)
+    sim = lr.LRSim(n, 2 ** n, dtype="c64")
+    sim.set_eigensolver(solver)
+    lr.run_ops(sim, ops, r=2 ** n)
+    _compare(lr, sim, ref, n, terms, TOL["c64"])
+    sim.close()
