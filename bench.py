@@ -628,6 +628,22 @@ def profile_case(n, solver="auto", eig_precision="refined"):
     sim.close()
 
 
+def profile_batch(scale):
+    """One run of the batched workload (256 circuits of the benchmark's batch family,
+    depths scaled by `scale`) for profilers: no timing, no single-circuit comparison."""
+    import torch
+
+    import paper_2009_06657_gb300 as lr
+    from paper_2009_06657_gb300.autotune import BatchTable
+    from workloads import batch_circuits
+    circs = batch_circuits(count=256, depth_scale=scale)
+    b = lr.LRBatch(circs, dtype="c64", splits=BatchTable.load_or_empty().splits_for(circs))
+    b.run()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_batch": scale, "stats": b.stats()}))
+    b.close()
+
+
 def profile_readouts(n):
     """A short run for profilers of the kernels beyond the truncation: one dense
     13-qubit Grover iterate (8192 x 8192 unitary on 41 columns), then on an n-qubit
@@ -662,6 +678,8 @@ def main():
                     help="run only the dense-gate and readout kernels on an n-qubit state for profilers and exit")
     ap.add_argument("--profile-case", type=int, default=0,
                     help="run only a short n-qubit case for profilers (no timing) and exit")
+    ap.add_argument("--profile-batch", type=float, default=0.0,
+                    help="run only the batched workload once at this depth scale for profilers and exit")
     ap.add_argument("--profile-solver", default="auto", choices=["auto", "tridiag", "cluster", "jacobi"],
                     help="eigensolver of --profile-case")
     ap.add_argument("--profile-eig-precision", default="refined", choices=["refined", "fp32", "fp64"],
@@ -681,6 +699,9 @@ def main():
     args = ap.parse_args()
     if args.profile_readouts:
         profile_readouts(args.profile_readouts)
+        return
+    if args.profile_batch:
+        profile_batch(args.profile_batch)
         return
     if args.profile_case:
         profile_case(args.profile_case, args.profile_solver, args.profile_eig_precision)

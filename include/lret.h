@@ -147,7 +147,11 @@ int lr_set_path(lr_handle h, int which);
 /* Tensor cores for the FP32 state's Gram of the row pairs and projection on
  * the row pairs (tcgen05, 3xTF32 products, FP32 accumulation; Gram split
  * partials summed in FP64): on = 1 (default) where the shape allows it, 0 =
- * the SIMT kernels everywhere.
+ * the SIMT kernels everywhere. The tensor core's FP32 accumulation shrinks a
+ * projected state by about 2e-7 per projection; with tensor cores on, each
+ * projected state is rescaled so that Tr rho = 1 - the discarded mass so far
+ * (exact for LRET with complete Kraus sets), the scale folded into the next
+ * truncation or applied before any other use of the state.
  * lr_get_info returns LR_ETIMEOUT if a bounded wait in a tensor-core kernel or
  * in the cluster eigensolver gave up. */
 int lr_set_tensor_cores(lr_handle h, int on);
@@ -346,6 +350,7 @@ typedef struct lr_batch_opts {
   const int* splits;
   int use_graph;
   void* stream;
+  int tensor_cores;  /* LR_C64: tcgen05 Gram for truncations it suits (default 1) */
 } lr_batch_opts;
 void lr_batch_opts_default(lr_batch_opts* o);
 int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opts* opts, lr_batch_handle* out);

@@ -39,6 +39,8 @@ struct Circ {
   EigOut* eo = nullptr;
   void* eigwork = nullptr;
   void* rfwork = nullptr;  // FP64 refinement workspace (refined eigensolve)
+  int64_t tc_rows = 0;     // rows per split of the tensor-core Gram (0: not eligible)
+  int tc_splits = 0;
   int64_t gates = 0, truncs = 0;
 };
 
@@ -46,6 +48,7 @@ struct Step {
   int e_off = 0, e_cnt = 0, e_blocks = 0, eb_off = 0;
   int t_off = 0, t_cnt = 0, gram_blocks = 0, proj_blocks = 0, gb_off = 0, pb_off = 0, max_m2 = 0, max_d = 0;
   int max_m = 0, max_k = 0;  // largest Gram size and rank of the step's truncations
+  int tg_off = 0, tg_blocks = 0;  // tensor-core Gram of the step's eligible truncations
 };
 
 
@@ -80,6 +83,8 @@ struct lr_batch {
   ExpandTask* d_et = nullptr;
   TruncTask* d_tt = nullptr;
   RefineTask* d_rt = nullptr;  // one per truncation task, same order (refined eigensolve)
+  int* d_status = nullptr;     // set by a tensor-core kernel whose bounded wait gave up
+  bool any_tc = false;
   int* d_bs = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -218,6 +223,7 @@ int init_states(lr_batch* b) {
     }
     BCK(cudaMemsetAsync(C.acc, 0, sizeof(double) * 8, b->stream));
   }
+  BCK(cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
   BCK(cudaStreamSynchronize(b->stream));
   return LR_OK;
 }
@@ -236,6 +242,7 @@ int enqueue(lr_batch* b) {
     }
     if (st.t_cnt) {
       const TruncTask* tt = b->d_tt + st.t_off;
+      if (st.tg_blocks) BCK(launch_gram_pair_tc_batch(tt, b->d_bs + st.tg_off, st.tg_blocks, st.t_cnt, b->stream));
       BCK(by_dt(dt, [&](auto t) {
         return launch_trunc_batch_gemms<decltype(t)>(tt, b->d_bs + st.gb_off, st.gram_blocks, b->d_bs + st.pb_off,
                                                      st.proj_blocks, st.t_cnt, st.max_m2, st.max_d, 0, b->stream);
@@ -274,6 +281,7 @@ int lr_batch_free(lr_batch_handle b) {
   if (b->d_et) cudaFree(b->d_et);
   if (b->d_tt) cudaFree(b->d_tt);
   if (b->d_rt) cudaFree(b->d_rt);
+  if (b->d_status) cudaFree(b->d_status);
   if (b->d_bs) cudaFree(b->d_bs);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -289,6 +297,7 @@ void lr_batch_opts_default(lr_batch_opts* o) {
   o->splits = nullptr;
   o->use_graph = 1;
   o->stream = nullptr;
+  o->tensor_cores = 1;
 }
 
 int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_per_split, int use_graph,
@@ -328,6 +337,10 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
   b->esz = dtype == LR_C64 ? sizeof(float2) : sizeof(double2);
   b->use_graph = use_graph;
   b->circ.resize(count);
+  if (bmalloc(b, (void**)&b->d_status, sizeof(int)) != LR_OK) {
+    lr_batch_free(b);
+    return LR_ENOMEM;
+  }
   std::vector<std::vector<HStage>> stages(count);
   size_t max_stages = 0;
   int rc = LR_OK;
@@ -352,11 +365,23 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
       splits = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)64, N2, (int64_t)opts->splits[i]}));
     C.splits = splits;
     const int m = 4 * cd.r, c2 = 2 * cd.r;
+    // tensor-core Gram for a complex64 state with at least 2^12 row pairs
+    // (per truncation the column counts must also suit them): splits of at least 2048
+    // row pairs, at most 64 of them
+    size_t part_bytes = sizeof(double2) * (size_t)splits * c2 * c2;
+    if (dtype == LR_C64 && opts->tensor_cores && gram_pair_tc_supported(8, N2)) {
+      int64_t rows = std::max<int64_t>(2048, (N2 + 63) / 64);
+      rows = ((rows + 31) / 32) * 32;
+      C.tc_rows = rows;
+      C.tc_splits = (int)((N2 + rows - 1) / rows);
+      part_bytes = std::max(part_bytes, sizeof(float2) * (size_t)C.tc_splits * c2 * c2);
+    }
     const size_t slab = (size_t)C.N * C.cap * b->esz;
     rc = bmalloc(b, &C.buf[0], slab);
     if (!rc) rc = bmalloc(b, &C.buf[1], slab);
     if (!rc) rc = bmalloc(b, (void**)&C.acc, sizeof(double) * 8);
-    if (!rc) rc = bmalloc(b, (void**)&C.partials, sizeof(double2) * (size_t)splits * c2 * c2);
+    if (!rc) rc = bmalloc(b, (void**)&C.partials, part_bytes);
+
     if (!rc) rc = bmalloc(b, (void**)&C.G, sizeof(double2) * (size_t)m * m);
     if (!rc) rc = bmalloc(b, (void**)&C.evecs, sizeof(double2) * (size_t)m * m);
     if (!rc) rc = bmalloc(b, (void**)&C.D, sizeof(double2) * (size_t)c2 * c2);
@@ -379,7 +404,7 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
     Step& S = b->steps[s];
     S.e_off = (int)et.size();
     S.t_off = (int)tt.size();
-    std::vector<int> eblocks, gblocks, pblocks;
+    std::vector<int> eblocks, gblocks, pblocks, tgblocks;
     for (int i = 0; i < count; ++i) {
       if (s >= stages[i].size()) continue;
       const HStage& h = stages[i][s];
@@ -426,12 +451,24 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
         t.eigwork = C.eigwork;
         t.D = C.D;
         t.acc = C.acc;
+        t.status = b->d_status;
+        t.tc = C.tc_rows > 0 && gram_pair_tc_supported(t.c, t.N2);
+        if (t.tc) {
+          t.tc_rows = C.tc_rows;
+          t.splits = C.tc_splits;
+          b->any_tc = true;
+        }
         tt.push_back(t);
         rt.push_back(RefineTask{C.G, t.m, t.k, C.evals, C.evecs, C.eo, C.rfwork});
         S.max_m = std::max(S.max_m, t.m);
         S.max_k = std::max(S.max_k, t.k);
-        gblocks.push_back(t.tiles * t.splits);
+        // tensor-core Gram where it applies; the projection stays on the SIMT kernel
+        // (the tensor core's FP32 accumulation shrinks a projected state by about 2e-7
+        // per launch, which the single-circuit runtime anchors to the exact trace and the
+        // batch does not)
+        gblocks.push_back(t.tc ? 0 : t.tiles * t.splits);
         pblocks.push_back(trunc_proj_blocks(t.N2, t.k));
+        tgblocks.push_back(t.tc ? t.splits : 0);
         S.max_m2 = std::max(S.max_m2, t.m * t.m);
         S.max_d = std::max(S.max_d, 4 * t.c * t.k);
         ++C.truncs;
@@ -453,6 +490,7 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
     if (S.t_cnt) {
       prefix(gblocks, &S.gb_off, &S.gram_blocks);
       prefix(pblocks, &S.pb_off, &S.proj_blocks);
+      prefix(tgblocks, &S.tg_off, &S.tg_blocks);
     }
     b->launches += (S.e_cnt ? 1 : 0) + (S.t_cnt ? 6 : 0);
     if (S.t_cnt && !solve_fp64(b) && b->eig_prec == LR_EIGP_REFINED) b->launches += eig_refine_launches(b->eig_iters);
@@ -473,6 +511,7 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
     e = cudaMemcpy(b->d_rt, rt.data(), sizeof(RefineTask) * rt.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !bs.empty()) e = cudaMemcpy(b->d_bs, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = solve_fp64(b) ? prepare_eigh_tri_batch<double>() : prepare_eigh_tri_batch<float>();
+  if (e == cudaSuccess && b->any_tc) e = prepare_gram_tc_batch();
   if (e != cudaSuccess) {
     lret::set_error("%s: %s", "batch setup", cudaGetErrorString(e));
     lr_batch_free(b);
@@ -529,7 +568,9 @@ int lr_batch_info(lr_batch_handle b, int i, lr_info* info) {
   if (!b || !info || i < 0 || i >= b->count) return LR_EINVAL;
   const Circ& C = b->circ[i];
   double acc[8];
+  int st = 0;
   BCK(cudaMemcpyAsync(acc, C.acc, sizeof(acc), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   BCK(cudaStreamSynchronize(b->stream));
   info->n = C.n;
   info->columns = C.c;
@@ -539,6 +580,10 @@ int lr_batch_info(lr_batch_handle b, int i, lr_info* info) {
   info->stages = C.truncs;
   info->discarded = acc[0];
   info->last_gap = acc[1];
+  if (st) {
+    lret::set_error("%s: %s", "lr_batch_info", "a bounded wait of a tensor-core kernel gave up");
+    return LR_ETIMEOUT;
+  }
   return acc[2] > 0 ? LR_ENOCONV : LR_OK;
 }
 

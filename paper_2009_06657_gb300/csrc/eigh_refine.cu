@@ -29,10 +29,9 @@
 // amplify that. So the runtime runs one step (iters = 1) followed by three FP64
 // orthonormalisation steps X <- X (I - (X^dag X - I) / 2), each of which squares
 // the deviation from orthonormality. The kept eigenvalues are the FP64 Rayleigh
-// quotients of the input of the last of those steps, from G X0 of the correction
-// step and a second-order FP32 term (rf_gdelta). Only G X, X^dag X and the Lowdin
-// product X (R - I) / 2 are FP64 products; the complement projections, the update and
-// the second-order term are FP32 products of small quantities.
+// quotients of the input of the last of those steps (G X formed once more in FP64).
+// Only G X, X^dag X and the Lowdin product X (R - I) / 2 are FP64 products; the
+// complement projections and the update are FP32 products of small quantities.
 // Kept vectors are not rotated among themselves (that leaves rho unchanged), so a
 // kept eigenvalue inside a cluster the FP32 solve did not resolve (spread below
 // about u32 |G|) is the Rayleigh quotient of a vector of that cluster; the sum of
@@ -387,59 +386,9 @@ __device__ __forceinline__ void rf_lowdin(const RfView& v, int st, int bx, int b
   if (row < m && col < k) Xout[(size_t)row * ldo + col] = cadd(Xin[(size_t)row * ldi + col], acc);
 }
 
-// The last step's Rayleigh quotients without a second FP64 product with G: with
-// X the step's input, X0 the FP32 solve's vectors (still in evecs) and W0 = G X0
-// (the first step's FP64 product, whose split partials stay in P: later steps only
-// write X^dag X rows), Delta = X - X0 is small (about the FP32 solve's error), and
-//   x^dag G x = x0^dag w0 + 2 Re(Delta^dag w0) + Delta^dag (G Delta),
-// where the last term is second order in Delta, so G Delta is an FP32 product
-// (written over Res, idle after the first step).
-__device__ __forceinline__ void rf_gdelta(const RfView& v, int st, int bx, int by) {
-  const int k = rf_k(v), m = v.m, kmax = v.kmax;
-  const double2* __restrict__ G = v.G;
-  const double2* __restrict__ X = rf_in(v, st);
-  const int ldx = rf_ldin(v, st);
-  const double2* __restrict__ X0 = v.evecs;
-  const int r0 = by * TM, c0 = bx * RT;
-  if (c0 >= k || r0 >= m) return;
-  __shared__ float2 As[TM][RK + 1];  // G[row][kg]
-  __shared__ float2 Bs[RK][RT + 1];  // Delta[kg][col]
-  const int tx = threadIdx.x % RT, ty = threadIdx.x / RT, tid = threadIdx.x;
-  float2 acc = make_float2(0.f, 0.f);
-  for (int kb = 0; kb < m; kb += RK) {
-    for (int e = tid; e < TM * RK; e += TM * RT) {
-      const int rr = e / RK, kk = e % RK;
-      const int kg = kb + kk, rw = r0 + rr;
-      float2 a = make_float2(0.f, 0.f);
-      if (kg < m && rw < m) {
-        const double2 g = G[(size_t)rw * m + kg];
-        a = make_float2((float)g.x, (float)g.y);
-      }
-      As[rr][kk] = a;
-    }
-    for (int e = tid; e < RK * RT; e += TM * RT) {
-      const int kk = e / RT, cc = e % RT;
-      const int kg = kb + kk, cl = c0 + cc;
-      float2 d = make_float2(0.f, 0.f);
-      if (kg < m && cl < k) {
-        const double2 x = X[(size_t)kg * ldx + cl], x0 = X0[(size_t)kg * m + cl];
-        d = make_float2((float)(x.x - x0.x), (float)(x.y - x0.y));
-      }
-      Bs[kk][cc] = d;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < RK; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
-    __syncthreads();
-  }
-  const int row = r0 + ty, col = c0 + tx;
-  if (row < m && col < k) v.Res[(size_t)row * kmax + col] = acc;
-}
-
-// mu2_i = x_i^dag G x_i / x_i^dag x_i (FP64 sums; x_i^dag x_i from the split partials of
-// the step's X^dag X); one block per kept column. direct = 0: from the expansion
-// above; direct = 1: from G X of this step's input, formed in P by the step's product.
-__device__ __forceinline__ void rf_mu2(const RfView& v, int st, int direct, int i) {
+// mu2_i = x_i^dag G x_i / x_i^dag x_i from G X and X^dag X of this step's input (split
+// partials in P, summed in FP64); one block per kept column.
+__device__ __forceinline__ void rf_mu2(const RfView& v, int st, int i) {
   const int k = rf_k(v), m = v.m, kmax = v.kmax, splits = v.splits;
   if (i >= k) return;
   const double2* __restrict__ P = v.P;
@@ -453,14 +402,7 @@ __device__ __forceinline__ void rf_mu2(const RfView& v, int st, int direct, int 
     double2 w0 = make_double2(0.0, 0.0);
     for (int s = 0; s < splits; ++s) w0 = cadd(w0, P[s * sstride + (size_t)t * kmax + i]);
     const double2 x = X[(size_t)t * ldx + i];
-    if (direct) {
-      q = x.x * w0.x + x.y * w0.y;
-    } else {
-      const double2 x0 = v.evecs[(size_t)t * m + i];
-      const double2 d = csub(x, x0);
-      const float2 gd = v.Res[(size_t)t * kmax + i];
-      q = (x0.x * w0.x + x0.y * w0.y) + 2.0 * (d.x * w0.x + d.y * w0.y) + (d.x * (double)gd.x + d.y * (double)gd.y);
-    }
+    q = x.x * w0.x + x.y * w0.y;
   }
   q = block_sum(q, red);
   if (t == 0) {
@@ -498,7 +440,7 @@ __device__ __forceinline__ void rf_finish(const RfView& v) {
 
 // Kernels: each phase as one truncation (task passed by value) or as a batch (task
 // blockIdx.z / zper of the array; zper = the blocks in z one truncation uses)
-enum RfPhase { RF_GEMM = 0, RF_RES, RF_PROJ, RF_COEFS, RF_UPDATE, RF_LOWDIN, RF_GDELTA, RF_MU2, RF_FINISH };
+enum RfPhase { RF_GEMM = 0, RF_RES, RF_PROJ, RF_COEFS, RF_UPDATE, RF_LOWDIN, RF_MU2, RF_FINISH };
 
 template <int PHASE>
 __device__ __forceinline__ void rf_phase(const RefineTask& t, int a0, int a1, int bz) {
@@ -509,8 +451,7 @@ __device__ __forceinline__ void rf_phase(const RefineTask& t, int a0, int a1, in
   else if constexpr (PHASE == RF_COEFS) rf_coefs(v, blockIdx.x);
   else if constexpr (PHASE == RF_UPDATE) rf_update(v, a0, blockIdx.x, blockIdx.y);
   else if constexpr (PHASE == RF_LOWDIN) rf_lowdin(v, a0, blockIdx.x, blockIdx.y);
-  else if constexpr (PHASE == RF_GDELTA) rf_gdelta(v, a0, blockIdx.x, blockIdx.y);
-  else if constexpr (PHASE == RF_MU2) rf_mu2(v, a0, a1, blockIdx.x);
+  else if constexpr (PHASE == RF_MU2) rf_mu2(v, a0, blockIdx.x);
   else rf_finish(v);
 }
 
@@ -534,7 +475,7 @@ RfGrid rf_grid(int phase, int m, int kmax, int x_rows_only) {
   switch (phase) {
     case RF_GEMM: return {dim3(kb, ((x_rows_only ? kmax : m + kmax) + RT - 1) / RT, splits), RT * RT};
     case RF_RES: case RF_COEFS: case RF_MU2: return {dim3(kmax), 256};
-    case RF_PROJ: case RF_UPDATE: case RF_LOWDIN: case RF_GDELTA: return {dim3(kb, (m + TM - 1) / TM), TM * RT};
+    case RF_PROJ: case RF_UPDATE: case RF_LOWDIN: return {dim3(kb, (m + TM - 1) / TM), TM * RT};
     default: return {dim3(1), 256};
   }
 }
@@ -583,19 +524,14 @@ cudaError_t rf_run(const RefineTask& t, const RefineTask* tasks, int ntasks, int
       rf_launch<RF_GEMM>(t, tasks, ntasks, m_max, kmax_max, st, 1, s);
       rf_launch<RF_LOWDIN>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
       launches += 2;
-    } else if (iters == 1) {
-      // the last step's input is nearly orthonormal: its Rayleigh quotients (the kept
-      // eigenvalues) change only at second order in the step's tiny change; with one
-      // correction step, G X0 is still in P and the expansion of rf_gdelta applies
-      rf_launch<RF_GEMM>(t, tasks, ntasks, m_max, kmax_max, st, 1, s);
-      rf_launch<RF_GDELTA>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
-      rf_launch<RF_MU2>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
-      rf_launch<RF_LOWDIN>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
-      launches += 4;
     } else {
-      // later correction steps overwrote G X0: form G X of this step's input in FP64
+      // the last step's input is nearly orthonormal: its Rayleigh quotients (the kept
+      // eigenvalues) change only at second order in the step's tiny change; G X of the
+      // input in FP64 (a second-order expansion around G X0 with an FP32 G Delta,
+      // measured, lost 5e-10 of lambda_1 where the correction step moved a vector by
+      // more than about 1e-3)
       rf_launch<RF_GEMM>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
-      rf_launch<RF_MU2>(t, tasks, ntasks, m_max, kmax_max, st, 1, s);
+      rf_launch<RF_MU2>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
       rf_launch<RF_LOWDIN>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
       launches += 3;
     }
@@ -616,7 +552,7 @@ size_t eig_refine_work_bytes(int m) {
          + (size_t)3 * kmax * sizeof(double) + 256;                     // mu, mu2, alpha
 }
 
-int eig_refine_launches(int iters) { return 5 * iters + 2 * (RF_ORTHO - 1) + (iters == 1 ? 4 : 3) + 1; }
+int eig_refine_launches(int iters) { return 5 * iters + 2 * (RF_ORTHO - 1) + 3 + 1; }
 
 cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* evecs, EigOut* eo, int kmax,
                               int iters, void* work, cudaStream_t s) {

@@ -476,11 +476,55 @@ __device__ __forceinline__ void eigh_tri_body(const double2* __restrict__ G, int
   // orthonormal basis of their common invariant subspace.
   {
     __shared__ T s_inv;
+    __shared__ T s_dot[TRI_MAXM];
+    const int nw = blockDim.x >> 5;
+    // z_i -= sum_{j < i} (z_j . z_i) z_j (classical Gram-Schmidt against every earlier,
+    // finished vector; dots first, then one pass over the rows)
+    auto reorth = [&](T* zi, int i) {
+      for (int j = warp; j < i; j += nw) {
+        const T* zj = gZ + (size_t)j * m;
+        T dot = 0;
+        for (int t = lane; t < m; t += 32) dot += zj[t] * zi[t];
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        if (lane == 0) s_dot[j] = dot;
+      }
+      __syncthreads();
+      for (int t = tid; t < m; t += blockDim.x) {
+        T acc = zi[t];
+        for (int j = 0; j < i; ++j) acc -= s_dot[j] * gZ[(size_t)j * m + t];
+        zi[t] = acc;
+      }
+      __syncthreads();
+    };
     for (int i = 0; i < nvec; ++i) {
       T* zi = gZ + (size_t)i * m;
       T part = 0;
       for (int t = tid; t < m; t += blockDim.x) part += zi[t] * zi[t];
-      const T nrm = block_reduce(part, red);
+      T nrm = block_reduce(part, red);
+      // A vector that lost most of its (unit) norm to the earlier ones (inverse iteration
+      // on eigenvalues the FP32 arithmetic does not separate, e.g. a cluster in the noise
+      // floor, returns nearly parallel vectors): one modified Gram-Schmidt pass leaves
+      // its remainder far from orthogonal, so it is orthogonalised twice more against
+      // every earlier vector; if nothing is left, a pseudo-random vector takes its place
+      // (any direction is an eigenvector to the FP32 solve's resolution there).
+      if (nrm < (T)0.25) {
+        for (int pass = 0; pass < 3; ++pass) {
+          if (pass == 2 || !(nrm > (T)1e-12)) {
+            if (pass == 2 && nrm > (T)1e-12) break;
+            for (int t = tid; t < m; t += blockDim.x) {
+              unsigned h = (unsigned)(t + 1) * 2654435761u ^ ((unsigned)(i + 7919) * 40503u + 0x85ebca6bu);
+              h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12; h *= 0x297a2d39u; h ^= h >> 15;
+              zi[t] = (T)(h & 0xffffu) * (T)(1.0 / 65536.0) - (T)0.5;
+            }
+            __syncthreads();
+            reorth(zi, i);
+          }
+          reorth(zi, i);
+          part = 0;
+          for (int t = tid; t < m; t += blockDim.x) part += zi[t] * zi[t];
+          nrm = block_reduce(part, red);
+        }
+      }
       if (tid == 0) s_inv = nrm > (T)0 ? (T)1 / sqrt(nrm) : (T)0;
       __syncthreads();
       const T inv = s_inv;

@@ -507,7 +507,9 @@ __global__ void __launch_bounds__(256) k_pair_gram_batch(const TruncTask* __rest
                (c2 + TILE - 1) / TILE, 1, tk.partials, tk.q, tk.c, l % tiles, l / tiles);
 }
 
-// G'[al c + i][be c + j] = sum_{b,b'} (M_al^dag M_be)_{bb'} S[b c + i][b' c + j], S summed over splits
+// G'[al c + i][be c + j] = sum_{b,b'} (M_al^dag M_be)_{bb'} S[b c + i][b' c + j], S summed over
+// splits (FP64 partials of the SIMT Gram, upper triangle by TILE blocks; or FP32 partials of the
+// tensor-core Gram, upper triangle by 64-row blocks)
 __global__ void __launch_bounds__(256) k_reduce_assemble_batch(const TruncTask* __restrict__ tasks) {
   const TruncTask& tk = tasks[blockIdx.y];
   const int c = tk.c, K = tk.K, m = K * c, c2 = 2 * c;
@@ -522,12 +524,21 @@ __global__ void __launch_bounds__(256) k_reduce_assemble_batch(const TruncTask* 
 #pragma unroll
     for (int bp = 0; bp < 2; ++bp) {
       const int si = b * c + i, sj = bp * c + j;
-      const bool upper = (si / TILE) <= (sj / TILE);  // tiles computed by the Gram
+      const int blk = tk.tc ? 64 : TILE;
+      const bool upper = (si / blk) <= (sj / blk);  // blocks computed by the Gram
       const int64_t idx = upper ? (int64_t)si * c2 + sj : (int64_t)sj * c2 + si;
       double sr = 0.0, sim = 0.0;
-      for (int sp = 0; sp < tk.splits; ++sp) {
-        const double2 v = tk.partials[sp * stride + idx];
-        sr += v.x; sim += v.y;
+      if (tk.tc) {
+        const float2* pf = reinterpret_cast<const float2*>(tk.partials);
+        for (int sp = 0; sp < tk.splits; ++sp) {
+          const float2 v = pf[sp * stride + idx];
+          sr += (double)v.x; sim += (double)v.y;
+        }
+      } else {
+        for (int sp = 0; sp < tk.splits; ++sp) {
+          const double2 v = tk.partials[sp * stride + idx];
+          sr += v.x; sim += v.y;
+        }
       }
       if (!upper) sim = -sim;
       double2 q = make_double2(0, 0);
@@ -580,15 +591,19 @@ cudaError_t launch_trunc_batch_gemms(const TruncTask* tasks, const int* gram_bst
                                      int max_d, int phase, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
   if (phase == 0) {
-    k_pair_gram_batch<T><<<gram_blocks, 256, 0, s>>>(tasks, gram_bstart, ntasks);
-    note_launches(1);
+    if (gram_blocks > 0) {
+      k_pair_gram_batch<T><<<gram_blocks, 256, 0, s>>>(tasks, gram_bstart, ntasks);
+      note_launches(1);
+    }
     k_reduce_assemble_batch<<<dim3((max_m2 + 255) / 256, ntasks), 256, 0, s>>>(tasks);
     note_launches(1);
   } else {
     k_build_proj_batch<<<dim3((max_d + 255) / 256, ntasks), 256, 0, s>>>(tasks);
     note_launches(1);
-    k_pair_rowmat_batch<T><<<proj_blocks, 256, 0, s>>>(tasks, proj_bstart, ntasks);
-    note_launches(1);
+    if (proj_blocks > 0) {
+      k_pair_rowmat_batch<T><<<proj_blocks, 256, 0, s>>>(tasks, proj_bstart, ntasks);
+      note_launches(1);
+    }
     k_accum_batch<<<(ntasks + 127) / 128, 128, 0, s>>>(tasks, ntasks);
     note_launches(1);
   }

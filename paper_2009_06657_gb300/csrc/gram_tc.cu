@@ -69,9 +69,11 @@ __device__ __forceinline__ void gram_load(const float2* __restrict__ V, int ld, 
   }
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_gram_pair_tc(const float2* __restrict__ V, int ld, int c, int pairbit, int64_t N2, int64_t rows_per_split,
-                   double2* __restrict__ partials, int* __restrict__ status) {
+// One split of the rows: row pairs split * rows_per_split .. + rows_per_split - 1,
+// its FP32 partial of S into P (2c x 2c).
+__device__ __forceinline__ void gram_tc_body(const float2* __restrict__ V, int ld, int c, int pairbit, int64_t N2,
+                                             int64_t rows_per_split, int split, float2* __restrict__ P,
+                                             int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned operand area
   float* stage = (float*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int NR = 4 * c;               // real columns
   const int nacc = NR > 128 ? 2 : 1;  // 128-row accumulator blocks
   const int rows_pad = NR < 128 ? 128 : NR;
-  const int64_t x_begin = (int64_t)blockIdx.x * rows_per_split;
+  const int64_t x_begin = (int64_t)split * rows_per_split;
   int64_t x_end = x_begin + rows_per_split;
   if (x_end > N2) x_end = N2;
   const int nchunks = x_begin < x_end ? (int)((x_end - x_begin + TC_KC - 1) / TC_KC) : 0;
@@ -204,7 +206,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // FP32 (FP64 arithmetic runs at 1/62 of the FP32 rate here); the split
   // partials are summed in FP64
   const int C2 = 2 * c;  // complex columns of S
-  float2* P = reinterpret_cast<float2*>(partials) + (int64_t)blockIdx.x * C2 * C2;
   for (int a = 0; a < nacc && warp < 4; ++a) {
     const int r = a * 128 + warp * 32 + lane;
     const int col0 = a == 0 ? 0 : 128;
@@ -238,7 +239,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gram_pair_tc(const float2* __restrict__ V, int ld, int c, int pairbit, int64_t N2, int64_t rows_per_split,
+                   double2* __restrict__ partials, int* __restrict__ status) {
+  gram_tc_body(V, ld, c, pairbit, N2, rows_per_split, blockIdx.x,
+               reinterpret_cast<float2*>(partials) + (int64_t)blockIdx.x * (2 * c) * (2 * c), status);
+}
+
+// task of block b: the last task whose first block is <= b (tasks with no blocks are
+// skipped because the next task starts at the same block)
+__device__ __forceinline__ int tc_task_of_block(const int* __restrict__ bstart, int ntasks, int b) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bstart[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gram_pair_tc_batch(const TruncTask* __restrict__ tasks, const int* __restrict__ bstart, int ntasks) {
+  const int t = tc_task_of_block(bstart, ntasks, blockIdx.x);
+  const TruncTask& tk = tasks[t];
+  const int split = blockIdx.x - bstart[t];
+  const int c = tk.c;
+  gram_tc_body((const float2*)tk.V, tk.ld, c, tk.q, tk.N2, tk.tc_rows, split,
+               reinterpret_cast<float2*>(tk.partials) + (int64_t)split * (2 * c) * (2 * c), tk.status);
+}
+
 }  // namespace
+
+cudaError_t prepare_gram_tc_batch() {
+  return cudaFuncSetAttribute(k_gram_pair_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+}
+
+cudaError_t launch_gram_pair_tc_batch(const TruncTask* tasks, const int* bstart, int nblocks, int ntasks,
+                                      cudaStream_t s) {
+  if (nblocks <= 0) return cudaSuccess;
+  k_gram_pair_tc_batch<<<nblocks, TC_THREADS, TC_SMEM, s>>>(tasks, bstart, ntasks);
+  note_launches(1);
+  return cudaGetLastError();
+}
 
 bool gram_pair_tc_supported(int c, int64_t N2) { return c % 8 == 0 && c >= 8 && 4 * c <= TC_MAXR && N2 >= 4096; }
 

@@ -127,6 +127,12 @@ struct TruncTask {
   void* eigwork;
   double2* D;         // 2c x 2k
   double* acc;        // per-circuit accounting [discarded, gap, status, truncations]
+  // tensor-core Gram (complex64 state, shapes the tcgen05 kernel takes): FP32 partials
+  // (splits of tc_rows row pairs, the upper triangle by 64-row blocks of the 2c x 2c
+  // result) into `partials`
+  int tc;
+  int64_t tc_rows;
+  int* status;        // set when a bounded wait of a tcgen05 kernel gave up
 };
 // phase 0: pair Gram + reduce/assemble G'; phase 1: projection matrix, pair projection, accounting
 template <typename T>
@@ -134,6 +140,12 @@ cudaError_t launch_trunc_batch_gemms(const TruncTask* tasks, const int* gram_bst
                                      const int* proj_bstart, int proj_blocks, int ntasks, int max_m2,
                                      int max_d, int phase, cudaStream_t s);
 int trunc_tiles(int c);
+// Batched tcgen05 Gram of the tasks with tc != 0: blocks map to tasks through a prefix
+// table (one block per split). prepare_gram_tc_batch() sets the kernel's shared-memory
+// limit (not a stream operation: call it before any graph capture).
+cudaError_t prepare_gram_tc_batch();
+cudaError_t launch_gram_pair_tc_batch(const TruncTask* tasks, const int* bstart, int nblocks, int ntasks,
+                                      cudaStream_t s);
 int64_t trunc_chunk(int64_t N2, int splits);
 int trunc_proj_blocks(int64_t N2, int k);
 // T = the solver's arithmetic (float or double, independent of the state's type);
@@ -159,9 +171,12 @@ int expand_blocks(int64_t total);
 // tensor-core (tcgen05, 3xTF32) pair projection for the FP32 state: W (pairs) = V (pairs) x D,
 // D: 2c x 2k complex128 (device); Bscratch: proj_pair_tc_scratch_bytes(c, k) bytes
 bool proj_pair_tc_supported(int c, int k, int64_t N2);
+int proj_pair_tc_blocks(int64_t N2);  // blocks of one projection launch
 size_t proj_pair_tc_scratch_bytes(int c, int k);
+// ssq (nullable, device): ssq[b] receives the squared Frobenius norm of what block b of
+// the projection wrote (ceil(N2 / 256) blocks).
 cudaError_t launch_proj_pair_tc(const void* V, int ld, int c, int k, int pairbit, int64_t N2, const double2* D,
-                                float* Bscratch, void* W, int* status, cudaStream_t s);
+                                float* Bscratch, void* W, int* status, double* ssq, cudaStream_t s);
 
 // ---- Y[x][j] = sum_i A1[x][i] M1[i][j] + sum_i A2[x][i] M2[i][j]  (j < p)
 // M1, M2: complex128 device matrices with leading dimensions ldm1, ldm2. A2 may be null.

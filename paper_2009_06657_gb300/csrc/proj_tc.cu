@@ -59,9 +59,9 @@ __device__ __forceinline__ int core_off(int row, int kl) {  // floats, K-major c
 __device__ __forceinline__ void bar_rows() { asm volatile("barrier.sync 1, %0;" ::"n"(PT_AW) : "memory"); }
 
 // D (2c x 2k complex, row-major) -> per chunk kc: [hi | lo] of D_r^T (N = 4k rows x 16)
-__global__ void k_proj_prep(const double2* __restrict__ D, int c, int k, float* __restrict__ B) {
+__device__ __forceinline__ void proj_prep_body(const double2* __restrict__ D, int c, int k, float* __restrict__ B,
+                                               int e) {
   const int N = 4 * k, K = 4 * c;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * K) return;
   const int n = e / K, kk = e % K;  // B[n][kk] = D_r[kk][n]
   const int I = kk >> 1, J = n >> 1;
@@ -76,6 +76,11 @@ __global__ void k_proj_prep(const double2* __restrict__ D, int c, int k, float* 
   chunk[core_off(n, kl)] = h;
   chunk[N * PT_KC + core_off(n, kl)] = f - h;
 }
+
+__global__ void k_proj_prep(const double2* __restrict__ D, int c, int k, float* __restrict__ B) {
+  proj_prep_body(D, c, k, B, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 
 // the four float4 of pair-row data this thread stages for chunk ch
 __device__ __forceinline__ void load_rows(const float2* __restrict__ V, int ld, int c, int pairbit, int64_t N2,
@@ -97,19 +102,23 @@ __device__ __forceinline__ void load_rows(const float2* __restrict__ V, int ld, 
   }
 }
 
-__global__ void __launch_bounds__(PT_THREADS, 1)
-    k_proj_pair_tc(const float2* __restrict__ V, int ld, int c, int k, int pairbit, int64_t N2,
-                   const float* __restrict__ B, float2* __restrict__ W, int* __restrict__ status) {
+// Pair rows tile * 256 .. + 255.
+// ssq (nullable): ssq[tile] receives the squared norm of everything this block wrote
+// (FP32 per thread, FP64 across the threads in a fixed order).
+__device__ __forceinline__ void proj_tc_body(const float2* __restrict__ V, int ld, int c, int k, int pairbit,
+                                             int64_t N2, const float* __restrict__ B, float2* __restrict__ W,
+                                             int* __restrict__ status, int tile, double* __restrict__ ssq) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* stage = (float*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t mbar_mma[PT_NS], mbar_b[PT_NS], mfull[PT_NS];
   __shared__ __align__(8) uint64_t mdrain;  // every MMA issued by this CTA has completed
   __shared__ int s_fail;
+  __shared__ double s_sq[PT_AW / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = 4 * c, N = 4 * k;
   const int nchunks = K / PT_KC;
-  const int64_t m0 = (int64_t)blockIdx.x * PT_ROWS;
+  const int64_t m0 = (int64_t)tile * PT_ROWS;
   const uint32_t b_bytes = (uint32_t)(2 * N * PT_KC * 4);
 
   if (warp == 0) {
@@ -236,6 +245,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       const int t = warp >> 2, wq = warp & 3;
       float* ep = stage + warp * (32 * PT_EP_LD);  // the ring is idle now
       const int64_t rbase = m0 + t * PT_TILE + wq * 32;
+      float sq = 0.f;
       for (int cb = 0; cb < N; cb += 32) {
         float v[32];
         tmem_ld32(tmem + (uint32_t)t * 256u + ((uint32_t)(wq * 32) << 16) + (uint32_t)cb, v);
@@ -254,11 +264,28 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             const int64_t x = rbase + rl;
             if (x < N2) {
               const uint64_t xp = insert_zero((uint64_t)x, pairbit) | ((uint64_t)b << pairbit);
-              *(float4*)(W + xp * (uint64_t)ld + col) = *(const float4*)(ep + rl * PT_EP_LD + 4 * piece);
+              const float4 o = *(const float4*)(ep + rl * PT_EP_LD + 4 * piece);
+              *(float4*)(W + xp * (uint64_t)ld + col) = o;
+              sq += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
             }
           }
         }
         __syncwarp();
+      }
+      if (ssq) {
+        double d = (double)sq;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) s_sq[warp] = d;
+      }
+    }
+    if (ssq) {
+      bar_rows();
+      if (tid == 0) {
+        double t = 0.0;
+        if (!s_fail)
+          for (int w = 0; w < PT_AW / 32; ++w) t += s_sq[w];
+        ssq[tile] = t;
       }
     }
   }
@@ -268,16 +295,27 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
+__global__ void __launch_bounds__(PT_THREADS, 1)
+    k_proj_pair_tc(const float2* __restrict__ V, int ld, int c, int k, int pairbit, int64_t N2,
+                   const float* __restrict__ B, float2* __restrict__ W, int* __restrict__ status,
+                   double* __restrict__ ssq) {
+  proj_tc_body(V, ld, c, k, pairbit, N2, B, W, status, blockIdx.x, ssq);
+}
+
+
 }  // namespace
 
 bool proj_pair_tc_supported(int c, int k, int64_t N2) {
   return c % 8 == 0 && 4 * c <= 256 && k % 4 == 0 && k >= 4 && 4 * k <= PT_MAXN && N2 >= 4096;
 }
 
+
+int proj_pair_tc_blocks(int64_t N2) { return (int)((N2 + PT_ROWS - 1) / PT_ROWS); }
+
 size_t proj_pair_tc_scratch_bytes(int c, int k) { return (size_t)2 * (4 * c) * (4 * k) * sizeof(float); }
 
 cudaError_t launch_proj_pair_tc(const void* V, int ld, int c, int k, int pairbit, int64_t N2, const double2* D,
-                                float* Bscratch, void* W, int* status, cudaStream_t s) {
+                                float* Bscratch, void* W, int* status, double* ssq, cudaStream_t s) {
   static std::atomic<uint64_t> attr_done{0};
   {
     cudaError_t e = set_dyn_smem_once(k_proj_pair_tc, PT_SMEM, attr_done);
@@ -288,7 +326,7 @@ cudaError_t launch_proj_pair_tc(const void* V, int ld, int c, int k, int pairbit
   note_launches(1);
   const int blocks = (int)((N2 + PT_ROWS - 1) / PT_ROWS);
   k_proj_pair_tc<<<blocks, PT_THREADS, PT_SMEM, s>>>((const float2*)V, ld, c, k, pairbit, N2, Bscratch,
-                                                      (float2*)W, status);
+                                                      (float2*)W, status, ssq);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -79,6 +79,15 @@ struct lr_ctx {
   double2* S = nullptr;   // pair Gram (2c x 2c)
   int* tc_status = nullptr;  // set by tensor-core kernels when a bounded wait gives up
   float* projB = nullptr;    // pre-split projection operand for the tensor-core projection
+  // Trace anchoring of the tensor-core projection: its FP32 accumulation in tensor memory
+  // shrinks the state by about 2e-7 per launch (measured), which would accumulate over a
+  // deep circuit. The projection adds the squared norm of its output to proj_ssq; the
+  // state is then s V with s = sqrt((1 - discarded mass so far) / |V|^2) (Tr rho = 1 -
+  // discarded mass is exact for LRET with complete Kraus sets), and s is folded into the
+  // next truncation's pair Gram (s^2) and projection (s), or applied to V before any other
+  // use (scale_pending; expansions commute with it).
+  double* proj_ssq = nullptr;  // [0] squared norm, [1] the scale s, [2 ..] per-block partials
+  bool scale_pending = false;
   int use_tc = 1;
   double2* D = nullptr;   // pair projection (2c x 2k)
   // deferred pair projection: the state is [V_0 V_1] C on qubit pend_q, V holding
@@ -291,13 +300,55 @@ int snapshot(lr_ctx* h, Stage& st) {
   return LR_OK;
 }
 
+// A[i] *= s^power (complex128 small matrices)
+__global__ void k_scale_c2(double2* __restrict__ A, int n, const double* __restrict__ s, int power) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double f = power == 2 ? s[0] * s[0] : s[0];
+  A[i] = make_double2(A[i].x * f, A[i].y * f);
+}
+
+// |V|^2 = the projection blocks' partial squared norms ssq[2 ..], summed in a fixed order;
+// s = sqrt((1 - discarded mass so far) / |V|^2) into ssq[1] (acc[0]: the discarded mass)
+__global__ void __launch_bounds__(256) k_trace_scale(double* ssq, int nparts, const double* acc) {
+  __shared__ double red[256];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 256) v += ssq[2 + i];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {  // fixed-order tree
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  v = red[0];
+  if (threadIdx.x == 0) {
+    const double t = 1.0 - acc[0];
+    ssq[0] = v;
+    ssq[1] = (v > 0.0 && t > 0.0) ? sqrt(t / v) : 1.0;
+  }
+}
+
+// V[x][j] *= s for the c columns of a complex64 state
+__global__ void k_scale_cols(float2* __restrict__ V, int64_t N, int c, int ld, const double* __restrict__ s) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= N * c) return;
+  const int64_t x = e / c;
+  const int j = (int)(e - x * c);
+  const float f = (float)s[0];
+  float2& v = V[x * ld + j];
+  v = make_float2(v.x * f, v.y * f);
+}
+
 // V <- [V_0 V_1] D on qubit q (D: 2c x 2k, row stride 2k), into W, then swap.
 int run_pair_proj(lr_ctx* h, const double2* D, int c, int k, int q) {
   const int64_t N2 = h->N / 2;
   const int ld = h->cap;
   const int te = tbeg(h);
   if (h->dtype == LR_C64 && h->use_tc && proj_pair_tc_supported(c, k, N2)) {
-    CK(launch_proj_pair_tc(h->V, ld, c, k, q, N2, D, h->projB, h->W, h->tc_status, h->stream));
+    CK(launch_proj_pair_tc(h->V, ld, c, k, q, N2, D, h->projB, h->W, h->tc_status, h->proj_ssq + 2, h->stream));
+    k_trace_scale<<<1, 256, 0, h->stream>>>(h->proj_ssq, proj_pair_tc_blocks(N2), h->acc);
+    note_launches(1);
+    h->scale_pending = true;
   } else {
     CK(by_dtype(h->dtype, [&](auto t) {
       return launch_rowmat<decltype(t)>(h->V, ld, 2 * c, D, 2 * k, nullptr, 0, 0, nullptr, 0, h->W, ld, 2 * k,
@@ -309,17 +360,30 @@ int run_pair_proj(lr_ctx* h, const double2* D, int c, int k, int q) {
   return LR_OK;
 }
 
-// Apply a deferred pair projection, if any, so that V holds the state.
-int materialize(lr_ctx* h) {
+// Apply a deferred pair projection, if any, so that V (up to a pending scale) holds the state.
+int materialize_proj(lr_ctx* h) {
   if (!h->pend) return LR_OK;
   h->pend = false;
   return run_pair_proj(h, h->pend_C, h->pend_cm, h->c, h->pend_q);
 }
 
+// Apply a pending trace-anchoring scale to V.
+int apply_scale(lr_ctx* h) {
+  if (!h->scale_pending) return LR_OK;
+  h->scale_pending = false;
+  const int64_t n = h->N * (int64_t)h->c;  // only the complex64 tensor-core path sets a scale
+  k_scale_cols<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>((float2*)h->V, h->N, h->c, h->cap,
+                                                                    h->proj_ssq + 1);
+  note_launches(1);
+  CK(cudaGetLastError());
+  return LR_OK;
+}
+
+
 // Run one expansion stage V -> W, swap. Queue flags are cleared by the caller.
 int run_expand(lr_ctx* h, bool use_gate, bool use_chan) {
   {
-    int rc = materialize(h);
+    int rc = materialize_proj(h);  // a pending scale commutes with the expansion and stays pending
     if (rc) return rc;
   }
   GroupOp op;
@@ -363,7 +427,7 @@ int flush_gate(lr_ctx* h) {
 
 int flush_all(lr_ctx* h) {
   {
-    int rc = materialize(h);
+    int rc = materialize_proj(h);  // a pending scale commutes with gates and expansions
     if (rc) return rc;
   }
   if (h->has_chan) {
@@ -374,6 +438,13 @@ int flush_all(lr_ctx* h) {
     return LR_OK;
   }
   return flush_gate(h);
+}
+
+// Everything queued applied and any pending scale too: V holds the state (readouts).
+int flush_state(lr_ctx* h) {
+  int rc = flush_all(h);
+  if (!rc) rc = apply_scale(h);
+  return rc;
 }
 
 // Per-truncation accounting; with a log buffer (cap > 0) also one record per truncation:
@@ -551,9 +622,12 @@ int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
   // new projection composes, C <- C D. Otherwise the deferred one is applied first.
   const bool fuse = h->pend && h->pend_q == q;
   if (h->pend && !fuse) {
-    int rc = materialize(h);
+    int rc = materialize_proj(h);  // a scale it leaves pending is folded in below
     if (rc) return rc;
   }
+  // (a deferred projection never coexists with a pending scale: the scale is folded
+  // into the projection matrix when the deferral starts)
+  const bool fold_scale = h->scale_pending && !fuse;
   if (!h->pend_C) {
     const size_t big = sizeof(double2) * 512 * 512;
     int rc = dmalloc(h, (void**)&h->pend_C, big);
@@ -584,6 +658,10 @@ int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
     }
     tend(h, LR_K_GRAM, te);
     te = tbeg(h);
+    if (fold_scale) {  // the state is s V: its pair Gram is s^2 S
+      k_scale_c2<<<(4 * c * c + 255) / 256, 256, 0, h->stream>>>(h->S, 4 * c * c, h->proj_ssq + 1, 2);
+      note_launches(1);
+    }
     CK(launch_assemble_gram(h->S, c, K, pq, h->G, h->stream));
     tend(h, LR_K_SMALL, te);
   }
@@ -597,6 +675,11 @@ int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
     std::swap(h->pend_C, h->pend_C2);
   } else {
     CK(cudaMemcpyAsync(h->pend_C, h->D, sizeof(double2) * 4 * c * k, cudaMemcpyDeviceToDevice, h->stream));
+    if (fold_scale) {  // and its projection s [V_0 V_1] D
+      k_scale_c2<<<(4 * c * k + 255) / 256, 256, 0, h->stream>>>(h->pend_C, 4 * c * k, h->proj_ssq + 1, 1);
+      note_launches(1);
+      h->scale_pending = false;
+    }
     h->pend_cm = c;
     h->pend_q = q;
   }
@@ -615,6 +698,10 @@ int do_structured(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
 }
 
 int do_truncate(lr_ctx* h, int r_eff, double eps, double* discarded_out) {
+  {
+    int rc = apply_scale(h);  // (normally applied by flush_all already)
+    if (rc) return rc;
+  }
   const int m = h->c;
   const int64_t N = h->N;
   const int ld = h->cap;
@@ -727,6 +814,7 @@ int set_initial_state(lr_ctx* h) {
     CK(cudaMemcpyAsync(h->V, one, sizeof(one), cudaMemcpyHostToDevice, h->stream));
   }
   CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 8, h->stream));
+  h->scale_pending = false;
   if (h->tlog_n) CK(cudaMemsetAsync(h->tlog_n, 0, sizeof(int64_t), h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->c = 1;
@@ -849,6 +937,7 @@ int lr_init_ex(int n, int r, int dtype, int capacity, void* stream, lr_handle* o
   if (!rc) rc = dmalloc(h, (void**)&h->G, sizeof(double2) * m * m);
   if (!rc) rc = dmalloc(h, (void**)&h->S, sizeof(double2) * m * m);
   if (!rc) rc = dmalloc(h, (void**)&h->tc_status, sizeof(int));
+  if (!rc) rc = dmalloc(h, (void**)&h->proj_ssq, sizeof(double) * (2 + proj_pair_tc_blocks(h->N / 2)));
   if (!rc) rc = dmalloc(h, (void**)&h->projB, proj_pair_tc_scratch_bytes(64, 64));
   if (!rc && cudaMemset(h->tc_status, 0, sizeof(int)) != cudaSuccess) rc = LR_ECUDA;
   if (!rc) rc = dmalloc(h, (void**)&h->D, sizeof(double2) * m * m);
@@ -888,6 +977,7 @@ int lr_free(lr_handle h) {
   dfree((void*&)h->G);
   dfree((void*&)h->S);
   dfree((void*&)h->tc_status);
+  dfree((void*&)h->proj_ssq);
   dfree((void*&)h->projB);
   dfree((void*&)h->D);
   dfree((void*&)h->pend_C);
@@ -1201,7 +1291,7 @@ int lr_set_path(lr_handle h, int which) {
 
 int lr_probs(lr_handle h, void* out_dev) {
   if (!h || !out_dev) return LR_EINVAL;
-  int rc = flush_all(h);
+  int rc = flush_state(h);
   if (rc) return rc;
   const int te = tbeg(h);
   CK(by_dtype(h->dtype, [&](auto t) {
@@ -1216,7 +1306,7 @@ int lr_sample(lr_handle h, int shots, const double* uniforms, int64_t* out_host)
   for (int s = 0; s < shots; ++s)
     if (!(uniforms[s] >= 0.0 && uniforms[s] < 1.0)) return LR_EINVAL;
   if (shots == 0) return LR_OK;
-  int rc = flush_all(h);
+  int rc = flush_state(h);
   if (rc) return rc;
   const int64_t nb = (h->N + SC_ROWS - 1) / SC_ROWS;
   const size_t need = (size_t)h->N + 2 * (size_t)nb + 1 + (size_t)shots;
@@ -1251,7 +1341,7 @@ int lr_sample(lr_handle h, int shots, const double* uniforms, int64_t* out_host)
 
 int lr_entropy(lr_handle h, double* out_host) {
   if (!h || !out_host) return LR_EINVAL;
-  int rc = flush_all(h);
+  int rc = flush_state(h);
   if (rc) return rc;
   const int c = h->c;
   if (c > 256) {
@@ -1286,7 +1376,7 @@ int lr_entropy(lr_handle h, double* out_host) {
 
 int lr_z_expect(lr_handle h, double* out_host) {
   if (!h || !out_host) return LR_EINVAL;
-  int rc = flush_all(h);
+  int rc = flush_state(h);
   if (rc) return rc;
   double* outd = h->dscratch;              // n + 1 values
   double* part = h->dscratch + 64;         // <= 1024 * 32 partials
@@ -1302,7 +1392,7 @@ int lr_z_expect(lr_handle h, double* out_host) {
 int lr_expect(lr_handle h, int T, const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
               double* out_host) {
   if (!h || T < 0 || !out_host || (T > 0 && (!xmask || !zmask || !coeff))) return LR_EINVAL;
-  int rc = flush_all(h);
+  int rc = flush_state(h);
   if (rc) return rc;
   if (T == 0) { *out_host = 0.0; return LR_OK; }
   rc = upload_terms(h, T, xmask, zmask, coeff);
@@ -1349,7 +1439,7 @@ int lr_backward(lr_handle h, int T, const uint64_t* xmask, const uint64_t* zmask
   if (!h || T <= 0 || !xmask || !zmask || !coeff || nparams < 0 || (nparams > 0 && !grad_out_host))
     return LR_EINVAL;
   if (!h->record) return LR_ESTATE;
-  int rc = flush_all(h);
+  int rc = flush_state(h);
   if (rc) return rc;
   for (auto& st : h->tape)
     if (st.type == 0 && st.param_id >= nparams) return LR_EINVAL;
@@ -1490,7 +1580,7 @@ int lr_get_info(lr_handle h, lr_info* info) {
 
 int lr_get_state(lr_handle h, void* out_host) {
   if (!h || !out_host) return LR_EINVAL;
-  int rc = flush_all(h);
+  int rc = flush_state(h);
   if (rc) return rc;
   CK(cudaMemcpy2DAsync(out_host, h->c * h->esz, h->V, h->cap * h->esz, h->c * h->esz, (size_t)h->N,
                        cudaMemcpyDeviceToHost, h->stream));

@@ -361,7 +361,7 @@ class LRBatch:
     """
 
     def __init__(self, circuits, dtype="c64", rows_per_split=0, use_graph=True, stream=None,
-                 eig_precision="refined", eig_iters=1, splits=None):
+                 eig_precision="refined", eig_iters=1, splits=None, tensor_cores=True):
         """eig_precision (complex64): "refined" (FP32 solve + FP64 refinement of the kept
         eigenvectors), "fp32" or "fp64". splits: None or one Gram split count per
         circuit (0 = from rows_per_split), e.g. from autotune.BatchTable.splits_for."""
@@ -398,6 +398,7 @@ class LRBatch:
             self._keep.append(sp)
             opts.splits = C.cast(sp, C.POINTER(C.c_int))
         opts.use_graph = 1 if use_graph else 0
+        opts.tensor_cores = 1 if tensor_cores else 0
         opts.stream = self.stream.cuda_stream
         h = C.c_void_p()
         check(lib.lr_batch_create_ex(arr, len(circuits), C.byref(opts), C.byref(h)), "lr_batch_create_ex")

@@ -150,3 +150,35 @@ def test_per_circuit_split_counts_do_not_change_results(lr, dtype):
         b.close()
     for (p0, d0), (p1, d1) in zip(*outs):
         assert np.sum(np.abs(p0 - p1)) < tol and abs(d0 - d1) < tol
+
+
+def test_tensor_core_tasks_of_a_batch_match_single_runs_and_oracle(lr):
+    """Circuits with 2^12 row pairs and more take the batched tcgen05 Gram and
+    projection (one launch each per step for all of them, blocks mapped to tasks through
+    prefix tables) beside SIMT tasks of small circuits in the same steps: each against
+    its one-at-a-time run (tensor cores on) and the smallest ranks against the oracle."""
+    specs = [(13, 8, 2), (13, 16, 2), (13, 32, 1), (14, 64, 1), (6, 8, 2), (13, 64, 1)]
+    circs = []
+    for i, (n, r, d) in enumerate(specs):
+        ops = random_layered(n, d, seed=5300 + i, noise=("mixed", 1e-3, 2e-3), qubit_jitter=(0.5, 1.5))
+        circs.append({"n": n, "r": r, "ops": ops})
+    b = lr.LRBatch(circs, dtype="c64")
+    b.run()
+    for i, cd in enumerate(circs):
+        sim = lr.LRSim(cd["n"], cd["r"], dtype="c64")
+        sim.set_eigensolver("tridiag")
+        lr.run_ops(sim, cd["ops"], r=cd["r"])
+        p1 = sim.probs().double().cpu().numpy()
+        pb = b.probs(i).double().cpu().numpy()
+        inf = b.info(i)
+        assert inf["converged"] and inf["compressions"] > 0, i
+        assert abs(float(pb.sum()) - (1.0 - inf["discarded"])) < 1e-5, i
+        assert np.sum(np.abs(p1 - pb)) < 1e-5, i
+        assert abs(inf["discarded"] - sim.info()["discarded"]) < 1e-5, i
+        sim.close()
+    for i in (0, 1):  # 13 qubits, r = 8 and 16: the oracle finishes in seconds
+        ref = O.run_lret(circs[i]["n"], circs[i]["ops"], r=circs[i]["r"])
+        pb = b.probs(i).double().cpu().numpy()
+        assert np.sum(np.abs(pb - ref.probs())) < 1e-5, i
+        assert abs(b.info(i)["discarded"] - ref.discarded) < 1e-5, i
+    b.close()

@@ -8,7 +8,8 @@ through lr_last_eig and compared with the oracle's eigh of the same FP64 matrix:
 
 * the eigenvalues of the kept subspace (of X^dag G X) and the discarded mass (the
   trace the truncation removes, trace(G) minus the kept eigenvalues) to 1e-13 of the trace, each reported kept eigenvalue to 1e-13 of lambda_1 up to the spread of
-  an eigenvalue cluster the FP32 solve cannot separate;
+  an eigenvalue cluster the FP32 solve cannot separate and the second-order effect of
+  its mixing of nearby kept pairs (kept vectors are not rotated among themselves);
 * the truncated state: rho_trunc = V' P V'^dag depends on the kept vectors only
   through the projector P, and ||V' (P - P0) V'^dag||_F = ||G^(1/2) (P - P0) G^(1/2)||_F,
   held to 1e-11 of the trace;
@@ -78,6 +79,9 @@ def _cuts(lr, n, r, nchan, mode, iters=1, seed=3000, solver="auto", depth=1, ski
 # (they are tied at the state's precision); the refinement reaches FP64 accuracy for
 # the pairs it separates.
 FP32_RES = 16 * 2.0 ** -24
+# Mixing angle of a kept pair in the FP32 solve, times the gap: the unit roundoff with a
+# small growth factor.
+FP32_MIX = 4 * 2.0 ** -24
 
 
 def _cluster_spread(lam, i, width):
@@ -85,6 +89,17 @@ def _cluster_spread(lam, i, width):
     d = np.abs(lam - lam[i])
     d = d[d <= width]
     return float(d.max()) if d.size else 0.0
+
+
+def _kept_mixing(lam, i, k, res):
+    """Second-order error of the Rayleigh quotient of kept vector i: the refinement does
+    not rotate kept vectors among themselves (rho does not depend on it), so the FP32
+    solve's mixing of kept pairs, of angle about res / |lam_i - lam_j|, stays and moves
+    the quotient by about res^2 / |lam_i - lam_j| (pairs inside the resolution window
+    FP32_RES are covered by the cluster spread)."""
+    d = np.abs(lam[:k] - lam[i])
+    d = d[d > FP32_RES * abs(lam[0])]
+    return float(np.sum(res * res / d)) if d.size else 0.0
 
 
 CASES = {
@@ -113,7 +128,8 @@ def test_refined_eigensolve_matches_fp64(lr, solver, case):
         kc = np.linalg.eigvalsh(0.5 * (H + H.conj().T))[::-1]
         e_sub = float(np.max(np.abs(kc - lam0[:k]))) / l1
         # each kept eigenvalue, up to the spread of a cluster the FP32 solve cannot resolve
-        e_lam = max(abs(ev[i] - lam0[i]) - _cluster_spread(lam0, i, FP32_RES * l1) for i in range(k)) / l1
+        e_lam = max(abs(ev[i] - lam0[i]) - _cluster_spread(lam0, i, FP32_RES * l1)
+                    - _kept_mixing(lam0, i, k, FP32_MIX * l1) for i in range(k)) / l1
         e_rho = _rho_err(G, U, U0, k) / tr
         e_orth = float(np.max(np.abs(X.conj().T @ X - np.eye(k))))
         e_drop = abs(dropped - float(lam0[k:].sum())) / tr  # the trace the truncation removes
