@@ -527,9 +527,9 @@ cudaError_t rf_run(const RefineTask& t, const RefineTask* tasks, int ntasks, int
     } else {
       // the last step's input is nearly orthonormal: its Rayleigh quotients (the kept
       // eigenvalues) change only at second order in the step's tiny change; G X of the
-      // input in FP64 (a second-order expansion around G X0 with an FP32 G Delta,
-      // measured, lost 5e-10 of lambda_1 where the correction step moved a vector by
-      // more than about 1e-3)
+      // input in FP64 (an expansion around G X0 with an FP32 G Delta would carry about
+      // 2^-24 |Delta|^2 lambda_1, above 1e-13 lambda_1 for a column the correction step
+      // moved by more than about 1e-3, as damped columns can be)
       rf_launch<RF_GEMM>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
       rf_launch<RF_MU2>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);
       rf_launch<RF_LOWDIN>(t, tasks, ntasks, m_max, kmax_max, st, 0, s);

@@ -542,3 +542,34 @@ def test_tensor_core_projection_keeps_the_trace_over_many_truncations(lr):
     assert np.sum(np.abs(p32 - p64)) < TOL["c64"]
     assert abs(i32["discarded"] - i64["discarded"]) < TOL["c64"]
     assert abs(h32 - h64) < TOL["c64"] * sum(abs(c) for c, _ in terms)
+
+
+def test_full_size_deep_mixed_path_matches_fp64_path(lr):
+    """The benchmark workload itself at depth: 20 qubits, r = 64, 8 layers of the
+    20-qubit family (480 truncations, 320 tensor-core projections) on the FP32-state path
+    against this library's FP64 path. The state's trace must equal 1 - discarded mass
+    (the tensor-core projection is anchored to it), and the readouts must agree within
+    the FP32 tolerance widened only by the tied cuts (the rule of the shallow full-size
+    test, applied to every cut of the FP64 path's log)."""
+    n, r, depth = 20, 64, 8
+    ops = random_layered(n, depth, seed=3000, noise=("dep", 5e-4))
+    terms = random_pauli_sum(n, 64, seed=3001)
+    out = {}
+    for dtype in ("c64", "c128"):
+        sim = lr.LRSim(n, r, dtype=dtype)
+        sim.set_trunc_log(1 << 14)
+        lr.run_ops(sim, ops, r=r)
+        out[dtype] = (sim.probs().double().cpu().numpy(), sim.expect(terms), sim.info(), sim.trunc_log())
+        sim.close()
+    (p32, h32, i32, log32), (p64, h64, i64, log64) = out["c64"], out["c128"]
+    assert i32["compressions"] == i64["compressions"] >= 400
+    tied = sum(2.0 * e["lambda_k"] for e in log64
+               if e["k"] < e["m"] and e["lambda_k"] - e["lambda_k1"] <= RES32 * e["lambda_1"])
+    bound = TOL["c64"] + tied
+    l1 = float(np.sum(np.abs(p32 - p64)))
+    print(f"depth {depth}: tied-cut allowance {tied:.3e}; L1 {l1:.3e}; trace error "
+          f"{abs(p32.sum() - (1.0 - i32['discarded'])):.3e}; discarded {i32['discarded']:.4f}")
+    assert abs(p32.sum() - (1.0 - i32["discarded"])) < 1e-6
+    assert abs(i32["discarded"] - i64["discarded"]) < TOL["c64"]
+    assert l1 < bound
+    assert abs(h32 - h64) < bound * sum(abs(c) for c, _ in terms)
