@@ -350,7 +350,11 @@ typedef struct lr_batch_opts {
   const int* splits;
   int use_graph;
   void* stream;
-  int tensor_cores;  /* LR_C64: tcgen05 Gram for truncations it suits (default 1) */
+  int tensor_cores;  /* LR_C64: tcgen05 Gram and projection for truncations they suit
+                        (default 1); a circuit so projected is rescaled to
+                        Tr rho = 1 - discarded mass after each projection, as in
+                        lr_set_tensor_cores (the scale is kept per circuit and taken
+                        into its next truncation and lr_batch_probs) */
 } lr_batch_opts;
 void lr_batch_opts_default(lr_batch_opts* o);
 int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opts* opts, lr_batch_handle* out);

@@ -41,6 +41,8 @@ struct Circ {
   void* rfwork = nullptr;  // FP64 refinement workspace (refined eigensolve)
   int64_t tc_rows = 0;     // rows per split of the tensor-core Gram (0: not eligible)
   int tc_splits = 0;
+  float* B = nullptr;      // tensor-core projection operand
+  double* tcs = nullptr;   // trace anchoring: [unused, s, per-block squared norms]
   int64_t gates = 0, truncs = 0;
 };
 
@@ -49,6 +51,7 @@ struct Step {
   int t_off = 0, t_cnt = 0, gram_blocks = 0, proj_blocks = 0, gb_off = 0, pb_off = 0, max_m2 = 0, max_d = 0;
   int max_m = 0, max_k = 0;  // largest Gram size and rank of the step's truncations
   int tg_off = 0, tg_blocks = 0;  // tensor-core Gram of the step's eligible truncations
+  int tp_off = 0, tp_blocks = 0, max_nk = 0;  // tensor-core projection
 };
 
 
@@ -211,6 +214,12 @@ int lower(const lr_circuit& cd, std::vector<HStage>& out, int64_t* gates) {
   return LR_OK;
 }
 
+// Prob(x) *= s^2 (complex64 batches: tensor-core circuits carry a trace scale s)
+__global__ void k_scale_probs(float* __restrict__ p, int64_t N, const double* __restrict__ s) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (x < N) p[x] = (float)((double)p[x] * s[0] * s[0]);
+}
+
 int init_states(lr_batch* b) {
   for (auto& C : b->circ) {
     BCK(cudaMemsetAsync(C.buf[0], 0, (size_t)C.N * C.cap * b->esz, b->stream));
@@ -222,6 +231,10 @@ int init_states(lr_batch* b) {
       BCK(cudaMemcpyAsync(C.buf[0], one, sizeof(one), cudaMemcpyHostToDevice, b->stream));
     }
     BCK(cudaMemsetAsync(C.acc, 0, sizeof(double) * 8, b->stream));
+    if (C.tcs) {
+      const double one[2] = {0.0, 1.0};
+      BCK(cudaMemcpyAsync(C.tcs, one, sizeof(one), cudaMemcpyHostToDevice, b->stream));
+    }
   }
   BCK(cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
   BCK(cudaStreamSynchronize(b->stream));
@@ -259,6 +272,8 @@ int enqueue(lr_batch* b) {
         return launch_trunc_batch_gemms<decltype(t)>(tt, b->d_bs + st.gb_off, st.gram_blocks, b->d_bs + st.pb_off,
                                                      st.proj_blocks, st.t_cnt, st.max_m2, st.max_d, 1, b->stream);
       }));
+      if (st.tp_blocks)
+        BCK(launch_proj_pair_tc_batch(tt, b->d_bs + st.tp_off, st.tp_blocks, st.t_cnt, st.max_nk, b->stream));
     }
   }
   return LR_OK;
@@ -275,7 +290,7 @@ int lr_batch_free(lr_batch_handle b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (auto& C : b->circ) {
     for (int i = 0; i < 2; ++i) if (C.buf[i]) cudaFree(C.buf[i]);
-    void* ps[] = {C.acc, C.partials, C.G, C.evecs, C.D, C.evals, C.eo, C.eigwork, C.rfwork};
+    void* ps[] = {C.acc, C.partials, C.G, C.evecs, C.D, C.evals, C.eo, C.eigwork, C.rfwork, C.B, C.tcs};
     for (void* p : ps) if (p) cudaFree(p);
   }
   if (b->d_et) cudaFree(b->d_et);
@@ -381,6 +396,9 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
     if (!rc) rc = bmalloc(b, &C.buf[1], slab);
     if (!rc) rc = bmalloc(b, (void**)&C.acc, sizeof(double) * 8);
     if (!rc) rc = bmalloc(b, (void**)&C.partials, part_bytes);
+    // (scratch of the largest supported shape, c = k = 64)
+    if (!rc && C.tc_rows) rc = bmalloc(b, (void**)&C.B, proj_pair_tc_scratch_bytes(64, 64));
+    if (!rc && C.tc_rows) rc = bmalloc(b, (void**)&C.tcs, sizeof(double) * (2 + proj_pair_tc_blocks(N2)));
 
     if (!rc) rc = bmalloc(b, (void**)&C.G, sizeof(double2) * (size_t)m * m);
     if (!rc) rc = bmalloc(b, (void**)&C.evecs, sizeof(double2) * (size_t)m * m);
@@ -404,7 +422,7 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
     Step& S = b->steps[s];
     S.e_off = (int)et.size();
     S.t_off = (int)tt.size();
-    std::vector<int> eblocks, gblocks, pblocks, tgblocks;
+    std::vector<int> eblocks, gblocks, pblocks, tgblocks, tpblocks;
     for (int i = 0; i < count; ++i) {
       if (s >= stages[i].size()) continue;
       const HStage& h = stages[i][s];
@@ -453,6 +471,9 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
         t.acc = C.acc;
         t.status = b->d_status;
         t.tc = C.tc_rows > 0 && gram_pair_tc_supported(t.c, t.N2);
+        t.tcp = C.tc_rows > 0 && proj_pair_tc_supported(t.c, t.k, t.N2);
+        t.tcs = C.tcs;
+        t.B = C.B;
         if (t.tc) {
           t.tc_rows = C.tc_rows;
           t.splits = C.tc_splits;
@@ -462,13 +483,13 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
         rt.push_back(RefineTask{C.G, t.m, t.k, C.evals, C.evecs, C.eo, C.rfwork});
         S.max_m = std::max(S.max_m, t.m);
         S.max_k = std::max(S.max_k, t.k);
-        // tensor-core Gram where it applies; the projection stays on the SIMT kernel
-        // (the tensor core's FP32 accumulation shrinks a projected state by about 2e-7
-        // per launch, which the single-circuit runtime anchors to the exact trace and the
-        // batch does not)
+        // tensor-core Gram and projection where they apply (the projection's output
+        // anchored to the exact trace through tcs, as in the single-circuit runtime)
         gblocks.push_back(t.tc ? 0 : t.tiles * t.splits);
-        pblocks.push_back(trunc_proj_blocks(t.N2, t.k));
+        pblocks.push_back(t.tcp ? 0 : trunc_proj_blocks(t.N2, t.k));
         tgblocks.push_back(t.tc ? t.splits : 0);
+        tpblocks.push_back(t.tcp ? proj_pair_tc_blocks(t.N2) : 0);
+        if (t.tcp) S.max_nk = std::max(S.max_nk, 16 * t.c * t.k);
         S.max_m2 = std::max(S.max_m2, t.m * t.m);
         S.max_d = std::max(S.max_d, 4 * t.c * t.k);
         ++C.truncs;
@@ -491,6 +512,7 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
       prefix(gblocks, &S.gb_off, &S.gram_blocks);
       prefix(pblocks, &S.pb_off, &S.proj_blocks);
       prefix(tgblocks, &S.tg_off, &S.tg_blocks);
+      prefix(tpblocks, &S.tp_off, &S.tp_blocks);
     }
     b->launches += (S.e_cnt ? 1 : 0) + (S.t_cnt ? 6 : 0);
     if (S.t_cnt && !solve_fp64(b) && b->eig_prec == LR_EIGP_REFINED) b->launches += eig_refine_launches(b->eig_iters);
@@ -512,6 +534,7 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
   if (e == cudaSuccess && !bs.empty()) e = cudaMemcpy(b->d_bs, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = solve_fp64(b) ? prepare_eigh_tri_batch<double>() : prepare_eigh_tri_batch<float>();
   if (e == cudaSuccess && b->any_tc) e = prepare_gram_tc_batch();
+  if (e == cudaSuccess && b->any_tc) e = prepare_proj_tc_batch();
   if (e != cudaSuccess) {
     lret::set_error("%s: %s", "batch setup", cudaGetErrorString(e));
     lr_batch_free(b);
@@ -593,6 +616,11 @@ int lr_batch_probs(lr_batch_handle b, int i, void* out_dev) {
   BCK(by_dt(b->dtype, [&](auto t) {
     return launch_probs<decltype(t)>(C.buf[C.cur], C.N, C.c, C.cap, out_dev, b->stream);
   }));
+  if (C.tcs) {  // the state is s V
+    k_scale_probs<<<(unsigned)((C.N + 255) / 256), 256, 0, b->stream>>>((float*)out_dev, C.N, C.tcs + 1);
+    lret::note_launches(1);
+    BCK(cudaGetLastError());
+  }
   BCK(cudaStreamSynchronize(b->stream));
   return LR_OK;
 }

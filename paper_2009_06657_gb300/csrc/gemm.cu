@@ -547,6 +547,10 @@ __global__ void __launch_bounds__(256) k_reduce_assemble_batch(const TruncTask* 
       cfma(acc, q, make_double2(sr, sim));
     }
   if (row == col) acc.y = 0.0;
+  if (tk.tcs) {  // the circuit's state is s V (trace anchoring of a tensor-core projection)
+    const double s2 = tk.tcs[1] * tk.tcs[1];
+    acc = make_double2(acc.x * s2, acc.y * s2);
+  }
   tk.G[e] = acc;
 }
 
@@ -561,6 +565,7 @@ __global__ void __launch_bounds__(256) k_build_proj_batch(const TruncTask* __res
   const int b = r / c, i = r % c, a = cl / k, j = cl % k;
   double2 acc = make_double2(0, 0);
   for (int al = 0; al < K; ++al) cfma(acc, tk.M[al][a][b], tk.evecs[(int64_t)(al * c + i) * m + j]);
+  if (tk.tcs) acc = make_double2(acc.x * tk.tcs[1], acc.y * tk.tcs[1]);  // and its projection s [V_0 V_1] D
   tk.D[e] = acc;
 }
 
@@ -583,6 +588,7 @@ __global__ void k_accum_batch(const TruncTask* __restrict__ tasks, int ntasks) {
   tk.acc[1] = tk.eo->gap;
   if ((double)tk.eo->status > tk.acc[2]) tk.acc[2] = (double)tk.eo->status;
   tk.acc[3] += 1.0;
+  if (tk.tcs) tk.tcs[1] = 1.0;  // the scale is folded into this projection (a tensor-core one sets a new one)
 }
 
 template <typename T>

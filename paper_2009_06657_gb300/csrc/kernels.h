@@ -133,6 +133,13 @@ struct TruncTask {
   int tc;
   int64_t tc_rows;
   int* status;        // set when a bounded wait of a tcgen05 kernel gave up
+  // tensor-core projection (tcp != 0) with the trace anchoring of the single-circuit
+  // runtime: B the pre-split operand; tcs (per circuit, or null) = [unused, s, per-block
+  // squared norms of the last tensor-core projection]: the circuit's state is s V, s
+  // folded into the next truncation's Gram (s^2) and projection matrix (s)
+  int tcp;
+  float* B;
+  double* tcs;
 };
 // phase 0: pair Gram + reduce/assemble G'; phase 1: projection matrix, pair projection, accounting
 template <typename T>
@@ -146,6 +153,12 @@ int trunc_tiles(int c);
 cudaError_t prepare_gram_tc_batch();
 cudaError_t launch_gram_pair_tc_batch(const TruncTask* tasks, const int* bstart, int nblocks, int ntasks,
                                       cudaStream_t s);
+// Batched tcgen05 projection of the tasks with tcp != 0 (one block per 256 pair rows,
+// blocks mapped to tasks through a prefix table), then each such task's new scale
+// s = sqrt((1 - discarded mass so far) / |V|^2) into tcs[1]. max_nk: the largest 16 c k.
+cudaError_t prepare_proj_tc_batch();
+cudaError_t launch_proj_pair_tc_batch(const TruncTask* tasks, const int* bstart, int nblocks, int ntasks,
+                                      int max_nk, cudaStream_t s);
 int64_t trunc_chunk(int64_t N2, int splits);
 int trunc_proj_blocks(int64_t N2, int k);
 // T = the solver's arithmetic (float or double, independent of the state's type);

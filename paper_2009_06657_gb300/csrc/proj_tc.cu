@@ -81,6 +81,13 @@ __global__ void k_proj_prep(const double2* __restrict__ D, int c, int k, float* 
   proj_prep_body(D, c, k, B, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// one task per blockIdx.y (tasks without the tensor-core projection return at once)
+__global__ void k_proj_prep_batch(const TruncTask* __restrict__ tasks) {
+  const TruncTask& tk = tasks[blockIdx.y];
+  if (!tk.tcp) return;
+  proj_prep_body(tk.D, tk.c, tk.k, tk.B, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 
 // the four float4 of pair-row data this thread stages for chunk ch
 __device__ __forceinline__ void load_rows(const float2* __restrict__ V, int ld, int c, int pairbit, int64_t N2,
@@ -303,7 +310,59 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
 }
 
 
+// task of block b: the last task whose first block is <= b
+__device__ __forceinline__ int pt_task_of_block(const int* __restrict__ bstart, int ntasks, int b) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bstart[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(PT_THREADS, 1)
+    k_proj_pair_tc_batch(const TruncTask* __restrict__ tasks, const int* __restrict__ bstart, int ntasks) {
+  const int t = pt_task_of_block(bstart, ntasks, blockIdx.x);
+  const TruncTask& tk = tasks[t];
+  proj_tc_body((const float2*)tk.V, tk.ld, tk.c, tk.k, tk.q, tk.N2, tk.B, (float2*)tk.W, tk.status,
+               blockIdx.x - bstart[t], tk.tcs + 2);
+}
+
+// one block per task: the per-block squared norms summed in a fixed order, the new scale
+__global__ void __launch_bounds__(256) k_trace_scale_batch(const TruncTask* __restrict__ tasks) {
+  const TruncTask& tk = tasks[blockIdx.x];
+  if (!tk.tcp) return;
+  __shared__ double red[256];
+  const int nparts = (int)((tk.N2 + PT_ROWS - 1) / PT_ROWS);
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 256) v += tk.tcs[2 + i];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double tr = 1.0 - tk.acc[0], n2 = red[0];
+    tk.tcs[1] = (n2 > 0.0 && tr > 0.0) ? sqrt(tr / n2) : 1.0;
+  }
+}
+
 }  // namespace
+
+cudaError_t prepare_proj_tc_batch() {
+  return cudaFuncSetAttribute(k_proj_pair_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM);
+}
+
+cudaError_t launch_proj_pair_tc_batch(const TruncTask* tasks, const int* bstart, int nblocks, int ntasks,
+                                      int max_nk, cudaStream_t s) {
+  if (nblocks <= 0) return cudaSuccess;
+  k_proj_prep_batch<<<dim3((max_nk + 255) / 256, ntasks), 256, 0, s>>>(tasks);
+  k_proj_pair_tc_batch<<<nblocks, PT_THREADS, PT_SMEM, s>>>(tasks, bstart, ntasks);
+  k_trace_scale_batch<<<ntasks, 256, 0, s>>>(tasks);
+  note_launches(3);
+  return cudaGetLastError();
+}
 
 bool proj_pair_tc_supported(int c, int k, int64_t N2) {
   return c % 8 == 0 && 4 * c <= 256 && k % 4 == 0 && k >= 4 && 4 * k <= PT_MAXN && N2 >= 4096;
