@@ -231,7 +231,8 @@ def run_ours(args, rank, world):
     # FP64 comparators at the same size (few truncations; rate per noisy gate-step)
     fp64 = bench_fp64(args, layers, dev, stream) if (rank == 0 and not args.no_fp64) else None
     adj = bench_adjoint(dev, stream) if (rank == 0 and not args.no_adjoint) else None
-    bat = bench_batch(dev, stream, scale=args.batch_scale) if (rank == 0 and not args.no_batch) else None
+    bat = (bench_batch(dev, stream, scale=args.batch_scale, cluster_min_m=args.batch_cluster_min_m)
+           if (rank == 0 and not args.no_batch) else None)
     epsl = bench_eps(dev, stream) if (rank == 0 and not args.no_eps) else None
     grv = bench_grover(dev, stream) if (rank == 0 and not args.no_grover) else None
     return dict(ms=ms, g_per=g_per, c_per=c_per, ktimes=ktimes, clk=clk, e2e_s=e2e_s, fp64=fp64, info=info,
@@ -441,7 +442,7 @@ def bench_grover(dev, stream, reps=3):
     return out
 
 
-def bench_batch(dev, stream, scale=1.0, sample_single=4, eig_precision="refined"):
+def bench_batch(dev, stream, scale=1.0, sample_single=4, eig_precision="refined", cluster_min_m=None):
     """256 seeded circuits (n ~ U{8..18}, r in {8,16,32,64}, depth ~ U{40..200}
     layers scaled by `scale`, mixed depolarizing 1e-3 / amplitude damping 2e-3),
     complex64, the eigensolve `eig_precision` (FP32 solve + FP64 refinement of the
@@ -449,7 +450,8 @@ def bench_batch(dev, stream, scale=1.0, sample_single=4, eig_precision="refined"
     advanced together by one CUDA-graph launch (timed once with CUDA events, after
     a warm-up run of the same circuits at 2% depth); against the first
     `sample_single` circuits run one at a time through the single-circuit path
-    (rate per gate-step)."""
+    (rate per gate-step). cluster_min_m: Gram matrices with at least this many rows
+    go to the 8-CTA cluster eigensolver (None: the library's default)."""
     import torch
 
     import paper_2009_06657_gb300 as lr
@@ -461,12 +463,13 @@ def bench_batch(dev, stream, scale=1.0, sample_single=4, eig_precision="refined"
     with torch.cuda.stream(stream):
         warm = batch_circuits(count=256, depth_scale=0.02)
         wb = lr.LRBatch(warm, dtype="c64", stream=stream, eig_precision=eig_precision,
-                        splits=table.splits_for(warm))
+                        splits=table.splits_for(warm), cluster_min_m=cluster_min_m)
         wb.run()
         torch.cuda.synchronize()
         wb.close()
         t0 = time.perf_counter()
-        b = lr.LRBatch(circs, dtype="c64", stream=stream, eig_precision=eig_precision, splits=splits)
+        b = lr.LRBatch(circs, dtype="c64", stream=stream, eig_precision=eig_precision, splits=splits,
+                       cluster_min_m=cluster_min_m)
         t_build = time.perf_counter() - t0
         st = b.stats()
         torch.cuda.synchronize()
@@ -495,6 +498,7 @@ def bench_batch(dev, stream, scale=1.0, sample_single=4, eig_precision="refined"
     return {"workload": f"256 random circuits, n U{{8..18}}, r in {{8,16,32,64}}, depth U{{40..200}} x {scale}, "
                         "mixed depolarizing 1e-3 / amplitude damping 2e-3, complex64",
             "eig_precision": eig_precision,
+            "cluster_min_m": cluster_min_m if cluster_min_m is not None else "library default (256)",
             "splits_table": os.path.basename(DEFAULT_TABLE) if table.entries else None,
             "splits_table_device": table.device or None,
             "gates": st["gates"], "truncations": st["truncations"], "truncations_done": trunc,
@@ -695,6 +699,7 @@ def main():
     ap.add_argument("--no-grover", action="store_true")
     ap.add_argument("--no-eig-variants", action="store_true")
     ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--batch-cluster-min-m", type=int, default=None)
     ap.add_argument("--no-eps", action="store_true")
     args = ap.parse_args()
     if args.profile_readouts:

@@ -355,6 +355,10 @@ typedef struct lr_batch_opts {
                         Tr rho = 1 - discarded mass after each projection, as in
                         lr_set_tensor_cores (the scale is kept per circuit and taken
                         into its next truncation and lr_batch_probs) */
+  int cluster_min_m; /* truncations whose Gram matrix has at least this many rows are
+                        solved by the 8-CTA cluster eigensolver, the others by the
+                        one-CTA solver, the two launches running side by side within a
+                        step; 0 = every truncation on the one-CTA solver (default 256) */
 } lr_batch_opts;
 void lr_batch_opts_default(lr_batch_opts* o);
 int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opts* opts, lr_batch_handle* out);
@@ -367,7 +371,8 @@ int lr_batch_info(lr_batch_handle b, int i, lr_info* info);
 /* Prob(x) of circuit i into a caller-owned device buffer (float for LR_C64).
  * Synchronises the batch's stream. */
 int lr_batch_probs(lr_batch_handle b, int i, void* out_dev);
-/* Totals: gates, truncations, schedule steps, kernel launches per run. */
+/* Totals: gates, truncations, schedule steps, and kernel launches per run (those
+ * captured in the graph; without a graph, those of the last lr_batch_run, 0 before). */
 int lr_batch_stats(lr_batch_handle b, int64_t* gates, int64_t* truncations, int64_t* steps, int64_t* launches);
 int lr_batch_free(lr_batch_handle b);
 

@@ -57,7 +57,7 @@ class lr_circuit(C.Structure):
 class lr_batch_opts(C.Structure):
     _fields_ = [("dtype", C.c_int), ("eig_precision", C.c_int), ("eig_iters", C.c_int),
                 ("rows_per_split", C.c_int), ("splits", C.POINTER(C.c_int)), ("use_graph", C.c_int),
-                ("stream", C.c_void_p), ("tensor_cores", C.c_int)]
+                ("stream", C.c_void_p), ("tensor_cores", C.c_int), ("cluster_min_m", C.c_int)]
 
 
 OP_KIND = {"rx": 0, "ry": 1, "rz": 2, "cnot": 3, "cz": 4, "dep": 5, "ad": 6, "bf": 7}

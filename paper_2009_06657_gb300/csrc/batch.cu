@@ -52,6 +52,8 @@ struct Step {
   int max_m = 0, max_k = 0;  // largest Gram size and rank of the step's truncations
   int tg_off = 0, tg_blocks = 0;  // tensor-core Gram of the step's eligible truncations
   int tp_off = 0, tp_blocks = 0, max_nk = 0;  // tensor-core projection
+  int tri_off = 0, tri_cnt = 0;  // step-local indices of the one-CTA solver's tasks
+  int cl_off = 0, cl_cnt = 0;    // the cluster solver's tasks (in lr_batch::cl_tasks)
 };
 
 
@@ -79,6 +81,10 @@ struct lr_batch {
   int count = 0, dtype = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;  // created here: the legacy default stream cannot be captured
+  cudaStream_t side = nullptr;  // second branch of a step's eigensolves
+  cudaEvent_t fork = nullptr, join = nullptr;
+  int cluster_min_m = 0;
+  std::vector<ClusterTask> cl_tasks;  // step-major
   size_t esz = 0;
   std::vector<Circ> circ;
   std::vector<Step> steps;
@@ -88,6 +94,7 @@ struct lr_batch {
   RefineTask* d_rt = nullptr;  // one per truncation task, same order (refined eigensolve)
   int* d_status = nullptr;     // set by a tensor-core kernel whose bounded wait gave up
   bool any_tc = false;
+  bool any_cluster = false;
   int* d_bs = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -244,6 +251,28 @@ int init_states(lr_batch* b) {
 // the eigensolver's arithmetic: FP64 for a complex128 state or when asked for
 bool solve_fp64(const lr_batch* b) { return b->dtype == LR_C128 || b->eig_prec == LR_EIGP_FP64; }
 
+// whether an m x m Gram matrix goes to the cluster solver
+bool uses_cluster(const lr_batch* b, int m) {
+  return b->cluster_min_m > 0 && m >= b->cluster_min_m && m <= eigh_cluster_max_m() && m >= 2;
+}
+
+// The step's eigensolves: the large Gram matrices on the cluster solver (main stream),
+// the others on the one-CTA solver (a forked branch when both kinds are present).
+template <typename T>
+cudaError_t solve_step(lr_batch* b, const Step& st, const TruncTask* tt, int all_vecs) {
+  const int* tri_sel = b->d_bs + st.tri_off;
+  const ClusterTask* cl = b->cl_tasks.data() + st.cl_off;
+  if (!st.cl_cnt) return launch_eigh_tri_batch<T>(tt, tri_sel, st.tri_cnt, all_vecs, b->stream);
+  if (!st.tri_cnt) return launch_eigh_cluster_batch<T>(cl, st.cl_cnt, all_vecs, b->stream);
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+  if (e == cudaSuccess) e = launch_eigh_tri_batch<T>(tt, tri_sel, st.tri_cnt, all_vecs, b->side);
+  if (e == cudaSuccess) e = launch_eigh_cluster_batch<T>(cl, st.cl_cnt, all_vecs, b->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
+  return e;
+}
+
 int enqueue(lr_batch* b) {
   const int dt = b->dtype;
   for (const Step& st : b->steps) {
@@ -260,11 +289,9 @@ int enqueue(lr_batch* b) {
         return launch_trunc_batch_gemms<decltype(t)>(tt, b->d_bs + st.gb_off, st.gram_blocks, b->d_bs + st.pb_off,
                                                      st.proj_blocks, st.t_cnt, st.max_m2, st.max_d, 0, b->stream);
       }));
-      if (solve_fp64(b)) {
-        BCK(launch_eigh_tri_batch<double>(tt, st.t_cnt, 0, b->stream));
-      } else {
-        const int refine = b->eig_prec == LR_EIGP_REFINED;
-        BCK(launch_eigh_tri_batch<float>(tt, st.t_cnt, refine, b->stream));
+      const int refine = !solve_fp64(b) && b->eig_prec == LR_EIGP_REFINED;
+      BCK(solve_fp64(b) ? solve_step<double>(b, st, tt, 0) : solve_step<float>(b, st, tt, refine));
+      if (!solve_fp64(b)) {
         if (refine)
           BCK(launch_eig_refine_batch(b->d_rt + st.t_off, st.t_cnt, st.max_m, st.max_k, b->eig_iters, b->stream));
       }
@@ -299,6 +326,9 @@ int lr_batch_free(lr_batch_handle b) {
   if (b->d_status) cudaFree(b->d_status);
   if (b->d_bs) cudaFree(b->d_bs);
   if (b->own_stream) cudaStreamDestroy(b->stream);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
   delete b;
   return LR_OK;
 }
@@ -313,6 +343,7 @@ void lr_batch_opts_default(lr_batch_opts* o) {
   o->use_graph = 1;
   o->stream = nullptr;
   o->tensor_cores = 1;
+  o->cluster_min_m = 256;
 }
 
 int lr_batch_create(const lr_circuit* circuits, int count, int dtype, int rows_per_split, int use_graph,
@@ -335,12 +366,14 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
   if (!circuits || count < 1 || (dtype != LR_C64 && dtype != LR_C128)) return LR_EINVAL;
   if (opts->eig_precision < LR_EIGP_REFINED || opts->eig_precision > LR_EIGP_FP64) return LR_EINVAL;
   if (opts->eig_precision == LR_EIGP_REFINED && (opts->eig_iters < 1 || opts->eig_iters > 4)) return LR_EINVAL;
+  if (opts->cluster_min_m < 0) return LR_EINVAL;
   if (rows_per_split <= 0) rows_per_split = 4096;
   lr_batch* b = new lr_batch();
   b->count = count;
   b->dtype = dtype;
   b->eig_prec = dtype == LR_C128 ? LR_EIGP_FP64 : opts->eig_precision;
   b->eig_iters = opts->eig_iters;
+  b->cluster_min_m = opts->cluster_min_m;
   b->stream = (cudaStream_t)stream;
   if (!b->stream && use_graph) {
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -405,7 +438,9 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
     if (!rc) rc = bmalloc(b, (void**)&C.D, sizeof(double2) * (size_t)c2 * c2);
     if (!rc) rc = bmalloc(b, (void**)&C.evals, sizeof(double) * m);
     if (!rc) rc = bmalloc(b, (void**)&C.eo, sizeof(EigOut));
-    if (!rc) rc = bmalloc(b, &C.eigwork, eigh_work_bytes(m, solve_fp64(b)));
+    size_t ew = eigh_work_bytes(m, solve_fp64(b));
+    if (uses_cluster(b, m)) ew = std::max(ew, eigh_cluster_work_bytes(solve_fp64(b)));
+    if (!rc) rc = bmalloc(b, &C.eigwork, ew);
     if (!rc && !solve_fp64(b) && b->eig_prec == LR_EIGP_REFINED) rc = bmalloc(b, &C.rfwork, eig_refine_work_bytes(m));
   }
   if (rc) {
@@ -422,7 +457,8 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
     Step& S = b->steps[s];
     S.e_off = (int)et.size();
     S.t_off = (int)tt.size();
-    std::vector<int> eblocks, gblocks, pblocks, tgblocks, tpblocks;
+    std::vector<int> eblocks, gblocks, pblocks, tgblocks, tpblocks, tri_sel;
+    S.cl_off = (int)b->cl_tasks.size();
     for (int i = 0; i < count; ++i) {
       if (s >= stages[i].size()) continue;
       const HStage& h = stages[i][s];
@@ -479,6 +515,10 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
           t.splits = C.tc_splits;
           b->any_tc = true;
         }
+        if (uses_cluster(b, t.m))
+          b->cl_tasks.push_back(ClusterTask{C.G, C.eigwork, C.evals, C.evecs, C.eo, t.m, t.k});
+        else
+          tri_sel.push_back((int)tt.size() - S.t_off);
         tt.push_back(t);
         rt.push_back(RefineTask{C.G, t.m, t.k, C.evals, C.evecs, C.eo, C.rfwork});
         S.max_m = std::max(S.max_m, t.m);
@@ -513,9 +553,12 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
       prefix(pblocks, &S.pb_off, &S.proj_blocks);
       prefix(tgblocks, &S.tg_off, &S.tg_blocks);
       prefix(tpblocks, &S.tp_off, &S.tp_blocks);
+      S.tri_off = (int)bs.size();
+      S.tri_cnt = (int)tri_sel.size();
+      bs.insert(bs.end(), tri_sel.begin(), tri_sel.end());
+      S.cl_cnt = (int)b->cl_tasks.size() - S.cl_off;
+      if (S.cl_cnt) b->any_cluster = true;
     }
-    b->launches += (S.e_cnt ? 1 : 0) + (S.t_cnt ? 6 : 0);
-    if (S.t_cnt && !solve_fp64(b) && b->eig_prec == LR_EIGP_REFINED) b->launches += eig_refine_launches(b->eig_iters);
   }
   rc = bmalloc(b, (void**)&b->d_et, sizeof(ExpandTask) * std::max<size_t>(1, et.size()));
   if (!rc) rc = bmalloc(b, (void**)&b->d_tt, sizeof(TruncTask) * std::max<size_t>(1, tt.size()));
@@ -533,6 +576,11 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
     e = cudaMemcpy(b->d_rt, rt.data(), sizeof(RefineTask) * rt.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !bs.empty()) e = cudaMemcpy(b->d_bs, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = solve_fp64(b) ? prepare_eigh_tri_batch<double>() : prepare_eigh_tri_batch<float>();
+  if (e == cudaSuccess && b->any_cluster)
+    e = solve_fp64(b) ? prepare_eigh_cluster_batch<double>() : prepare_eigh_cluster_batch<float>();
+  if (e == cudaSuccess && b->any_cluster) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess && b->any_cluster) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && b->any_cluster) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
   if (e == cudaSuccess && b->any_tc) e = prepare_gram_tc_batch();
   if (e == cudaSuccess && b->any_tc) e = prepare_proj_tc_batch();
   if (e != cudaSuccess) {
@@ -549,6 +597,7 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
       rc = enqueue(b);
       // captured launches run on each replay, not now
       b->graph_kernels = lret::launches_total() - before;
+      b->launches = b->graph_kernels;
       lret::note_launches(-b->graph_kernels);
       cudaGraph_t g = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -579,7 +628,10 @@ int lr_batch_run(lr_batch_handle b) {
     lret::note_launches(b->graph_kernels);
     return LR_OK;
   }
-  return enqueue(b);
+  const long long before = lret::launches_total();
+  const int rc = enqueue(b);
+  b->launches = lret::launches_total() - before;
+  return rc;
 }
 
 int lr_batch_reset(lr_batch_handle b) {

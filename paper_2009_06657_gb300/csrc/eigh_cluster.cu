@@ -598,11 +598,16 @@ __device__ __forceinline__ long long phase_clock() { return clock64(); }
 
 }  // namespace
 
+// The arguments are references: the single-matrix kernel binds them to its parameters
+// and the batched kernel to its launch's task list (also kernel parameters), so that
+// neither holds them in registers across the solve.
 template <typename T>
-__global__ void __launch_bounds__(CL_THREADS, 1)
-    k_eigh_cluster(const double2* __restrict__ G, int m, cx<T>* __restrict__ gref, T* __restrict__ gZ,
-                   double* __restrict__ evals, double2* __restrict__ evecs, EigOut* __restrict__ out, int r,
-                   double eps, int all_vecs) {
+__device__ __forceinline__ void eigh_cluster_body(const double2* __restrict__ const& G, const int& m,
+                                                  cx<T>* __restrict__ const& gref, T* __restrict__ const& gZ,
+                                                  double* __restrict__ const& evals,
+                                                  double2* __restrict__ const& evecs,
+                                                  EigOut* __restrict__ const& out, const int& r, const double& eps,
+                                                  const int& all_vecs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ClusterShared<T>& sh = *reinterpret_cast<ClusterShared<T>*>(smem_raw);
   cg::cluster_group cluster = cg::this_cluster();
@@ -1457,6 +1462,32 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
 }
 
 template <typename T>
+__global__ void __launch_bounds__(CL_THREADS, 1)
+    k_eigh_cluster(const double2* __restrict__ G, int m, cx<T>* __restrict__ gref, T* __restrict__ gZ,
+                   double* __restrict__ evals, double2* __restrict__ evecs, EigOut* __restrict__ out, int r,
+                   double eps, int all_vecs) {
+  eigh_cluster_body<T>(G, m, gref, gZ, evals, evecs, out, r, eps, all_vecs);
+}
+
+// One cluster of CL CTAs per task A.task[blockIdx.y]. The task list is a kernel
+// parameter (constant bank): read through it, the solve keeps its arguments out of
+// registers as the single-matrix kernel does.
+struct ClusterBatchArgs {
+  ClusterTask task[CL_BATCH_MAX];
+  int all_vecs;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(CL_THREADS, 1)
+    k_eigh_cluster_batch(const __grid_constant__ ClusterBatchArgs A) {
+  const ClusterTask& tk = A.task[blockIdx.y];
+  cx<T>* gref = (cx<T>*)tk.work;
+  T* gZ = (T*)(gref + (size_t)CL_MAXM * CL_MAXM);
+  const double eps = 0.0;
+  eigh_cluster_body<T>(tk.G, tk.m, gref, gZ, tk.evals, tk.evecs, tk.out, tk.r, eps, A.all_vecs);
+}
+
+template <typename T>
 size_t eigh_cluster_smem() {
   return sizeof(ClusterShared<T>) + (size_t)LuExtra<T>::slots * 6 * CL_MAXM * sizeof(T);
 }
@@ -1491,6 +1522,40 @@ cudaError_t launch_eigh_cluster(const double2* G, int m, void* work, double* eva
   return e;
 }
 
+template <typename T>
+cudaError_t prepare_eigh_cluster_batch() {
+  return cudaFuncSetAttribute(k_eigh_cluster_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)eigh_cluster_smem<T>());
+}
+
+template <typename T>
+cudaError_t launch_eigh_cluster_batch(const ClusterTask* tasks, int n, int all_vecs, cudaStream_t s) {
+  for (int t0 = 0; t0 < n; t0 += CL_BATCH_MAX) {
+    const int cnt = n - t0 < CL_BATCH_MAX ? n - t0 : CL_BATCH_MAX;
+    ClusterBatchArgs A;
+    for (int i = 0; i < cnt; ++i) A.task[i] = tasks[t0 + i];
+    A.all_vecs = all_vecs;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL, cnt, 1);
+    cfg.blockDim = dim3(CL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = eigh_cluster_smem<T>();
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_eigh_cluster_batch<T>, A);
+    note_launches(1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int eigh_cluster_max_m() { return CL_MAXM; }
+
 size_t eigh_cluster_work_bytes(bool fp64) {
   const size_t e = fp64 ? sizeof(double) : sizeof(float);
   // reflectors (complex, last row tau), Z (real), three row buffers (complex)
@@ -1501,5 +1566,10 @@ template cudaError_t launch_eigh_cluster<float>(const double2*, int, void*, doub
                                                 int, cudaStream_t);
 template cudaError_t launch_eigh_cluster<double>(const double2*, int, void*, double*, double2*, EigOut*, int,
                                                  double, int, cudaStream_t);
+
+template cudaError_t prepare_eigh_cluster_batch<float>();
+template cudaError_t prepare_eigh_cluster_batch<double>();
+template cudaError_t launch_eigh_cluster_batch<float>(const ClusterTask*, int, int, cudaStream_t);
+template cudaError_t launch_eigh_cluster_batch<double>(const ClusterTask*, int, int, cudaStream_t);
 
 }  // namespace lret

@@ -552,7 +552,6 @@ size_t eig_refine_work_bytes(int m) {
          + (size_t)3 * kmax * sizeof(double) + 256;                     // mu, mu2, alpha
 }
 
-int eig_refine_launches(int iters) { return 5 * iters + 2 * (RF_ORTHO - 1) + 3 + 1; }
 
 cudaError_t launch_eig_refine(const double2* G, int m, double* evals, double2* evecs, EigOut* eo, int kmax,
                               int iters, void* work, cudaStream_t s) {

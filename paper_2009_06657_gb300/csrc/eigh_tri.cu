@@ -632,10 +632,12 @@ __host__ __device__ __forceinline__ int tri_split_for(int m, size_t elem, size_t
   return m;
 }
 
-// one circuit's eigensolve per block; every eigenvector only where a refinement follows
+// one circuit's eigensolve per block (task tasks[sel[blockIdx.x]]); every eigenvector
+// only where a refinement follows
 template <typename T>
-__global__ void __launch_bounds__(TRI_THREADS) k_eigh_tri_batch(const TruncTask* __restrict__ tasks, int all_vecs) {
-  const TruncTask& tk = tasks[blockIdx.x];
+__global__ void __launch_bounds__(TRI_THREADS)
+    k_eigh_tri_batch(const TruncTask* __restrict__ tasks, const int* __restrict__ sel, int all_vecs) {
+  const TruncTask& tk = tasks[sel[blockIdx.x]];
   const int m = tk.m;
   const int c_split = tri_split_for(m, sizeof(cx<T>), TRI_DYN_MAX);
   cx<T>* gpacked = (cx<T>*)tk.eigwork;
@@ -651,16 +653,16 @@ cudaError_t prepare_eigh_tri_batch() {
 // prepare_eigh_tri_batch<T>() must have run once (it is not a stream operation,
 // so it stays outside graph capture)
 template <typename T>
-cudaError_t launch_eigh_tri_batch(const TruncTask* tasks, int ntasks, int all_vecs, cudaStream_t s) {
-  if (ntasks <= 0) return cudaSuccess;
-  k_eigh_tri_batch<T><<<ntasks, TRI_THREADS, TRI_DYN_MAX, s>>>(tasks, all_vecs);
+cudaError_t launch_eigh_tri_batch(const TruncTask* tasks, const int* sel, int nsel, int all_vecs, cudaStream_t s) {
+  if (nsel <= 0) return cudaSuccess;
+  k_eigh_tri_batch<T><<<nsel, TRI_THREADS, TRI_DYN_MAX, s>>>(tasks, sel, all_vecs);
   note_launches(1);
   return cudaGetLastError();
 }
 template cudaError_t prepare_eigh_tri_batch<float>();
 template cudaError_t prepare_eigh_tri_batch<double>();
-template cudaError_t launch_eigh_tri_batch<float>(const TruncTask*, int, int, cudaStream_t);
-template cudaError_t launch_eigh_tri_batch<double>(const TruncTask*, int, int, cudaStream_t);
+template cudaError_t launch_eigh_tri_batch<float>(const TruncTask*, const int*, int, int, cudaStream_t);
+template cudaError_t launch_eigh_tri_batch<double>(const TruncTask*, const int*, int, int, cudaStream_t);
 
 template <typename T>
 static int tri_c_split(int m, size_t budget) {

@@ -162,9 +162,10 @@ cudaError_t launch_proj_pair_tc_batch(const TruncTask* tasks, const int* bstart,
 int64_t trunc_chunk(int64_t N2, int splits);
 int trunc_proj_blocks(int64_t N2, int k);
 // T = the solver's arithmetic (float or double, independent of the state's type);
-// all_vecs != 0 returns every eigenvector (for a refinement that follows)
+// all_vecs != 0 returns every eigenvector (for a refinement that follows); one block per
+// task tasks[sel[i]], i < nsel
 template <typename T>
-cudaError_t launch_eigh_tri_batch(const TruncTask* tasks, int ntasks, int all_vecs, cudaStream_t s);
+cudaError_t launch_eigh_tri_batch(const TruncTask* tasks, const int* sel, int nsel, int all_vecs, cudaStream_t s);
 template <typename T>
 cudaError_t prepare_eigh_tri_batch();
 
@@ -222,6 +223,24 @@ template <typename T>
 cudaError_t launch_eigh_cluster(const double2* G, int m, void* work, double* evals, double2* evecs, EigOut* out,
                                 int r, double eps, int all_vecs, cudaStream_t s);
 size_t eigh_cluster_work_bytes(bool fp64);
+int eigh_cluster_max_m();
+// Batched cluster solve: one 8-CTA cluster per task (work: eigh_cluster_work_bytes;
+// r = the kept count; the task list is copied into the launch's parameters,
+// CL_BATCH_MAX tasks per launch). prepare_eigh_cluster_batch<T>() sets the
+// shared-memory limit (not a stream operation: call it before any graph capture).
+struct ClusterTask {
+  const double2* G;
+  void* work;
+  double* evals;
+  double2* evecs;
+  EigOut* out;
+  int m, r;
+};
+constexpr int CL_BATCH_MAX = 64;
+template <typename T>
+cudaError_t prepare_eigh_cluster_batch();
+template <typename T>
+cudaError_t launch_eigh_cluster_batch(const ClusterTask* tasks, int n, int all_vecs, cudaStream_t s);
 
 // ---- FP64 refinement of the kept eigenvectors after an FP32 solve that returned
 // all m eigenvectors (evecs m x m, columns descending; evals m): `iters` steps on
@@ -242,7 +261,6 @@ struct RefineTask {
 };
 cudaError_t launch_eig_refine_batch(const RefineTask* tasks, int ntasks, int m_max, int kmax_max, int iters,
                                     cudaStream_t s);
-int eig_refine_launches(int iters);  // kernel launches of one refinement
 
 // ---- adjoint of a truncation: builds Mcat ((k+m) x m complex128) =
 // [U_r^dag ; B + B^dag] with B = U_d (F o (U_d^dag C)) U_r^dag, F_ji = 1/(lam_i - lam_j).

@@ -361,10 +361,12 @@ class LRBatch:
     """
 
     def __init__(self, circuits, dtype="c64", rows_per_split=0, use_graph=True, stream=None,
-                 eig_precision="refined", eig_iters=1, splits=None, tensor_cores=True):
+                 eig_precision="refined", eig_iters=1, splits=None, tensor_cores=True, cluster_min_m=None):
         """eig_precision (complex64): "refined" (FP32 solve + FP64 refinement of the kept
         eigenvectors), "fp32" or "fp64". splits: None or one Gram split count per
-        circuit (0 = from rows_per_split), e.g. from autotune.BatchTable.splits_for."""
+        circuit (0 = from rows_per_split), e.g. from autotune.BatchTable.splits_for.
+        cluster_min_m: Gram matrices with at least this many rows go to the 8-CTA cluster
+        eigensolver (0: none; None: the library's default)."""
         if not torch.cuda.is_available():
             raise RuntimeError("liblret needs a CUDA device")
         self.dtype = _ffi.LR_C64 if dtype in ("c64", "complex64", _ffi.LR_C64) else _ffi.LR_C128
@@ -399,6 +401,8 @@ class LRBatch:
             opts.splits = C.cast(sp, C.POINTER(C.c_int))
         opts.use_graph = 1 if use_graph else 0
         opts.tensor_cores = 1 if tensor_cores else 0
+        if cluster_min_m is not None:
+            opts.cluster_min_m = int(cluster_min_m)
         opts.stream = self.stream.cuda_stream
         h = C.c_void_p()
         check(lib.lr_batch_create_ex(arr, len(circuits), C.byref(opts), C.byref(h)), "lr_batch_create_ex")

@@ -152,6 +152,32 @@ def test_per_circuit_split_counts_do_not_change_results(lr, dtype):
         assert np.sum(np.abs(p0 - p1)) < tol and abs(d0 - d1) < tol
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_cluster_and_one_cta_eigensolvers_of_a_batch_agree(lr, dtype):
+    """Truncations whose Gram matrix has at least cluster_min_m rows run on the 8-CTA
+    cluster solver, in a graph branch beside the one-CTA solver of the others: every
+    truncation on one solver (0; 2), or split between the two (64: the 9-qubit circuit's
+    128- and 64-row matrices on the cluster, the rest on one CTA), gives the same states."""
+    circs = _small_batch() + [{"n": 9, "r": 32, "ops": random_layered(9, 2, seed=5400, noise=("mixed", 2e-2, 4e-2),
+                                                                     qubit_jitter=(0.5, 1.5))}]
+    tol = 1e-11 if dtype == "c128" else 1e-5
+    outs = []
+    for cmin in (0, 2, 64):
+        b = lr.LRBatch(circs, dtype=dtype, cluster_min_m=cmin)
+        b.run()
+        outs.append([(b.probs(i).double().cpu().numpy(), b.info(i)) for i in range(len(circs))])
+        b.close()
+    for other in outs[1:]:
+        for i, ((p0, i0), (p1, i1)) in enumerate(zip(outs[0], other)):
+            assert i1["converged"], i
+            assert np.sum(np.abs(p0 - p1)) < tol, i
+            assert abs(i0["discarded"] - i1["discarded"]) < tol, i
+    # and the 9-qubit circuit against the oracle
+    ref = O.run_lret(9, circs[-1]["ops"], r=32)
+    assert np.sum(np.abs(outs[2][-1][0] - ref.probs())) < tol
+    assert abs(outs[2][-1][1]["discarded"] - ref.discarded) < tol
+
+
 def test_tensor_core_tasks_of_a_batch_match_single_runs_and_oracle(lr):
     """Circuits with 2^12 row pairs and more take the batched tcgen05 Gram and
     projection (one launch each per step for all of them, blocks mapped to tasks through
