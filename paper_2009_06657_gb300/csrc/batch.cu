@@ -7,10 +7,13 @@
 // and, folded into it, a one-qubit gate on the same qubit; Gram of the row
 // pairs, eigensolve, projection on the row pairs). Stage s of every circuit
 // runs in the same batched launches: one expansion launch, then the truncation
-// launches (pair Gram + assembly, one eigensolver block per circuit,
-// projection + accounting). Per-step task tables and block-to-task prefix
-// tables are built and uploaded once; the whole schedule is captured into one
-// CUDA graph, so a run is a single graph launch.
+// launches (pair Gram, split sums, assembly; the eigensolves: one CTA per circuit,
+// or an 8-CTA cluster for the largest Gram matrices, the two in parallel graph
+// branches; for a complex64 state the FP64 refinement; projection matrix,
+// projection, accounting). The Gram and the projection of a complex64 circuit
+// with enough rows run on the tensor cores. Per-step task tables and block-to-task
+// prefix tables are built and uploaded once; the whole schedule is captured into
+// one CUDA graph, so a run is a single graph launch.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -34,7 +37,7 @@ struct Circ {
   int c = 1;     // columns after the whole schedule
   int splits = 1;
   double* acc = nullptr;
-  double2 *partials = nullptr, *G = nullptr, *evecs = nullptr, *D = nullptr;
+  double2 *partials = nullptr, *S = nullptr, *G = nullptr, *evecs = nullptr, *D = nullptr;
   double* evals = nullptr;
   EigOut* eo = nullptr;
   void* eigwork = nullptr;
@@ -317,7 +320,7 @@ int lr_batch_free(lr_batch_handle b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (auto& C : b->circ) {
     for (int i = 0; i < 2; ++i) if (C.buf[i]) cudaFree(C.buf[i]);
-    void* ps[] = {C.acc, C.partials, C.G, C.evecs, C.D, C.evals, C.eo, C.eigwork, C.rfwork, C.B, C.tcs};
+    void* ps[] = {C.acc, C.partials, C.S, C.G, C.evecs, C.D, C.evals, C.eo, C.eigwork, C.rfwork, C.B, C.tcs};
     for (void* p : ps) if (p) cudaFree(p);
   }
   if (b->d_et) cudaFree(b->d_et);
@@ -436,6 +439,7 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
     if (!rc) rc = bmalloc(b, (void**)&C.G, sizeof(double2) * (size_t)m * m);
     if (!rc) rc = bmalloc(b, (void**)&C.evecs, sizeof(double2) * (size_t)m * m);
     if (!rc) rc = bmalloc(b, (void**)&C.D, sizeof(double2) * (size_t)c2 * c2);
+    if (!rc) rc = bmalloc(b, (void**)&C.S, sizeof(double2) * (size_t)c2 * c2);
     if (!rc) rc = bmalloc(b, (void**)&C.evals, sizeof(double) * m);
     if (!rc) rc = bmalloc(b, (void**)&C.eo, sizeof(EigOut));
     size_t ew = eigh_work_bytes(m, solve_fp64(b));
@@ -498,6 +502,7 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
           for (int a = 0; a < 2; ++a)
             for (int g = 0; g < 2; ++g) put(t.M[al][a][g], h.M[al][a][g]);
         t.partials = C.partials;
+        t.S = C.S;
         t.G = C.G;
         t.evals = C.evals;
         t.evecs = C.evecs;
@@ -530,7 +535,7 @@ int lr_batch_create_ex(const lr_circuit* circuits, int count, const lr_batch_opt
         tgblocks.push_back(t.tc ? t.splits : 0);
         tpblocks.push_back(t.tcp ? proj_pair_tc_blocks(t.N2) : 0);
         if (t.tcp) S.max_nk = std::max(S.max_nk, 16 * t.c * t.k);
-        S.max_m2 = std::max(S.max_m2, t.m * t.m);
+        S.max_m2 = std::max({S.max_m2, t.m * t.m, 4 * t.c * t.c});
         S.max_d = std::max(S.max_d, 4 * t.c * t.k);
         ++C.truncs;
         ++b->truncs;

@@ -507,9 +507,35 @@ __global__ void __launch_bounds__(256) k_pair_gram_batch(const TruncTask* __rest
                (c2 + TILE - 1) / TILE, 1, tk.partials, tk.q, tk.c, l % tiles, l / tiles);
 }
 
-// G'[al c + i][be c + j] = sum_{b,b'} (M_al^dag M_be)_{bb'} S[b c + i][b' c + j], S summed over
-// splits (FP64 partials of the SIMT Gram, upper triangle by TILE blocks; or FP32 partials of the
-// tensor-core Gram, upper triangle by 64-row blocks)
+// S = the pair Gram summed over splits, in split order (FP64 partials of the SIMT Gram, upper
+// triangle by TILE blocks; or FP32 partials of the tensor-core Gram, upper triangle by 64-row
+// blocks); only the blocks the Gram computed are written
+__global__ void __launch_bounds__(256) k_split_sum_batch(const TruncTask* __restrict__ tasks) {
+  const TruncTask& tk = tasks[blockIdx.y];
+  const int c2 = 2 * tk.c;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= c2 * c2) return;
+  const int si = e / c2, sj = e % c2;
+  const int blk = tk.tc ? 64 : TILE;
+  if (si / blk > sj / blk) return;
+  const int64_t stride = (int64_t)c2 * c2;
+  double sr = 0.0, sim = 0.0;
+  if (tk.tc) {
+    const float2* pf = reinterpret_cast<const float2*>(tk.partials);
+    for (int sp = 0; sp < tk.splits; ++sp) {
+      const float2 v = pf[sp * stride + e];
+      sr += (double)v.x; sim += (double)v.y;
+    }
+  } else {
+    for (int sp = 0; sp < tk.splits; ++sp) {
+      const double2 v = tk.partials[sp * stride + e];
+      sr += v.x; sim += v.y;
+    }
+  }
+  tk.S[e] = make_double2(sr, sim);
+}
+
+// G'[al c + i][be c + j] = sum_{b,b'} (M_al^dag M_be)_{bb'} S[b c + i][b' c + j]
 __global__ void __launch_bounds__(256) k_reduce_assemble_batch(const TruncTask* __restrict__ tasks) {
   const TruncTask& tk = tasks[blockIdx.y];
   const int c = tk.c, K = tk.K, m = K * c, c2 = 2 * c;
@@ -517,7 +543,6 @@ __global__ void __launch_bounds__(256) k_reduce_assemble_batch(const TruncTask* 
   if (e >= m * m) return;
   const int row = e / m, col = e % m;
   const int al = row / c, i = row % c, be = col / c, j = col % c;
-  const int64_t stride = (int64_t)c2 * c2;
   double2 acc = make_double2(0, 0);
 #pragma unroll
   for (int b = 0; b < 2; ++b)
@@ -527,20 +552,8 @@ __global__ void __launch_bounds__(256) k_reduce_assemble_batch(const TruncTask* 
       const int blk = tk.tc ? 64 : TILE;
       const bool upper = (si / blk) <= (sj / blk);  // blocks computed by the Gram
       const int64_t idx = upper ? (int64_t)si * c2 + sj : (int64_t)sj * c2 + si;
-      double sr = 0.0, sim = 0.0;
-      if (tk.tc) {
-        const float2* pf = reinterpret_cast<const float2*>(tk.partials);
-        for (int sp = 0; sp < tk.splits; ++sp) {
-          const float2 v = pf[sp * stride + idx];
-          sr += (double)v.x; sim += (double)v.y;
-        }
-      } else {
-        for (int sp = 0; sp < tk.splits; ++sp) {
-          const double2 v = tk.partials[sp * stride + idx];
-          sr += v.x; sim += v.y;
-        }
-      }
-      if (!upper) sim = -sim;
+      const double2 v = tk.S[idx];
+      const double sr = v.x, sim = upper ? v.y : -v.y;
       double2 q = make_double2(0, 0);
 #pragma unroll
       for (int a = 0; a < 2; ++a) cfmac(q, tk.M[al][a][b], tk.M[be][a][bp]);
@@ -601,8 +614,9 @@ cudaError_t launch_trunc_batch_gemms(const TruncTask* tasks, const int* gram_bst
       k_pair_gram_batch<T><<<gram_blocks, 256, 0, s>>>(tasks, gram_bstart, ntasks);
       note_launches(1);
     }
+    k_split_sum_batch<<<dim3((max_m2 + 255) / 256, ntasks), 256, 0, s>>>(tasks);  // max_m2 >= (2c)^2 too
     k_reduce_assemble_batch<<<dim3((max_m2 + 255) / 256, ntasks), 256, 0, s>>>(tasks);
-    note_launches(1);
+    note_launches(2);
   } else {
     k_build_proj_batch<<<dim3((max_d + 255) / 256, ntasks), 256, 0, s>>>(tasks);
     note_launches(1);

@@ -120,6 +120,7 @@ struct TruncTask {
   int c, ld, K, k, q, splits, tiles, m;
   double2 M[4][2][2]; // Kt_a G
   double2* partials;  // splits x (2c)^2
+  double2* S;         // (2c)^2: the partials summed over splits
   double2* G;         // m x m Gram of the implicit V'
   double* evals;
   double2* evecs;
@@ -141,7 +142,8 @@ struct TruncTask {
   float* B;
   double* tcs;
 };
-// phase 0: pair Gram + reduce/assemble G'; phase 1: projection matrix, pair projection, accounting
+// phase 0: pair Gram, split sums, assembly of G'; phase 1: projection matrix, pair projection,
+// accounting. max_m2: the largest m^2 or (2c)^2 of the tasks.
 template <typename T>
 cudaError_t launch_trunc_batch_gemms(const TruncTask* tasks, const int* gram_bstart, int gram_blocks,
                                      const int* proj_bstart, int proj_blocks, int ntasks, int max_m2,
