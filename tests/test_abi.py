@@ -134,3 +134,19 @@ def test_package_import_fails_loudly_without_the_library(tmp_path):
 def test_launch_counter_reads_without_device(lib):
     n = lib.lib.lr_launch_count()
     assert isinstance(n, int) and n >= 0
+
+
+def test_batch_options_struct_matches_the_header(lib):
+    """lr_batch_opts_default (host only) fills the caller's struct: every field the
+    Python mirror declares holds the header's default, and nothing past the mirror's
+    size is written (a field added to one side only would show here)."""
+    import ctypes as C
+    f = lib
+    size = C.sizeof(f.lr_batch_opts)
+    buf = (C.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    f.lib.lr_batch_opts_default(C.cast(buf, C.POINTER(f.lr_batch_opts)))
+    o = f.lr_batch_opts.from_buffer(buf)
+    assert o.dtype == f.LR_C64 and o.eig_precision == f.LR_EIGP_REFINED and o.eig_iters == 1
+    assert o.rows_per_split == 0 and not o.splits and o.use_graph == 1 and not o.stream
+    assert o.tensor_cores == 1 and o.cluster_min_m == 256
+    assert all(b == 0xAB for b in buf[size:])

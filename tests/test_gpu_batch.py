@@ -157,13 +157,14 @@ def test_cluster_and_one_cta_eigensolvers_of_a_batch_agree(lr, dtype):
     """Truncations whose Gram matrix has at least cluster_min_m rows run on the 8-CTA
     cluster solver, in a graph branch beside the one-CTA solver of the others: every
     truncation on one solver (0; 2), or split between the two (64: the 9-qubit circuit's
-    128- and 64-row matrices on the cluster, the rest on one CTA), gives the same states."""
+    128- and 64-row matrices on the cluster, the rest on one CTA; with the graph and
+    with direct launches on two streams), gives the same states."""
     circs = _small_batch() + [{"n": 9, "r": 32, "ops": random_layered(9, 2, seed=5400, noise=("mixed", 2e-2, 4e-2),
                                                                      qubit_jitter=(0.5, 1.5))}]
     tol = 1e-11 if dtype == "c128" else 1e-5
     outs = []
-    for cmin in (0, 2, 64):
-        b = lr.LRBatch(circs, dtype=dtype, cluster_min_m=cmin)
+    for cmin, graph in ((0, True), (2, True), (64, True), (64, False)):
+        b = lr.LRBatch(circs, dtype=dtype, cluster_min_m=cmin, use_graph=graph)
         b.run()
         outs.append([(b.probs(i).double().cpu().numpy(), b.info(i)) for i in range(len(circs))])
         b.close()
