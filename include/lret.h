@@ -292,7 +292,10 @@ int64_t lr_device_bytes(lr_handle h);
  * stay in it (every value a call reads is written by that call first): calls
  * that overlap on the GPU, from different streams or threads, race and must be
  * serialised by the caller. T > LR_STATIC_MAX_TERMS returns LR_ECAPACITY.
- * Synchronises the stream. */
+ * Synchronises the stream, so it is not a call to make on a stream that is
+ * capturing a graph (nor on NULL while any global-mode capture is open); the
+ * first call on a device, which does the one-time address lookup, belongs
+ * before any stream capture the process starts. */
 #define LR_STATIC_MAX_TERMS 256
 int lr_expect_static(const void* V_dev, int n, int c, int ld, int dtype, int T,
                      const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
