@@ -140,10 +140,9 @@ CIRCUITS = [
 @pytest.mark.parametrize("case", CIRCUITS, ids=[f"n{c[0]}r{c[1]}d{c[2]}" for c in CIRCUITS])
 def test_truncated_circuit_parity(lr, dtype, case, solver):
     n, r, depth, noise, seed = case
-    if dtype == "c128" and solver != "tridiag" and 4 * r > 128:
-        pytest.skip("FP64 Jacobi above 128 columns runs at the FP64 rate of this part; tridiagonal path covers it")
-    if solver == "jacobi" and dtype == "c64" and 4 * r > 128:
-        pytest.skip("FP32 Jacobi above 128 columns is the slow reference solver")
+    if solver == "jacobi" and 4 * r > 128:
+        pytest.skip("Jacobi above 128 columns is the slow reference solver (the FP64 one runs at the FP64 "
+                    "rate of this part); the tridiagonal and cluster solvers cover these sizes")
     if dtype == "c64":
         depth = 1  # FP32 rounding at deep near-tied cuts alone would approach the tolerance
     ops, ref, _ = _pick(n, r, depth, noise, seed, dtype)
@@ -259,6 +258,33 @@ def test_errors(lr):
     with pytest.raises(LRError) as e:
         sim.apply_gate([1, 1], np.eye(4))
     assert e.value.status == LR_EINVAL
+
+
+def test_column_limit_of_the_eigensolvers(lr):
+    """256 columns is the largest truncation the eigensolvers take (the benchmark's
+    r = 64 with four Kraus operators reaches it exactly). With r = 65 the fourth
+    depolarizing channel makes 256 columns and is truncated to 65; the fifth would
+    need 260 and its truncation is refused with LR_ECAPACITY. The refusal leaves the
+    expanded state (Eq. 4 without the truncation) in place and readable."""
+    from paper_2009_06657_gb300._ffi import LRError, LR_ECAPACITY
+    n, r = 7, 65
+    ops = random_layered(n, 1, seed=1500, noise=("dep", 0.02), qubit_jitter=(0.5, 1.5))
+    chans = [i for i, o in enumerate(ops) if O.is_channel(o)]
+    pre, last = ops[: chans[4]], ops[chans[4]]
+    ref = O.run_lret(n, pre, r=r)
+    assert [e["m"] for e in ref.log] == [4, 16, 64, 256]
+    ref.channel(last["q"], O.channel_kraus(last))  # the refused truncation's channel, untruncated
+    sim = lr.LRSim(n, r, dtype="c128")  # capacity 4r = 260 columns
+    lr.run_ops(sim, pre, r=r)
+    assert sim.info()["columns"] == r
+    sim.apply_channel("dep", last["q"], last["p"])
+    with pytest.raises(LRError) as e:
+        sim.compress(r)
+    assert e.value.status == LR_ECAPACITY
+    assert sim.info()["columns"] == 4 * r
+    p = sim.probs().cpu().numpy()
+    assert np.sum(np.abs(p - ref.probs())) < TOL["c128"]
+    sim.close()
 
 
 def test_deterministic_repeat(lr):
@@ -486,7 +512,9 @@ def test_deferred_projection_matches_oracle_and_eager_projection(lr, dtype):
         pytest.skip("no seed with well-separated cuts")
     sim = lr.LRSim(n, r, dtype=dtype)
     lr.run_ops(sim, ops, r=r)
-    tol = TOL[dtype] + 2 * UNIT[dtype] * _cut_sensitivity(ref)
+    tol = TOL[dtype]
+    print(f"{dtype}: L1 Prob(x) {np.sum(np.abs(sim.probs().double().cpu().numpy() - ref.probs())):.3e}, "
+          f"predicted cut error {UNIT[dtype] * _cut_sensitivity(ref):.3e}")
     _compare(lr, sim, ref, n, random_pauli_sum(n, 12, seed=s + 1), tol)
     assert abs(sim.info()["discarded"] - ref.discarded) < tol
     # eager: read the state's trace after every truncation (materialises it)
