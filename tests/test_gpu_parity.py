@@ -264,8 +264,8 @@ def test_column_limit_of_the_eigensolvers(lr):
     """256 columns is the largest truncation the eigensolvers take (the benchmark's
     r = 64 with four Kraus operators reaches it exactly). With r = 65 the fourth
     depolarizing channel makes 256 columns and is truncated to 65; the fifth would
-    need 260 and its truncation is refused with LR_ECAPACITY. The refusal leaves the
-    expanded state (Eq. 4 without the truncation) in place and readable."""
+    need 260 and its truncation is refused with LR_ECAPACITY. rho is then what it was
+    before the refused call: the accepted channel applied (Eq. 4), not truncated."""
     from paper_2009_06657_gb300._ffi import LRError, LR_ECAPACITY
     n, r = 7, 65
     ops = random_layered(n, 1, seed=1500, noise=("dep", 0.02), qubit_jitter=(0.5, 1.5))
