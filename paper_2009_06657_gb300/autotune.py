@@ -17,6 +17,10 @@ smaller n on a tie), and a rank with no entry at all takes 0 (the library's rule
 from rows_per_split).
 
     python -m paper_2009_06657_gb300.autotune --out table.json   (needs the GPU)
+
+The table read by default is `tuning/batch_splits.json` beside this module; the
+environment variable LRET_TUNING_TABLE names another file (for a GPU or a workload
+the committed table was not measured on).
 """
 from __future__ import annotations
 
@@ -25,7 +29,13 @@ import json
 import os
 
 DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "batch_splits.json")
+TABLE_ENV = "LRET_TUNING_TABLE"
 CANDIDATES = (1, 2, 4, 8, 16, 32, 64)
+
+
+def table_path():
+    """The table file in use: $LRET_TUNING_TABLE if set and non-empty, else the committed one."""
+    return os.environ.get(TABLE_ENV) or DEFAULT_TABLE
 
 
 class BatchTable:
@@ -74,13 +84,14 @@ class BatchTable:
             json.dump(self.to_json(), f, indent=1)
 
     @classmethod
-    def load(cls, path=DEFAULT_TABLE):
-        with open(path) as f:
+    def load(cls, path=None):
+        with open(path or table_path()) as f:
             d = json.load(f)
         return cls(d.get("entries", []), d.get("device", ""), d.get("candidates", CANDIDATES))
 
     @classmethod
-    def load_or_empty(cls, path=DEFAULT_TABLE):
+    def load_or_empty(cls, path=None):
+        path = path or table_path()
         return cls.load(path) if os.path.exists(path) else cls()
 
 
@@ -136,13 +147,14 @@ def tune(ns=range(8, 19), ranks=(8, 16, 32, 64), candidates=CANDIDATES, copies=8
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--out", default=DEFAULT_TABLE)
+    ap.add_argument("--out", default=None, help="table file to write (default: $LRET_TUNING_TABLE or the committed table)")
     ap.add_argument("--copies", type=int, default=8)
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     table = tune(copies=args.copies, reps=args.reps, log=print)
-    table.save(args.out)
-    print("wrote", args.out)
+    out = args.out or table_path()
+    table.save(out)
+    print("wrote", out)
 
 
 if __name__ == "__main__":

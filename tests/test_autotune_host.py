@@ -4,7 +4,7 @@ import os
 
 import pytest
 
-from paper_2009_06657_gb300.autotune import DEFAULT_TABLE, BatchTable
+from paper_2009_06657_gb300.autotune import DEFAULT_TABLE, TABLE_ENV, BatchTable, table_path
 
 
 def _table():
@@ -57,7 +57,7 @@ def test_committed_table_covers_the_batch_workload():
     if not os.path.exists(DEFAULT_TABLE):
         pytest.skip("no tuned table committed")
     d = json.load(open(DEFAULT_TABLE))
-    t = BatchTable.load()
+    t = BatchTable.load(DEFAULT_TABLE)
     assert d["device"] and t.entries
     for n in range(8, 19):
         for r in (8, 16, 32, 64):
@@ -65,3 +65,16 @@ def test_committed_table_covers_the_batch_workload():
             assert (n, r) in t.entries and 1 <= sp <= min(64, 1 << (n - 1))
             ms = t.times[(n, r)]
             assert min(ms, key=lambda k: (ms[k], int(k))) == str(sp)  # the fastest candidate was kept
+
+
+def test_environment_variable_names_the_table(tmp_path, monkeypatch):
+    p = tmp_path / "mine.json"
+    _table().save(str(p))
+    monkeypatch.setenv(TABLE_ENV, str(p))
+    assert table_path() == str(p)
+    t = BatchTable.load_or_empty()
+    assert t.device == "test" and t.lookup(12, 64) == 8
+    monkeypatch.setenv(TABLE_ENV, str(tmp_path / "missing.json"))
+    assert BatchTable.load_or_empty().entries == {}  # a named file that does not exist: no table
+    monkeypatch.delenv(TABLE_ENV)
+    assert table_path() == DEFAULT_TABLE
